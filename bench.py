@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark: f(A) b time-to-1e-8 relative error, double-pass vs single-pass
+multi-shift BiCGstab(l), and hop-kernel (stencil) GB/s against the HBM roofline.
+
+Default workload: 16^3 x 32 Wilson-Dirac lattice, U = exp(i 0.4 H) (seeded),
+mu = 0.1, m = -1.8, antiperiodic time, l = 2, Neuberger PFE with 20 poles,
+A scaled by a power-iteration estimate of its largest eigenvalue; synthetic
+stand-in for the paper's quenched gauge ensembles.
+
+One step = one solve y = f(A) b by the double-pass form in mixed precision
+(FP64 head until every live shift residual is below switch_resid |b|, then
+FP32 bulk with FP64 scalars), with b resident on the device and L2 flushed
+before each step.  value = mean ms per solve (lower is better).  The same
+line reports the single-pass FP64 and double-pass FP64/FP32 solves, each at
+the loosest tolerance whose result meets 1e-8 relative error against a
+tol = 1e-12 FP64 solve.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl fapath|reference]
+
+With torchrun (N > 1) each rank solves its own replica of the workload (the
+solves are independent; no collective on the data path): scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "f(A)b time-to-1e-8 rel err (double vs single pass); stencil GB/s vs HBM peak"
+TARGET = 1e-8
+TOLS = (1e-8, 3e-9, 1e-9, 3e-10, 1e-10, 3e-11, 1e-11)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="fapath", choices=["fapath", "reference"])
+    p.add_argument("--workload", default="wilson_16x16x16x32")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--switch-resid", type=float, default=0.0)
+    return p.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ oracle baseline (CPU)
+def oracle_sample(w, c, outer=1):
+    """Time `outer` outer iterations of the oracle's seed recurrence (the work
+    of one outer iteration of either pass of the oracle's double-pass form)."""
+    from oracle import dirac, msbicgstab as ms
+    op = dirac.Operator(w["U"], w["mass"], w["mu"], c, w["t_bc"])
+    t0 = time.perf_counter()
+    ms.seed_recurrence(op.A, w["b"], w["ell"], outer)
+    return time.perf_counter() - t0
+
+
+def golden_outer_iters(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            g = json.load(f)
+        return g["outer_iters"], g.get("oracle_seconds")
+    return None, None
+
+
+def cpu_baseline(w, c, outer_ref, outer=2):
+    t = oracle_sample(w, c, outer)
+    per_solve_ms = t / outer * 2 * outer_ref * 1e3
+    return {"value": per_solve_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"{outer} outer iterations of the FP64 numpy oracle's BiCGstab({w['ell']}) "
+                      f"recurrence on {'x'.join(map(str, w['dims']))} ({t:.1f} s), scaled by "
+                      f"2 x {outer_ref} outer iterations (pass 1 + pass 2 of the double-pass form); "
+                      f"numpy elementwise, 1 thread of {os.cpu_count()} host cores"}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 CPU oracle as it stands, rank 0 only."""
+    if rank != 0:
+        return
+    import inputs
+    from oracle import dirac, scale
+    w = inputs.make_workload(args.workload)
+    op = dirac.Operator(w["U"], w["mass"], w["mu"], 1.0, w["t_bc"])
+    c = scale.power_scale(op.A, w["v0"], 100)
+    outer_ref, _ = golden_outer_iters(args.workload)
+    if outer_ref is None:
+        outer_ref = 100
+    for _ in range(args.warmup):
+        oracle_sample(w, c, 1)
+    ts = [oracle_sample(w, c, 1) for _ in range(args.steps)]
+    per_solve = statistics.mean(ts) * 2 * outer_ref * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": per_solve, "unit": "ms", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args.workload, w),
+        "cpu_baseline": {"value": per_solve, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: 1 outer iteration of the FP64 numpy oracle's "
+                                   f"BiCGstab({w['ell']}) recurrence, scaled by 2 x {outer_ref} outer "
+                                   f"iterations (both passes of the oracle's double-pass solve)"},
+        "e2e": {"value": per_solve, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(name, w):
+    return {"workload": name, "lattice": "x".join(map(str, w["dims"])), "ell": w["ell"], "ns": w["ns"],
+            "mu": w["mu"], "mass": w["mass"], "eps": w["eps"], "poles": "neuberger",
+            "target_rel_err": TARGET, "l2": "flushed before every timed step (512 MB write)"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import inputs
+    import paper_1010_2592_gb300 as fa
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = inputs.make_workload(args.workload)
+    dims, ell, ns = w["dims"], w["ell"], w["ns"]
+    V = int(np.prod(dims))
+    stream = torch.cuda.current_stream()
+    ctx = fa.Context(dims, stream)
+    ctx.set_gauge(torch.from_numpy(w["U"]).cuda())
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], 1.0)
+    c = ctx.estimate_scale(torch.from_numpy(w["v0"]).cuda(), 100)
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], c)
+    om, sg = fa.neuberger_poles(ns)
+    ctx.set_poles(om, sg)
+    b = torch.from_numpy(w["b"]).cuda()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    # reference solution for the error measurement (untimed)
+    yref = ctx.apply_f(b, ell=ell, tol=1e-12, max_outer=4000, precision="f64").y
+    yref_norm = torch.linalg.vector_norm(yref).item()
+
+    def err(y):
+        return (torch.linalg.vector_norm(y - yref) / yref_norm).item()
+
+    variants = {
+        "double_mixed": dict(mode="double", precision="mixed", switch_resid=args.switch_resid),
+        "double_f64": dict(mode="double", precision="f64"),
+        "single_f64": dict(mode="single", precision="f64"),
+        "double_f32": dict(mode="double", precision="f32"),
+    }
+    chosen = {}
+    for name, kw in variants.items():
+        pick = None
+        for tol in TOLS:
+            r = ctx.apply_f(b, ell=ell, tol=tol, max_outer=4000, check=False, **kw)
+            e = err(r.y) if r.stats["status"] == 0 else float("inf")
+            pick = (tol, e, r.stats)
+            if e <= TARGET:
+                break
+        chosen[name] = pick
+
+    def timed(name, steps, warmup, hop=False):
+        kw = dict(variants[name])
+        tol = chosen[name][0]
+        for _ in range(warmup):
+            ctx.apply_f(b, ell=ell, tol=tol, max_outer=4000, **kw)
+        ms_list = []
+        launches = 0
+        last = None
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            n0 = ctx.launch_count()
+            s.record(stream)
+            last = ctx.apply_f(b, ell=ell, tol=tol, max_outer=4000, hop_timing=hop, **kw)
+            e.record(stream)
+            torch.cuda.synchronize()
+            launches += ctx.launch_count() - n0
+            ms_list.append(s.elapsed_time(e))
+        return ms_list, launches, last
+
+    # headline: double-pass, mixed precision, hop kernels timed with CUDA events
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.hop_timing_reset()
+    head_ms, head_launches, head_res = timed("double_mixed", args.steps, args.warmup, hop=True)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    ms_step = statistics.mean(head_ms)
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = t.item()
+    hop32_ms, hop32_n = ctx.hop_timing("f32")
+    hop64_ms, hop64_n = ctx.hop_timing("f64")
+
+    # comparison variants (fewer steps)
+    other = {}
+    for name in ("double_f64", "single_f64", "double_f32"):
+        k = max(1, min(args.steps, 3))
+        lst, _, res = timed(name, k, 1)
+        tol, e, _ = chosen[name]
+        other[name] = {"ms": statistics.mean(lst), "tol": tol, "rel_err": e,
+                       "outer_iters": res.stats["outer_iters"], "meets_1e-8": e <= TARGET}
+    tol_h, e_h, _ = chosen["double_mixed"]
+    other["double_mixed"] = {"ms": ms_step, "tol": tol_h, "rel_err": e_h,
+                             "outer_iters": head_res.stats["outer_iters"],
+                             "switch_outer": head_res.stats["switch_outer"], "meets_1e-8": e_h <= TARGET}
+
+    # end to end through the host-buffer entry point: pinned b in, pinned y out
+    b_pin = torch.from_numpy(w["b"]).pin_memory()
+    y_pin = torch.empty_like(b_pin).pin_memory()
+    kw = dict(variants["double_mixed"])
+    p = ctx.params(ell=ell, tol=tol_h, max_outer=4000, **kw)
+    st = fa.SolverStats()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = ctx.lib.fa_apply_f_host(ctx.h, b_pin.data_ptr(), y_pin.data_ptr(), p, st)
+        t1 = time.perf_counter()
+        assert rc == 0, rc
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_err = float(np.linalg.norm(y_pin.numpy() - yref.cpu().numpy()) / yref_norm)
+
+    # roofline of the FP32 hop kernel: 96 B in + 96 B out + 4 x 48 B links per site
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            peak, peak_src = float(json.load(f)["hbm_gbs"]), "measured"
+    hop_bytes = 384.0 * V
+    achieved = hop_bytes / (hop32_ms * 1e-3) / 1e9 if hop32_ms > 0 else None
+    hop64_gflop = 1320.0 * V / (hop64_ms * 1e-3) / 1e9 if hop64_ms > 0 else None
+
+    line = {
+        "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": config_of(args.workload, w),
+        "variants": other,
+        "speedup_double_mixed_vs_single_f64": other["single_f64"]["ms"] / ms_step,
+        "roofline": {"kernel": "hop_kernel<float> (one D_w sweep, FP32 12-real links)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_source": peak_src, "algorithmic_bytes_per_launch": hop_bytes,
+                     "mean_launch_ms": hop32_ms, "launches_timed": hop32_n},
+        "hop_f64": {"mean_launch_ms": hop64_ms, "launches_timed": hop64_n, "gflops_1320_per_site": hop64_gflop},
+        "stencil_gbs": achieved,
+        "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": int(b_pin.numel() * 16),
+                "d2h_bytes_per_step": int(y_pin.numel() * 16), "rel_err": e2e_err},
+        "gpu_launches": head_launches // max(1, args.steps),
+        "gpu_launches_total_timed": head_launches,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        outer_ref, _ = golden_outer_iters(args.workload)
+        if outer_ref is None:
+            outer_ref = head_res.stats["outer_iters"]
+        line["cpu_baseline"] = cpu_baseline(w, c, outer_ref)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,278 @@
+"""Python binding of libfapath: f(A) b by multi-shift BiCGstab(l) on a GB300.
+
+Argument marshalling only.  Every step of the computation runs in the CUDA
+kernels of `libfapath.so` behind the C-ABI declared in `include/fapath.h`;
+PyTorch provides device memory and the current CUDA stream.  There is no CPU
+fallback: importing works without a GPU, but every call needs the built
+library and a CUDA device, and raises otherwise.
+
+Fields are complex128 tensors in the canonical layouts
+    spinor (T, Z, Y, X, 4, 3)        gauge (T, Z, Y, X, 4, 3, 3)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfapath.so")
+
+FA_OK, FA_EINVAL, FA_ENOMEM, FA_ECUDA, FA_EBREAKDOWN, FA_ENOCONV, FA_ENONFINITE, FA_ETIMEOUT, \
+    FA_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
+SINGLE, DOUBLE = 0, 1
+F64, F32, MIXED = 0, 1, 2
+_PREC = {"f64": F64, "f32": F32, "mixed": MIXED, F64: F64, F32: F32, MIXED: MIXED}
+_MODE = {"single": SINGLE, "double": DOUBLE, SINGLE: SINGLE, DOUBLE: DOUBLE}
+
+EXPORTS = (
+    "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
+    "fa_set_poles", "fa_neuberger_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
+    "fa_apply_f", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
+    "fa_hop_timing_reset", "fa_status_string", "fa_last_error", "fa_version",
+)
+
+
+class FAError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load_library()
+        msg = lib.fa_status_string(status).decode()
+        detail = lib.fa_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}){': ' + detail if detail else ''}")
+        self.status = status
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("ell", ctypes.c_int), ("tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("mode", ctypes.c_int), ("precision", ctypes.c_int),
+                ("switch_resid", ctypes.c_double), ("flags", ctypes.c_int)]
+
+
+class SolverStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("switch_outer", ctypes.c_int), ("ns", ctypes.c_int),
+                ("iters_per_shift", ctypes.c_int * 64), ("resid_recurrence", ctypes.c_double),
+                ("n_mv", ctypes.c_longlong), ("n_dot", ctypes.c_longlong),
+                ("n_launch", ctypes.c_longlong), ("t_pass1_ms", ctypes.c_double),
+                ("t_sweep_ms", ctypes.c_double), ("t_pass2_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(status=self.status, outer_iters=self.outer_iters,
+                    switch_outer=self.switch_outer,
+                    iters_per_shift=list(self.iters_per_shift[:self.ns]),
+                    resid_recurrence=self.resid_recurrence, n_mv=self.n_mv, n_dot=self.n_dot,
+                    n_launch=self.n_launch, t_pass1_ms=self.t_pass1_ms,
+                    t_sweep_ms=self.t_sweep_ms, t_pass2_ms=self.t_pass2_ms)
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libfapath.so and declare its signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libfapath.so not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "fa_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), P]),
+        "fa_destroy": (I, [P]),
+        "fa_set_gauge": (I, [P, P, I]),
+        "fa_set_params": (I, [P, D, D, I, D]),
+        "fa_estimate_scale": (I, [P, P, I, ctypes.POINTER(D)]),
+        "fa_set_poles": (I, [P, I, P, P]),
+        "fa_neuberger_poles": (I, [I, P, P]),
+        "fa_apply_dw": (I, [P, P, P, I, I]),
+        "fa_apply_A": (I, [P, P, P, I, I]),
+        "fa_solve_multishift": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+        "fa_apply_f": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+        "fa_apply_f_host": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+        "fa_sync": (I, [P]),
+        "fa_launch_count": (LL, [P]),
+        "fa_hop_timing": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
+        "fa_hop_timing_reset": (I, [P]),
+        "fa_status_string": (ctypes.c_char_p, [I]),
+        "fa_last_error": (ctypes.c_char_p, []),
+        "fa_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _lib = L
+    return L
+
+
+def _check(status, where):
+    if status != FA_OK:
+        raise FAError(status, where)
+
+
+def neuberger_poles(ns):
+    """(omega, sigma) of Neuberger's expansion, computed by the library."""
+    lib = load_library()
+    om = np.empty(ns, dtype=np.float64)
+    sg = np.empty(ns, dtype=np.float64)
+    _check(lib.fa_neuberger_poles(ns, om.ctypes.data, sg.ctypes.data), "fa_neuberger_poles")
+    return om, sg
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the fapath path runs on the GPU only")
+    return torch
+
+
+def _spinor_check(t, shape, name):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128
+            and t.is_contiguous() and tuple(t.shape) == shape):
+        raise ValueError(f"{name}: expected a contiguous complex128 CUDA tensor of shape {shape}")
+    return t
+
+
+@dataclass
+class Result:
+    y: object
+    stats: dict
+
+
+class Context:
+    """One lattice, gauge field and operator, bound to a CUDA stream."""
+
+    def __init__(self, dims, stream=None):
+        torch = _torch()
+        self.lib = load_library()
+        self.dims = tuple(int(d) for d in dims)
+        X, Y, Z, T = self.dims
+        self.spinor_shape = (T, Z, Y, X, 4, 3)
+        self.gauge_shape = (T, Z, Y, X, 4, 3, 3)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        _check(self.lib.fa_create(ctypes.byref(h), arr, ctypes.c_void_p(self.stream.cuda_stream)),
+               "fa_create")
+        self.h = h
+        self.ns = 0
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.fa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_spinor(self):
+        torch = _torch()
+        return torch.empty(self.spinor_shape, dtype=torch.complex128, device="cuda")
+
+    # -- setup
+    def set_gauge(self, U):
+        torch = _torch()
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+            assert U.shape == self.gauge_shape
+            _check(self.lib.fa_set_gauge(self.h, U.ctypes.data, 0), "fa_set_gauge")
+        else:
+            if not (U.is_cuda and U.dtype == torch.complex128 and U.is_contiguous()
+                    and tuple(U.shape) == self.gauge_shape):
+                raise ValueError("gauge field: contiguous complex128 CUDA tensor expected")
+            _check(self.lib.fa_set_gauge(self.h, U.data_ptr(), 1), "fa_set_gauge")
+
+    def set_params(self, mass, mu, t_bc=-1, scale=1.0):
+        _check(self.lib.fa_set_params(self.h, float(mass), float(mu), int(t_bc), float(scale)),
+               "fa_set_params")
+
+    def set_poles(self, omega, sigma):
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        sg = np.ascontiguousarray(sigma, dtype=np.float64)
+        _check(self.lib.fa_set_poles(self.h, len(om), om.ctypes.data, sg.ctypes.data), "fa_set_poles")
+        self.ns = len(om)
+
+    def estimate_scale(self, v0, iters=100):
+        v0 = _spinor_check(v0, self.spinor_shape, "v0")
+        out = ctypes.c_double()
+        _check(self.lib.fa_estimate_scale(self.h, v0.data_ptr(), int(iters), ctypes.byref(out)),
+               "fa_estimate_scale")
+        return out.value
+
+    # -- operators
+    def apply_dw(self, x, dagger=False, precision="f64", out=None):
+        x = _spinor_check(x, self.spinor_shape, "x")
+        out = self.empty_spinor() if out is None else _spinor_check(out, self.spinor_shape, "out")
+        _check(self.lib.fa_apply_dw(self.h, x.data_ptr(), out.data_ptr(), int(bool(dagger)),
+                                    _PREC[precision]), "fa_apply_dw")
+        return out
+
+    def apply_A(self, x, dagger=False, precision="f64", out=None):
+        x = _spinor_check(x, self.spinor_shape, "x")
+        out = self.empty_spinor() if out is None else _spinor_check(out, self.spinor_shape, "out")
+        _check(self.lib.fa_apply_A(self.h, x.data_ptr(), out.data_ptr(), int(bool(dagger)),
+                                   _PREC[precision]), "fa_apply_A")
+        return out
+
+    # -- solvers
+    @staticmethod
+    def params(ell=2, tol=1e-10, max_outer=2000, mode="double", precision="f64",
+               switch_resid=0.0, timing=False, hop_timing=False):
+        return SolverParams(int(ell), float(tol), int(max_outer), _MODE[mode], _PREC[precision],
+                            float(switch_resid), (1 if timing else 0) | (2 if hop_timing else 0))
+
+    def apply_f(self, b, out=None, check=True, **kw):
+        b = _spinor_check(b, self.spinor_shape, "b")
+        y = self.empty_spinor() if out is None else _spinor_check(out, self.spinor_shape, "out")
+        p = self.params(**kw)
+        st = SolverStats()
+        rc = self.lib.fa_apply_f(self.h, b.data_ptr(), y.data_ptr(), ctypes.byref(p), ctypes.byref(st))
+        if check:
+            _check(rc, "fa_apply_f")
+        return Result(y, st.as_dict())
+
+    def apply_f_host(self, b, check=True, **kw):
+        """b, y in host memory (numpy complex128, canonical shape)."""
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        assert b.shape == self.spinor_shape
+        y = np.empty_like(b)
+        p = self.params(**kw)
+        st = SolverStats()
+        rc = self.lib.fa_apply_f_host(self.h, b.ctypes.data, y.ctypes.data, ctypes.byref(p),
+                                      ctypes.byref(st))
+        if check:
+            _check(rc, "fa_apply_f_host")
+        return Result(y, st.as_dict())
+
+    def solve_multishift(self, b, **kw):
+        b = _spinor_check(b, self.spinor_shape, "b")
+        xs = [self.empty_spinor() for _ in range(self.ns)]
+        ptrs = (ctypes.c_void_p * self.ns)(*[x.data_ptr() for x in xs])
+        kw.setdefault("mode", "single")
+        p = self.params(**kw)
+        st = SolverStats()
+        _check(self.lib.fa_solve_multishift(self.h, b.data_ptr(), ptrs, ctypes.byref(p),
+                                            ctypes.byref(st)), "fa_solve_multishift")
+        return Result(xs, st.as_dict())
+
+    def sync(self):
+        _check(self.lib.fa_sync(self.h), "fa_sync")
+
+    def launch_count(self):
+        return int(self.lib.fa_launch_count(self.h))
+
+    def hop_timing(self, precision="f32"):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(self.lib.fa_hop_timing(self.h, _PREC[precision], ctypes.byref(ms), ctypes.byref(n)),
+               "fa_hop_timing")
+        return ms.value, n.value
+
+    def hop_timing_reset(self):
+        _check(self.lib.fa_hop_timing_reset(self.h), "fa_hop_timing_reset")

@@ -1,0 +1,266 @@
+// C-ABI entry points of libfapath (declared in include/fapath.h).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "fa_context.h"
+
+namespace fa {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return FA_ECUDA;
+}
+
+}  // namespace fa
+
+using namespace fa;
+
+#define CUDA_OR(x, what)                                   \
+    do {                                                   \
+        cudaError_t _e = (x);                              \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+#define TRY(x)                        \
+    do {                              \
+        int _rc = (x);                \
+        if (_rc != FA_OK) return _rc; \
+    } while (0)
+
+extern "C" {
+
+const char* fa_version(void) { return "fapath 0.1 (sm_103a)"; }
+
+const char* fa_last_error(void) { return g_err; }
+
+const char* fa_status_string(int s) {
+    switch (s) {
+        case FA_OK: return "ok";
+        case FA_EINVAL: return "invalid argument";
+        case FA_ENOMEM: return "out of memory";
+        case FA_ECUDA: return "CUDA error";
+        case FA_EBREAKDOWN: return "Krylov breakdown";
+        case FA_ENOCONV: return "not converged within max_outer";
+        case FA_ENONFINITE: return "non-finite recurrence scalar";
+        case FA_ETIMEOUT: return "device wait timed out";
+        case FA_ESTATE: return "call out of order (gauge field, parameters or poles missing)";
+        default: return "unknown status";
+    }
+}
+
+int fa_create(fa_ctx** out, const int dims[4], void* cuda_stream) {
+    if (!out || !dims) return FA_EINVAL;
+    *out = nullptr;
+    for (int k = 0; k < 4; ++k)
+        if (dims[k] < 2 || dims[k] > 4096) {
+            set_error("fa_create: extent %d out of range", dims[k]);
+            return FA_EINVAL;
+        }
+    const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V > (1LL << 26)) {
+        set_error("fa_create: volume %lld above 2^26 sites", V);
+        return FA_EINVAL;
+    }
+    fa_ctx* c = new (std::nothrow) fa_ctx();
+    if (!c) return FA_ENOMEM;
+    c->g = Geom{dims[0], dims[1], dims[2], dims[3], (int)V};
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "fa_create: cudaGetDevice");
+    }
+    *out = c;
+    return FA_OK;
+}
+
+int fa_destroy(fa_ctx* c) {
+    if (!c) return FA_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : c->hop_ev) cudaEventDestroy(e);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    delete c;
+    return FA_OK;
+}
+
+int fa_set_gauge(fa_ctx* c, const double* U, int on_device) {
+    if (!c || !U) return FA_EINVAL;
+    const int V = c->g.V;
+    const size_t canon_bytes = (size_t)V * 72 * sizeof(double);
+    CUDA_OR(c->links64.ensure((size_t)36 * V * sizeof(double2)), "fa_set_gauge: alloc FP64 links");
+    CUDA_OR(c->links32.ensure((size_t)12 * V * sizeof(float4)), "fa_set_gauge: alloc FP32 links");
+    const double* src = U;
+    DevBuf stage;
+    if (!on_device) {
+        CUDA_OR(stage.ensure(canon_bytes), "fa_set_gauge: alloc staging");
+        CUDA_OR(cudaMemcpyAsync(stage.p, U, canon_bytes, cudaMemcpyHostToDevice, c->stream), "fa_set_gauge: copy");
+        src = stage.as<double>();
+    }
+    TRY(launch_pack_links(c->g, src, c->links64.as<double2>(), c->links32.as<float4>(), c->stream));
+    c->launches++;
+    CUDA_OR(cudaStreamSynchronize(c->stream), "fa_set_gauge: sync");
+    c->have_gauge = true;
+    return FA_OK;
+}
+
+int fa_set_params(fa_ctx* c, double wilson_mass, double mu, int t_bc, double scale_c) {
+    if (!c) return FA_EINVAL;
+    if (!std::isfinite(wilson_mass) || !std::isfinite(mu) || !(t_bc == 1 || t_bc == -1) ||
+        !(scale_c > 0.0) || !std::isfinite(scale_c) || std::fabs(mu) > 20.0)
+        return FA_EINVAL;
+    c->mass = wilson_mass;
+    c->mu = mu;
+    c->t_bc = (double)t_bc;
+    c->scale_c = scale_c;
+    c->have_params = true;
+    return FA_OK;
+}
+
+int fa_set_poles(fa_ctx* c, int ns, const double* omega, const double* sigma) {
+    if (!c || !omega || !sigma || ns < 1 || ns > kMaxShifts) return FA_EINVAL;
+    for (int s = 0; s < ns; ++s)
+        if (!(sigma[s] > 0.0) || !std::isfinite(sigma[s]) || !std::isfinite(omega[s])) return FA_EINVAL;
+    c->ns = ns;
+    for (int s = 0; s < ns; ++s) {
+        c->omega[s] = omega[s];
+        c->sigma[s] = sigma[s];
+    }
+    c->have_poles = true;
+    return FA_OK;
+}
+
+int fa_neuberger_poles(int ns, double* omega, double* sigma) {
+    if (ns < 1 || ns > kMaxShifts || !omega || !sigma) return FA_EINVAL;
+    const double pi = 3.14159265358979323846;
+    for (int s = 1; s <= ns; ++s) {
+        const double th = pi * (s - 0.5) / (2.0 * ns);
+        const double cth = std::cos(th);
+        omega[s - 1] = (1.0 / ns) / (cth * cth);
+        const double t = std::tan(th);
+        sigma[s - 1] = t * t;
+    }
+    return FA_OK;
+}
+
+int fa_estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out) {
+    if (!c) return FA_EINVAL;
+    return estimate_scale(c, v0, iters, scale_out);
+}
+
+// canonical in -> internal (FP64 or FP32), one or two hops, -> canonical out
+static int apply_op(fa_ctx* c, const double* in, double* out, int dagger, int precision, bool is_A) {
+    if (!c || !in || !out || in == out) return FA_EINVAL;
+    if (!c->have_gauge || !c->have_params) return FA_ESTATE;
+    const int V = c->g.V;
+    cudaStream_t st = c->stream;
+    const bool dg = dagger != 0;
+    if (precision == FA_F64) {
+        const size_t b = (size_t)12 * V * sizeof(double2);
+        CUDA_OR(c->io64a.ensure(b), "alloc");
+        CUDA_OR(c->io64b.ensure(b), "alloc");
+        double2 *a = c->io64a.as<double2>(), *o = c->io64b.as<double2>();
+        TRY(launch_pack_spinor_f64(c->g, in, a, st));
+        if (is_A) {
+            CUDA_OR(c->tmp64.ensure(b), "alloc");
+            double2* t = c->tmp64.as<double2>();
+            TRY(hop_f64(c, a, t, 1.0, false, true, dg, nullptr, nullptr, nullptr));
+            TRY(hop_f64(c, t, o, c->scale_c, false, true, dg, nullptr, nullptr, nullptr));
+        } else {
+            TRY(hop_f64(c, a, o, 1.0, dg, dg, dg, nullptr, nullptr, nullptr));
+        }
+        TRY(launch_unpack_spinor_f64(c->g, o, out, st));
+    } else if (precision == FA_F32) {
+        const size_t b = (size_t)6 * V * sizeof(float4);
+        CUDA_OR(c->io32a.ensure(b), "alloc");
+        CUDA_OR(c->io32b.ensure(b), "alloc");
+        float4 *a = c->io32a.as<float4>(), *o = c->io32b.as<float4>();
+        TRY(launch_pack_spinor_f32(c->g, in, a, st));
+        if (is_A) {
+            CUDA_OR(c->tmp32.ensure(b), "alloc");
+            float4* t = c->tmp32.as<float4>();
+            TRY(hop_f32(c, a, t, 1.0, false, true, dg, nullptr, nullptr, nullptr));
+            TRY(hop_f32(c, t, o, c->scale_c, false, true, dg, nullptr, nullptr, nullptr));
+        } else {
+            TRY(hop_f32(c, a, o, 1.0, dg, dg, dg, nullptr, nullptr, nullptr));
+        }
+        TRY(launch_unpack_spinor_f32(c->g, o, out, st));
+    } else {
+        return FA_EINVAL;
+    }
+    c->launches += 2;
+    return FA_OK;
+}
+
+int fa_apply_dw(fa_ctx* c, const double* in, double* out, int dagger, int precision) {
+    return apply_op(c, in, out, dagger, precision, false);
+}
+
+int fa_apply_A(fa_ctx* c, const double* in, double* out, int dagger, int precision) {
+    return apply_op(c, in, out, dagger, precision, true);
+}
+
+int fa_solve_multishift(fa_ctx* c, const double* b, double* const* x_s, const fa_solver_params* p,
+                        fa_solver_stats* stats) {
+    if (!c || !b || !x_s || !p) return FA_EINVAL;
+    if (p->mode != FA_SINGLE || p->precision != FA_F64) return FA_EINVAL;
+    for (int s = 0; s < c->ns; ++s)
+        if (!x_s[s]) return FA_EINVAL;
+    return solve(c, b, nullptr, x_s, p, stats);
+}
+
+int fa_apply_f(fa_ctx* c, const double* b, double* y, const fa_solver_params* p, fa_solver_stats* stats) {
+    if (!c || !b || !y || !p || b == y) return FA_EINVAL;
+    return solve(c, b, y, nullptr, p, stats);
+}
+
+int fa_apply_f_host(fa_ctx* c, const double* b_host, double* y_host, const fa_solver_params* p,
+                    fa_solver_stats* stats) {
+    if (!c || !b_host || !y_host || !p) return FA_EINVAL;
+    const size_t bytes = (size_t)c->g.V * 24 * sizeof(double);
+    CUDA_OR(c->bhost_dev.ensure(bytes), "alloc staging");
+    CUDA_OR(c->yhost_dev.ensure(bytes), "alloc staging");
+    CUDA_OR(cudaMemcpyAsync(c->bhost_dev.p, b_host, bytes, cudaMemcpyHostToDevice, c->stream), "copy b");
+    const int rc = solve(c, c->bhost_dev.as<double>(), c->yhost_dev.as<double>(), nullptr, p, stats);
+    if (rc != FA_OK) return rc;
+    CUDA_OR(cudaMemcpyAsync(y_host, c->yhost_dev.p, bytes, cudaMemcpyDeviceToHost, c->stream), "copy y");
+    CUDA_OR(cudaStreamSynchronize(c->stream), "sync");
+    return FA_OK;
+}
+
+int fa_sync(fa_ctx* c) {
+    if (!c) return FA_EINVAL;
+    CUDA_OR(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "fa_sync");
+    CUDA_OR(cudaGetLastError(), "fa_sync");
+    return FA_OK;
+}
+
+long long fa_launch_count(const fa_ctx* c) { return c ? c->launches : -1; }
+
+int fa_hop_timing(const fa_ctx* c, int precision, double* mean_ms, long long* count) {
+    if (!c || !mean_ms || !count || (precision != FA_F64 && precision != FA_F32)) return FA_EINVAL;
+    const int k = precision == FA_F64 ? 0 : 1;
+    *count = c->hop_count[k];
+    *mean_ms = c->hop_count[k] ? c->hop_ms[k] / (double)c->hop_count[k] : 0.0;
+    return FA_OK;
+}
+
+int fa_hop_timing_reset(fa_ctx* c) {
+    if (!c) return FA_EINVAL;
+    c->hop_ms[0] = c->hop_ms[1] = 0.0;
+    c->hop_count[0] = c->hop_count[1] = 0;
+    return FA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// Wilson-Dirac hop kernels D_w(mu) for sm_103a, FP64 (18-real links) and
+// FP32 (12-real links), plus layout conversions.
+//
+// D_w(mu) is named in Sec. 1 (the kernel of the overlap operator at nonzero
+// chemical potential); the definition implemented is the standard mass form
+//   (D psi)(x) = (4+m) psi(x) - 1/2 sum_nu [ f+ (1 - g_nu) U_nu(x) psi(x+nu)
+//                                          + f- (1 + g_nu) U_nu(x-nu)^H psi(x-nu) ]
+// with f+- = e^{+-mu} on time hops and the time-boundary sign on hops that
+// cross t = T-1 <-> 0.  Each hop projects the neighbour spinor to a half
+// spinor with the DeGrand-Rossi projector (1 -+ g_nu), multiplies the two
+// colour vectors by the link and rebuilds the lower spin components.
+//
+// One thread per site; the nearest-neighbour reuse of spinors and links is
+// left to L1/L2 (the 126 MB L2 holds several time slices of every field even
+// on 32^3 x 64).  Memory traffic floor per site and sweep: one spinor in, one
+// out, four links (FP32: 96 + 96 + 4 * 48 = 384 B).
+#include "fa_internal.cuh"
+
+namespace fa {
+
+// projector P = 1 - S g_MU (S = +1 forward hop, -1 backward hop) applied to
+// the 4 spin x 3 colour spinor p, as the two independent spin rows h0, h1.
+// i*a = (-a.i, a.r).
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const cx<R> p[12], cx<R> h[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<R> a0 = p[c], a1 = p[3 + c], a2 = p[6 + c], a3 = p[9 + c];
+        if (MU == 0) {        // h0 = a0 - S i a3, h1 = a1 - S i a2
+            h[c] = {a0.r + S * a3.i, a0.i - S * a3.r};
+            h[3 + c] = {a1.r + S * a2.i, a1.i - S * a2.r};
+        } else if (MU == 1) { // h0 = a0 + S a3, h1 = a1 - S a2
+            h[c] = {a0.r + S * a3.r, a0.i + S * a3.i};
+            h[3 + c] = {a1.r - S * a2.r, a1.i - S * a2.i};
+        } else if (MU == 2) { // h0 = a0 - S i a2, h1 = a1 + S i a3
+            h[c] = {a0.r + S * a2.i, a0.i - S * a2.r};
+            h[3 + c] = {a1.r - S * a3.i, a1.i + S * a3.r};
+        } else {              // h0 = a0 - S a2, h1 = a1 - S a3
+            h[c] = {a0.r - S * a2.r, a0.i - S * a2.i};
+            h[3 + c] = {a1.r - S * a3.r, a1.i - S * a3.i};
+        }
+    }
+}
+
+// acc += P psi given the projected, link-multiplied half spinor h.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void recon_add(cx<R> acc[12], const cx<R> h[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cx<R> h0 = h[c], h1 = h[3 + c];
+        acc[c] = cadd(acc[c], h0);
+        acc[3 + c] = cadd(acc[3 + c], h1);
+        if (MU == 0) {        // rows 2,3: S i h1, S i h0
+            acc[6 + c] = {acc[6 + c].r - S * h1.i, acc[6 + c].i + S * h1.r};
+            acc[9 + c] = {acc[9 + c].r - S * h0.i, acc[9 + c].i + S * h0.r};
+        } else if (MU == 1) { // rows 2,3: -S h1, S h0
+            acc[6 + c] = {acc[6 + c].r - S * h1.r, acc[6 + c].i - S * h1.i};
+            acc[9 + c] = {acc[9 + c].r + S * h0.r, acc[9 + c].i + S * h0.i};
+        } else if (MU == 2) { // rows 2,3: S i h0, -S i h1
+            acc[6 + c] = {acc[6 + c].r - S * h0.i, acc[6 + c].i + S * h0.r};
+            acc[9 + c] = {acc[9 + c].r + S * h1.i, acc[9 + c].i - S * h1.r};
+        } else {              // rows 2,3: -S h0, -S h1
+            acc[6 + c] = {acc[6 + c].r - S * h0.r, acc[6 + c].i - S * h0.i};
+            acc[9 + c] = {acc[9 + c].r - S * h1.r, acc[9 + c].i - S * h1.i};
+        }
+    }
+}
+
+template <typename R, bool G5IN>
+__device__ __forceinline__ void load_in(const SpinorView<R>& in, int s, cx<R> p[12]) {
+    in.load(s, p);
+    if (G5IN) {
+#pragma unroll
+        for (int k = 6; k < 12; ++k) p[k] = {-p[k].r, -p[k].i};
+    }
+}
+
+// forward hop from site s to neighbour nb: acc += w (1 - g_MU) U_MU(s) psi(nb)
+template <int MU, bool WEIGHT, bool G5IN, typename R>
+__device__ __forceinline__ void hop_fwd(cx<R> acc[12], const SpinorView<R>& in, const LinkView<R>& U,
+                                        int s, int nb, R w) {
+    cx<R> p[12], h[6], L[3][3], c[6];
+    load_in<R, G5IN>(in, nb, p);
+    project<MU, +1>(p, h);
+    U.load(MU, s, L);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<R> t = cmul(L[a][0], h[3 * sp]);
+            t = cfma(L[a][1], h[3 * sp + 1], t);
+            t = cfma(L[a][2], h[3 * sp + 2], t);
+            c[3 * sp + a] = WEIGHT ? cscale(w, t) : t;
+        }
+    recon_add<MU, +1>(acc, c);
+}
+
+// backward hop: acc += w (1 + g_MU) U_MU(nb)^H psi(nb), nb = s - MU
+template <int MU, bool WEIGHT, bool G5IN, typename R>
+__device__ __forceinline__ void hop_bwd(cx<R> acc[12], const SpinorView<R>& in, const LinkView<R>& U,
+                                        int nb, R w) {
+    cx<R> p[12], h[6], L[3][3], c[6];
+    load_in<R, G5IN>(in, nb, p);
+    project<MU, -1>(p, h);
+    U.load(MU, nb, L);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<R> t = cmul(cx<R>{L[0][a].r, -L[0][a].i}, h[3 * sp]);
+            t = cjfma(L[1][a], h[3 * sp + 1], t);
+            t = cjfma(L[2][a], h[3 * sp + 2], t);
+            c[3 * sp + a] = WEIGHT ? cscale(w, t) : t;
+        }
+    recon_add<MU, -1>(acc, c);
+}
+
+template <typename R, bool G5IN, bool G5OUT, bool DOT>
+__global__ void __launch_bounds__(kThreads)
+hop_kernel(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb,
+           R bc, SpinorView<R> dotv, double2* partials, const int* done) {
+    if (done != nullptr && *done) return;
+    const int s = blockIdx.x * kThreads + threadIdx.x;
+    cx<R> dres[1] = {czero<R>()};
+    if (s < g.V) {
+        const int X = g.X, Y = g.Y, Z = g.Z, T = g.T;
+        const int x = s % X;
+        const int r1 = s / X;
+        const int y = r1 % Y;
+        const int r2 = r1 / Y;
+        const int z = r2 % Z;
+        const int t = r2 / Z;
+        const int sY = X, sZ = X * Y, sT = X * Y * Z;
+        cx<R> acc[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = czero<R>();
+        hop_fwd<0, false, G5IN>(acc, in, U, s, (x == X - 1) ? s - (X - 1) : s + 1, R(1));
+        hop_bwd<0, false, G5IN>(acc, in, U, (x == 0) ? s + (X - 1) : s - 1, R(1));
+        hop_fwd<1, false, G5IN>(acc, in, U, s, (y == Y - 1) ? s - (Y - 1) * sY : s + sY, R(1));
+        hop_bwd<1, false, G5IN>(acc, in, U, (y == 0) ? s + (Y - 1) * sY : s - sY, R(1));
+        hop_fwd<2, false, G5IN>(acc, in, U, s, (z == Z - 1) ? s - (Z - 1) * sZ : s + sZ, R(1));
+        hop_bwd<2, false, G5IN>(acc, in, U, (z == 0) ? s + (Z - 1) * sZ : s - sZ, R(1));
+        const R wf = (t == T - 1) ? mulR(ef, bc) : ef;
+        const R wb = (t == 0) ? mulR(eb, bc) : eb;
+        hop_fwd<3, true, G5IN>(acc, in, U, s, (t == T - 1) ? s - (T - 1) * sT : s + sT, wf);
+        hop_bwd<3, true, G5IN>(acc, in, U, (t == 0) ? s + (T - 1) * sT : s - sT, wb);
+        cx<R> p[12];
+        load_in<R, G5IN>(in, s, p);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const bool neg = G5OUT && k >= 6;
+            const R a = neg ? -cdiag : cdiag;
+            const R b = neg ? -chop : chop;
+            cx<R> o = cscale(a, p[k]);
+            o = crfma(b, acc[k], o);
+            p[k] = o;
+        }
+        out.store(s, p);
+        if (DOT) {
+            cx<R> d[12];
+            dotv.load(s, d);
+            cx<R> a = czero<R>();
+#pragma unroll
+            for (int k = 0; k < 12; ++k) a = cjfma(d[k], p[k], a);
+            dres[0] = a;
+        }
+    }
+    if (DOT) block_reduce_store<1, R>(dres, partials, 0);
+}
+
+template <typename R, typename LP, typename SP>
+static int launch_hop_t(const Geom& g, const LP* links, const SP* in, SP* out, double diag, double ef,
+                        double eb, double t_bc, double scale, bool g5in, bool g5out, const SP* dot_with,
+                        double2* partials, const int* done, cudaStream_t st) {
+    LinkView<R> U{links, g.V};
+    SpinorView<R> vin{const_cast<SP*>(in), g.V};
+    SpinorView<R> vout{out, g.V};
+    SpinorView<R> vd{const_cast<SP*>(dot_with), g.V};
+    const R cdiag = (R)(scale * diag), chop = (R)(-0.5 * scale);
+    const R ref = (R)ef, reb = (R)eb, rbc = (R)t_bc;
+    const int nb = nblocks(g.V);
+    const bool dot = dot_with != nullptr;
+#define FA_HOP(A, B, C) hop_kernel<R, A, B, C><<<nb, kThreads, 0, st>>>(g, U, vin, vout, cdiag, chop, ref, reb, rbc, vd, partials, done)
+    if (!g5in && !g5out && !dot) FA_HOP(false, false, false);
+    else if (!g5in && g5out && !dot) FA_HOP(false, true, false);
+    else if (!g5in && g5out && dot) FA_HOP(false, true, true);
+    else if (g5in && g5out && !dot) FA_HOP(true, true, false);
+    else if (!g5in && !g5out && dot) FA_HOP(false, false, true);
+    else return FA_EINVAL;
+#undef FA_HOP
+    return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA;
+}
+
+int launch_hop_f64(const Geom& g, const double2* links, const double2* in, double2* out, double diag,
+                   double ef, double eb, double t_bc, double scale, bool g5in, bool g5out,
+                   const double2* dot_with, double2* partials, const int* done, cudaStream_t st) {
+    return launch_hop_t<double>(g, links, in, out, diag, ef, eb, t_bc, scale, g5in, g5out, dot_with,
+                                partials, done, st);
+}
+
+int launch_hop_f32(const Geom& g, const float4* links, const float4* in, float4* out, double diag,
+                   double ef, double eb, double t_bc, double scale, bool g5in, bool g5out,
+                   const float4* dot_with, double2* partials, const int* done, cudaStream_t st) {
+    return launch_hop_t<float>(g, links, in, out, diag, ef, eb, t_bc, scale, g5in, g5out, dot_with,
+                               partials, done, st);
+}
+
+// ------------------------------------------------------------------ layout conversions
+// canonical spinor: double [V][12][2]; element (s, k) at 2*(12 s + k)
+__global__ void pack_f64_kernel(int V, const double2* __restrict__ canon, double2* __restrict__ out) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = k*V + s
+    if (idx >= 12 * V) return;
+    const int k = idx / V, s = idx - k * V;
+    out[idx] = canon[(size_t)s * 12 + k];
+}
+
+__global__ void unpack_f64_kernel(int V, const double2* __restrict__ in, double2* __restrict__ canon) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = 12*s + k
+    if (idx >= 12 * V) return;
+    const int s = idx / 12, k = idx - s * 12;
+    canon[idx] = in[(size_t)k * V + s];
+}
+
+__global__ void pack_f32_kernel(int V, const double2* __restrict__ canon, float4* __restrict__ out) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = q*V + s
+    if (idx >= 6 * V) return;
+    const int q = idx / V, s = idx - q * V;
+    const double2 a = canon[(size_t)s * 12 + 2 * q], b = canon[(size_t)s * 12 + 2 * q + 1];
+    out[idx] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+__global__ void unpack_f32_kernel(int V, const float4* __restrict__ in, double2* __restrict__ canon) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = 6*s + q
+    if (idx >= 6 * V) return;
+    const int s = idx / 6, q = idx - s * 6;
+    const float4 a = in[(size_t)q * V + s];
+    canon[(size_t)s * 12 + 2 * q] = make_double2(a.x, a.y);
+    canon[(size_t)s * 12 + 2 * q + 1] = make_double2(a.z, a.w);
+}
+
+__global__ void convert_f64_f32_kernel(int V, const double2* __restrict__ in, float4* __restrict__ out) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = q*V + s
+    if (idx >= 6 * V) return;
+    const int q = idx / V, s = idx - q * V;
+    const double2 a = in[(size_t)(2 * q) * V + s], b = in[(size_t)(2 * q + 1) * V + s];
+    out[idx] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+// canonical links: double [V][4][3][3][2]
+__global__ void pack_links_kernel(int V, const double2* __restrict__ canon, double2* __restrict__ l64,
+                                  float4* __restrict__ l32) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = mu*V + s
+    if (idx >= 4 * V) return;
+    const int mu = idx / V, s = idx - mu * V;
+    const double2* src = canon + ((size_t)s * 4 + mu) * 9;
+    double2 e[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) e[k] = src[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) l64[((size_t)mu * 9 + k) * V + s] = e[k];
+    if (l32 != nullptr) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            l32[((size_t)mu * 3 + q) * V + s] =
+                make_float4((float)e[2 * q].x, (float)e[2 * q].y, (float)e[2 * q + 1].x, (float)e[2 * q + 1].y);
+    }
+}
+
+static int grid_for(size_t n) { return (int)((n + kThreads - 1) / kThreads); }
+static int last_status() { return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA; }
+
+int launch_pack_spinor_f64(const Geom& g, const double* canon, double2* out, cudaStream_t st) {
+    pack_f64_kernel<<<grid_for((size_t)12 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, out);
+    return last_status();
+}
+int launch_unpack_spinor_f64(const Geom& g, const double2* in, double* canon, cudaStream_t st) {
+    unpack_f64_kernel<<<grid_for((size_t)12 * g.V), kThreads, 0, st>>>(g.V, in, (double2*)canon);
+    return last_status();
+}
+int launch_pack_spinor_f32(const Geom& g, const double* canon, float4* out, cudaStream_t st) {
+    pack_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, out);
+    return last_status();
+}
+int launch_unpack_spinor_f32(const Geom& g, const float4* in, double* canon, cudaStream_t st) {
+    unpack_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, in, (double2*)canon);
+    return last_status();
+}
+int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, cudaStream_t st) {
+    pack_links_kernel<<<grid_for((size_t)4 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, l64, l32);
+    return last_status();
+}
+int launch_convert_f64_to_f32(const Geom& g, const double2* in, float4* out, cudaStream_t st) {
+    convert_f64_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, in, out);
+    return last_status();
+}
+
+}  // namespace fa

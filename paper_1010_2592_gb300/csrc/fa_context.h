@@ -1,0 +1,93 @@
+// Host-side context of libfapath (the opaque fa_ctx of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <vector>
+#include <string>
+
+#include "fa_internal.cuh"
+
+struct fa_ctx;
+
+namespace fa {
+
+// Device allocation that frees itself.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // (re)allocate to at least n bytes; contents undefined
+    cudaError_t ensure(size_t n) {
+        if (bytes >= n && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        bytes = n;
+        return cudaSuccess;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace fa
+
+struct fa_ctx {
+    fa::Geom g{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    // gauge field
+    fa::DevBuf links64, links32;
+    bool have_gauge = false;
+    // operator parameters
+    double mass = 0.0, mu = 0.0, t_bc = -1.0, scale_c = 1.0;
+    bool have_params = false;
+    // poles
+    int ns = 0;
+    double omega[fa::kMaxShifts] = {}, sigma[fa::kMaxShifts] = {};
+    bool have_poles = false;
+
+    // scratch of the operator entry points and the solver
+    fa::DevBuf io64a, io64b, io32a, io32b, tmp64, tmp32;
+    fa::DevBuf partials;                 // reduction partials
+    fa::DevBuf state;                    // DevState
+    fa::DevBuf shiftbuf;                 // sigma, omega, zeta, zeta_p, active, iters
+    fa::DevBuf rec;                      // alpha, beta, gamma records
+    fa::DevBuf prec, coef, cs;           // per-shift record, pass-2 weights, sweep output
+    fa::DevBuf r64, u64, rt64, r32, u32, rt32;   // seed vectors (l+1 each, contiguous)
+    fa::DevBuf y64;                      // accumulated result (FP64 internal)
+    fa::DevBuf xs64, us64;               // single-pass shift vectors
+    fa::DevBuf bhost_dev, yhost_dev;     // canonical staging for fa_apply_f_host
+    void* pinned = nullptr;              // host copy of DevState
+    size_t pinned_bytes = 0;
+
+    long long launches = 0;
+    // hop-kernel timing (index 0: FP64, 1: FP32)
+    double hop_ms[2] = {0.0, 0.0};
+    long long hop_count[2] = {0, 0};
+    bool hop_timing = false;
+    std::vector<cudaEvent_t> hop_ev;     // start/stop pairs, reused across solves
+    std::vector<int> hop_ev_kind;        // precision index of each recorded pair
+    size_t hop_ev_used = 0;              // pairs recorded since the last collection
+};
+
+namespace fa {
+// operator application on internal layouts (used by the C-ABI and the solver)
+int hop_f64(fa_ctx* c, const double2* in, double2* out, double scale, bool g5in, bool g5out, bool dagger_mu,
+            const double2* dot_with, double2* partials, const int* done);
+int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, bool g5out, bool dagger_mu,
+            const float4* dot_with, double2* partials, const int* done);
+int solve(fa_ctx* c, const double* b_canon, double* y_canon, double* const* xs_canon,
+          const fa_solver_params* p, fa_solver_stats* stats);
+int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out);
+}  // namespace fa

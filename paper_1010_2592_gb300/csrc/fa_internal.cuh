@@ -1,0 +1,233 @@
+// Internal definitions shared by the CUDA translation units of libfapath.
+//
+// Internal layouts (structure of arrays, one thread per lattice site):
+//   FP64 spinor  double2 [12][V]        component k = 3*spin + colour
+//   FP32 spinor  float4  [6][V]         chunk q holds components 2q, 2q+1
+//   FP64 links   double2 [4][9][V]      element 3*row + col of U_mu(x)
+//   FP32 links   float4  [4][3][V]      rows 0-1 (6 complex); row 2 rebuilt
+// Site index s = x + X*(y + Y*(z + Z*t)), as in the canonical layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "fapath.h"
+
+namespace fa {
+
+constexpr int kMaxEll = 8;
+constexpr int kMaxShifts = 64;
+constexpr int kThreads = 256;          // block size of all site kernels
+constexpr int kScalarThreads = 256;    // block size of the single-block scalar kernels
+
+struct Geom {
+    int X, Y, Z, T;
+    int V;
+};
+
+// ------------------------------------------------------------------ complex
+template <typename R> struct cx { R r, i; };
+
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mulR(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mulR(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float addR(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double addR(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float subR(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double subR(double a, double b) { return __dsub_rn(a, b); }
+
+template <typename R> __device__ __forceinline__ cx<R> czero() { return {R(0), R(0)}; }
+template <typename R> __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return {addR(a.r, b.r), addR(a.i, b.i)}; }
+template <typename R> __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return {subR(a.r, b.r), subR(a.i, b.i)}; }
+// acc + a*b
+template <typename R> __device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> acc) {
+    acc.r = fmaR(a.r, b.r, acc.r);
+    acc.r = fmaR(-a.i, b.i, acc.r);
+    acc.i = fmaR(a.r, b.i, acc.i);
+    acc.i = fmaR(a.i, b.r, acc.i);
+    return acc;
+}
+// acc + conj(a)*b
+template <typename R> __device__ __forceinline__ cx<R> cjfma(cx<R> a, cx<R> b, cx<R> acc) {
+    acc.r = fmaR(a.r, b.r, acc.r);
+    acc.r = fmaR(a.i, b.i, acc.r);
+    acc.i = fmaR(a.r, b.i, acc.i);
+    acc.i = fmaR(-a.i, b.r, acc.i);
+    return acc;
+}
+template <typename R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+    cx<R> t;
+    t.r = fmaR(-a.i, b.i, mulR(a.r, b.r));
+    t.i = fmaR(a.i, b.r, mulR(a.r, b.i));
+    return t;
+}
+template <typename R> __device__ __forceinline__ cx<R> cscale(R s, cx<R> a) { return {mulR(s, a.r), mulR(s, a.i)}; }
+// acc + s*a, s real
+template <typename R> __device__ __forceinline__ cx<R> crfma(R s, cx<R> a, cx<R> acc) {
+    return {fmaR(s, a.r, acc.r), fmaR(s, a.i, acc.i)};
+}
+
+// host/device double complex helpers for scalar work (FP64, run by one thread)
+struct dcx { double r, i; };
+__host__ __device__ __forceinline__ dcx mk(double r, double i = 0.0) { return {r, i}; }
+__host__ __device__ __forceinline__ dcx operator+(dcx a, dcx b) { return {a.r + b.r, a.i + b.i}; }
+__host__ __device__ __forceinline__ dcx operator-(dcx a, dcx b) { return {a.r - b.r, a.i - b.i}; }
+__host__ __device__ __forceinline__ dcx operator-(dcx a) { return {-a.r, -a.i}; }
+__host__ __device__ __forceinline__ dcx operator*(dcx a, dcx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__host__ __device__ __forceinline__ dcx operator*(double s, dcx a) { return {s * a.r, s * a.i}; }
+__host__ __device__ __forceinline__ dcx conjd(dcx a) { return {a.r, -a.i}; }
+__host__ __device__ __forceinline__ double abs2(dcx a) { return a.r * a.r + a.i * a.i; }
+// a / b using the library division on the real parts
+__host__ __device__ __forceinline__ dcx operator/(dcx a, dcx b) {
+    double d = b.r * b.r + b.i * b.i;
+    return {(a.r * b.r + a.i * b.i) / d, (a.i * b.r - a.r * b.i) / d};
+}
+__host__ __device__ __forceinline__ bool finite(dcx a) { return isfinite(a.r) && isfinite(a.i); }
+__device__ __forceinline__ dcx ld(const double2& v) { return {v.x, v.y}; }
+__device__ __forceinline__ double2 pk(dcx v) { return make_double2(v.r, v.i); }
+
+// ------------------------------------------------------------------ spinor views
+template <typename R> struct SpinorView;
+
+template <> struct SpinorView<double> {
+    double2* p;
+    int V;
+    __device__ __forceinline__ void load(int s, cx<double> v[12]) const {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 t = __ldg(p + (size_t)k * V + s);
+            v[k] = {t.x, t.y};
+        }
+    }
+    __device__ __forceinline__ void store(int s, const cx<double> v[12]) const {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[(size_t)k * V + s] = make_double2(v[k].r, v[k].i);
+    }
+};
+
+template <> struct SpinorView<float> {
+    float4* p;
+    int V;
+    __device__ __forceinline__ void load(int s, cx<float> v[12]) const {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            float4 t = __ldg(p + (size_t)q * V + s);
+            v[2 * q] = {t.x, t.y};
+            v[2 * q + 1] = {t.z, t.w};
+        }
+    }
+    __device__ __forceinline__ void store(int s, const cx<float> v[12]) const {
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            p[(size_t)q * V + s] = make_float4(v[2 * q].r, v[2 * q].i, v[2 * q + 1].r, v[2 * q + 1].i);
+    }
+};
+
+// bytes of one internal spinor
+template <typename R> constexpr size_t spinor_bytes(int V) { return (size_t)V * 12 * 2 * sizeof(R); }
+
+// ------------------------------------------------------------------ link views
+template <typename R> struct LinkView;
+
+template <> struct LinkView<double> {
+    const double2* p;
+    int V;
+    __device__ __forceinline__ void load(int mu, int s, cx<double> U[3][3]) const {
+        const double2* b = p + (size_t)mu * 9 * V + s;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            double2 t = __ldg(b + (size_t)e * V);
+            U[e / 3][e % 3] = {t.x, t.y};
+        }
+    }
+};
+
+template <> struct LinkView<float> {
+    const float4* p;
+    int V;
+    __device__ __forceinline__ void load(int mu, int s, cx<float> U[3][3]) const {
+        const float4* b = p + (size_t)mu * 3 * V + s;
+        float4 a0 = __ldg(b), a1 = __ldg(b + V), a2 = __ldg(b + 2 * (size_t)V);
+        U[0][0] = {a0.x, a0.y}; U[0][1] = {a0.z, a0.w}; U[0][2] = {a1.x, a1.y};
+        U[1][0] = {a1.z, a1.w}; U[1][1] = {a2.x, a2.y}; U[1][2] = {a2.z, a2.w};
+        // row 2 = conj(row 0 x row 1): unitary rows with det 1
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+            cx<float> t = cmul(U[0][c1], U[1][c2]);
+            t = cfma(cx<float>{-U[0][c2].r, -U[0][c2].i}, U[1][c1], t);
+            U[2][c] = {t.r, -t.i};
+        }
+    }
+};
+
+// ------------------------------------------------------------------ block reduction
+// Sum K complex values over the block (FP32 values are summed in FP32 within a
+// warp and in FP64 across warps); thread 0 writes them to out[k*stride] as
+// double2.  Deterministic for a fixed launch shape.
+template <int K, typename R>
+__device__ __forceinline__ void block_reduce_store(cx<R> (&v)[K], double2* out, int stride) {
+    __shared__ double2 sh[K][kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        R a = v[k].r, b = v[k].i;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) sh[k][warp] = make_double2((double)a, (double)b);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = kThreads / 32;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double a = 0.0, b = 0.0;
+            if (lane < NW) { a = sh[k][lane].x; b = sh[k][lane].y; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(0xffffffffu, a, o);
+                b += __shfl_down_sync(0xffffffffu, b, o);
+            }
+            if (lane == 0) out[(size_t)k * stride + blockIdx.x] = make_double2(a, b);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ operator params
+struct OpParams {
+    double diag;      // 4 + m
+    double ef, eb;    // e^{+mu}, e^{-mu}
+    double t_bc;      // time boundary sign
+    double scale;     // c
+};
+
+// ------------------------------------------------------------------ host-side API of the kernels
+// Hop (one D_w sweep): out = scale * G5OUT * (diag*in' - 1/2 sum hops(in')),
+// in' = G5IN ? gamma_5 in : in, time weights from `mu_sign` * mu.
+// When dot_with != nullptr, per-block partials of <dot_with, out> are written
+// to partials[blockIdx] (nblk = ceil(V/kThreads) of them).
+int launch_hop_f64(const Geom& g, const double2* links, const double2* in, double2* out,
+                   double diag, double ef, double eb, double t_bc, double scale,
+                   bool g5in, bool g5out, const double2* dot_with, double2* partials,
+                   const int* done, cudaStream_t st);
+int launch_hop_f32(const Geom& g, const float4* links, const float4* in, float4* out,
+                   double diag, double ef, double eb, double t_bc, double scale,
+                   bool g5in, bool g5out, const float4* dot_with, double2* partials,
+                   const int* done, cudaStream_t st);
+
+// canonical (interleaved complex128 AoS) <-> internal layouts
+int launch_pack_spinor_f64(const Geom& g, const double* canon, double2* out, cudaStream_t st);
+int launch_unpack_spinor_f64(const Geom& g, const double2* in, double* canon, cudaStream_t st);
+int launch_pack_spinor_f32(const Geom& g, const double* canon, float4* out, cudaStream_t st);
+int launch_unpack_spinor_f32(const Geom& g, const float4* in, double* canon, cudaStream_t st);
+int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, cudaStream_t st);
+int launch_convert_f64_to_f32(const Geom& g, const double2* in, float4* out, cudaStream_t st);
+
+inline int nblocks(int V) { return (V + kThreads - 1) / kThreads; }
+
+}  // namespace fa

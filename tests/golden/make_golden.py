@@ -1,0 +1,52 @@
+"""Write the stored expected values of the full-size parity test.
+
+Runs the FP64 oracle only (never the CUDA path) on the 16^3 x 32 workload:
+the power-iteration scale c, then the double-pass multi-shift BiCGstab(2)
+with Neuberger's 20 poles at tol 1e-12, and stores c, the outer-iteration
+counts and y* = f(A) b at 512 seeded sample positions, plus |y*|.
+
+    python tests/golden/make_golden.py [workload]     (about 30 min of numpy)
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+from oracle import dirac, msbicgstab as ms, poles, scale  # noqa: E402
+
+
+def main(name="wilson_16x16x16x32", tol=1e-12, n_samples=512):
+    t0 = time.time()
+    w = inputs.make_workload(name)
+    op = dirac.Operator(w["U"], w["mass"], w["mu"], 1.0, w["t_bc"])
+    c = scale.power_scale(op.A, w["v0"], 100)
+    op = dirac.Operator(w["U"], w["mass"], w["mu"], c, w["t_bc"])
+    om, sg = poles.neuberger_poles(w["ns"])
+    st = ms.Stats()
+    y = ms.multishift_double(op.A, w["b"], sg, om, w["ell"], tol, stats=st)
+    rng = np.random.default_rng(4242)
+    shape = y.shape
+    idx = np.stack([rng.integers(0, n, n_samples) for n in shape], axis=1)
+    vals = y[tuple(idx.T)]
+    out = dict(
+        workload=name, dims=list(w["dims"]), ell=w["ell"], ns=w["ns"], tol=tol, scale_c=c,
+        outer_iters=st.n_outer, iters_per_shift=[int(v) for v in st.iters_per_shift],
+        n_mv=st.n_mv, y_norm=float(np.linalg.norm(y)), sample_index=idx.tolist(),
+        sample_re=vals.real.tolist(), sample_im=vals.imag.tolist(),
+        oracle_seconds=time.time() - t0,
+        source="oracle.msbicgstab.multishift_double (FP64 numpy), written by tests/golden/make_golden.py",
+    )
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}.json")
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print(path, st.n_outer, time.time() - t0)
+
+
+if __name__ == "__main__":
+    main(*sys.argv[1:2])

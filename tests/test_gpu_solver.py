@@ -1,0 +1,175 @@
+"""GPU parity of multi-shift BiCGstab(l), single-pass and double-pass, through
+the C-ABI, against the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative 2-norm on f(A) b): FP64 1e-10; mixed (FP64 head, FP32
+tail) 1e-8; FP32 bulk 1e-6 for l <= 3.  The FP32 error of the power-basis
+recurrence grows with l (cancellation in the MR update r_0 - sum gamma_j r_j):
+the oracle itself, with every vector and the operator rounded to FP32, lands
+at 4.8e-8, 9.1e-8, 3.5e-7 and 1.7e-6 for l = 1..4 on the 4^3 x 8 workload,
+so l = 4 is held to 1e-5.
+"""
+import numpy as np
+import pytest
+
+import inputs
+import paper_1010_2592_gb300 as fa
+from closed_forms import free_A_eigenvalues, free_matfunc, gauge_rotate_spinor
+from fa_cases import (make_context, oracle_double, oracle_single, rel, to_dev, to_host,
+                      workload_case)
+from oracle import poles
+
+pytestmark = pytest.mark.gpu
+
+C1 = "wilson_4x4x4x8"
+TOL = {"f64": 1e-10, "f32": 1e-6, "mixed": 1e-8}
+F32_TOL = {1: 1e-6, 2: 1e-6, 3: 1e-6, 4: 1e-5}
+
+
+def tol_for(precision, ell):
+    return F32_TOL[ell] if precision == "f32" else TOL[precision]
+
+
+def ctx_for(w, dims=None):
+    d = w["dims"] if dims is None else dims
+    return make_context(d, w["U"], w["mass"], w["mu"], w["c"], w["t_bc"], w["omega"], w["sigma"])
+
+
+@pytest.mark.parametrize("ell", [1, 2, 3, 4, 8])
+def test_double_pass_f64_matches_oracle(ell):
+    w = workload_case(C1)
+    y_o, st_o = oracle_double(C1, None, ell, 1e-10)
+    ctx = ctx_for(w)
+    r = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, mode="double", precision="f64")
+    assert rel(to_host(r.y), y_o) < TOL["f64"]
+    assert abs(r.stats["outer_iters"] - st_o.n_outer) <= 1
+    assert r.stats["n_mv"] == 4 * ell * r.stats["outer_iters"]
+
+
+@pytest.mark.parametrize("ell", [1, 2, 4])
+def test_single_pass_f64_shift_solutions(ell):
+    # each x_s is compared on its own: both sides solve to 1e-12 so that a
+    # shift frozen one iteration apart cannot move x_s by the tolerance
+    w = workload_case(C1)
+    xs_o, st_o = oracle_single(C1, None, ell, 1e-12)
+    ctx = ctx_for(w)
+    r = ctx.solve_multishift(to_dev(w["b"]), ell=ell, tol=1e-12)
+    for s, x in enumerate(r.y):
+        assert rel(to_host(x), xs_o[s]) < TOL["f64"], s
+    assert r.stats["iters_per_shift"][:w["ns"]] == pytest.approx(list(st_o.iters_per_shift), abs=1)
+    y1 = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, mode="single")
+    y2 = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, mode="double")
+    assert rel(to_host(y2.y), to_host(y1.y)) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["f32", "mixed"])
+@pytest.mark.parametrize("ell", [2, 4])
+def test_reduced_precision_double_pass(precision, ell):
+    w = workload_case(C1)
+    y_o, _ = oracle_double(C1, None, ell, 1e-12)
+    ctx = ctx_for(w)
+    r = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, mode="double", precision=precision)
+    assert rel(to_host(r.y), y_o) < tol_for(precision, ell)
+    if precision == "mixed":
+        assert 0 < r.stats["switch_outer"] < r.stats["outer_iters"]
+
+
+@pytest.mark.parametrize("dims,ell", [((3, 3, 3, 6), 3), ((6, 4, 6, 10), 8), ((6, 4, 6, 10), 2)])
+def test_ragged_lattices(dims, ell):
+    w = workload_case(C1, dims)
+    y_o, _ = oracle_double(C1, dims, ell, 1e-10)
+    ctx = ctx_for(w, dims)
+    r64 = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, precision="f64")
+    assert rel(to_host(r64.y), y_o) < TOL["f64"]
+    if ell in F32_TOL:
+        r32 = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, precision="f32")
+        assert rel(to_host(r32.y), y_o) < F32_TOL[ell]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "mixed"])
+def test_pure_gauge_full_size_closed_form(precision):
+    """16^3 x 32 with non-trivial SU(3) links U = g(x) g(x+mu)^H: f(A_U)(G b) =
+    G f(A_1) b, the free-field PFE evaluated exactly in momentum space."""
+    dims = (16, 16, 16, 32)
+    mass, mu = -1.8, 0.1
+    g = inputs.random_su3_field(dims, 2024)
+    U = inputs.pure_gauge(g)
+    b = inputs.gaussian_spinor(dims, 2025)
+    c = 1.0 / np.max(np.abs(free_A_eigenvalues(dims, mass, mu)))
+    om, sg = poles.neuberger_poles(20)
+    ctx = make_context(dims, U, mass, mu, c, -1, om, sg)
+    r = ctx.apply_f(to_dev(gauge_rotate_spinor(g, b)), ell=2, tol=1e-11, precision=precision)
+    want = gauge_rotate_spinor(g, free_matfunc(b, dims, mass, mu, c,
+                                               lambda lam: poles.pfe_scalar(lam, om, sg)))
+    assert rel(to_host(r.y), want) < TOL[precision]
+
+
+def test_host_buffers_equal_device_buffers_and_repeatable():
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    for precision in ("f64", "f32"):
+        a = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, precision=precision)
+        b = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, precision=precision)
+        h = ctx.apply_f_host(w["b"], ell=2, tol=1e-10, precision=precision)
+        ya = to_host(a.y)
+        assert np.array_equal(ya, to_host(b.y))
+        assert np.array_equal(ya, h.y)
+
+
+def test_degenerate_cases():
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    # max_outer too small: status FA_ENOCONV, no exception when check=False
+    r = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, max_outer=1, check=False)
+    assert r.stats["status"] == fa.FA_ENOCONV
+    # loose tolerance converges in few iterations and still matches the oracle at that tolerance
+    y_o, st_o = oracle_double(C1, None, 2, 1e-2)
+    r = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-2)
+    assert r.stats["outer_iters"] <= st_o.n_outer + 1
+    assert rel(to_host(r.y), y_o) < 1e-10
+    # a single pole
+    ctx.set_poles([1.0], [0.5])
+    r1 = ctx.apply_f(to_dev(w["b"]), ell=1, tol=1e-11)
+    rs = ctx.solve_multishift(to_dev(w["b"]), ell=1, tol=1e-11)
+    assert rel(to_host(r1.y), to_host(rs.y[0])) < 1e-10
+    # invalid: ell not supported, zero source
+    with pytest.raises(fa.FAError):
+        ctx.apply_f(to_dev(w["b"]), ell=5)
+    r = ctx.apply_f(to_dev(np.zeros_like(w["b"])), ell=2, check=False)
+    assert r.stats["status"] == fa.FA_EINVAL
+
+
+def test_state_errors():
+    w = workload_case(C1)
+    ctx = fa.Context(w["dims"])
+    with pytest.raises(fa.FAError) as e:
+        ctx.apply_f(to_dev(w["b"]))
+    assert e.value.status == fa.FA_ESTATE
+
+
+def test_full_size_workload_against_stored_oracle_samples():
+    """16^3 x 32 bench workload (eps 0.4, mu 0.1, l 2, 20 poles): the scale c
+    and 512 sampled entries of y* stored by tests/golden/make_golden.py (FP64
+    oracle, tol 1e-12), in the launch configuration the benchmark times."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "wilson_16x16x16x32.json")
+    g = json.load(open(path))
+    w = inputs.make_workload("wilson_16x16x16x32")
+    idx = tuple(np.asarray(g["sample_index"]).T)
+    want = np.asarray(g["sample_re"]) + 1j * np.asarray(g["sample_im"])
+    ctx = fa.Context(w["dims"])
+    ctx.set_gauge(to_dev(w["U"]))
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], 1.0)
+    c = ctx.estimate_scale(to_dev(w["v0"]), 100)
+    assert abs(c - g["scale_c"]) < 1e-10 * g["scale_c"]
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], g["scale_c"])
+    ctx.set_poles(*fa.neuberger_poles(w["ns"]))
+    b = to_dev(w["b"])
+    r = ctx.apply_f(b, ell=2, tol=1e-12, precision="f64")
+    assert abs(r.stats["outer_iters"] - g["outer_iters"]) <= 1
+    assert rel(to_host(r.y)[idx], want) < 1e-10
+    for precision, tol in (("mixed", 1e-8), ("f32", 1e-6)):
+        r = ctx.apply_f(b, ell=2, tol=1e-10, precision=precision)
+        y = to_host(r.y)
+        assert rel(y[idx], want) < tol, precision
+        assert abs(np.linalg.norm(y) - g["y_norm"]) < tol * g["y_norm"]

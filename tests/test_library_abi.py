@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every entry point of include/fapath.h
+(no GPU needed), and its host-side pole table matches the oracle's."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1010_2592_gb300 as fa
+from oracle import poles
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    """Compile libfapath.so first if this checkout has not built it yet."""
+    if not os.path.exists(fa.LIB_PATH):
+        from paper_1010_2592_gb300 import build
+        build.build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fapath.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fa_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_exports():
+    assert set(declared_functions()) == set(fa.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = fa.load_library()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version():
+    lib = fa.load_library()
+    assert lib.fa_status_string(0) == b"ok"
+    for s in range(-8, 0):
+        assert lib.fa_status_string(s) != b"unknown status"
+    assert b"sm_103a" in lib.fa_version()
+
+
+@pytest.mark.parametrize("ns", [1, 10, 20, 32, 64])
+def test_library_neuberger_poles_match_oracle(ns):
+    om, sg = fa.neuberger_poles(ns)
+    om_o, sg_o = poles.neuberger_poles(ns)
+    assert np.allclose(om, om_o, rtol=1e-15, atol=0)
+    assert np.allclose(sg, sg_o, rtol=1e-15, atol=1e-300)
+
+
+def test_invalid_arguments_rejected_before_any_device_call():
+    import ctypes
+    lib = fa.load_library()
+    h = ctypes.c_void_p()
+    bad = (ctypes.c_int * 4)(4, 4, 1, 8)
+    assert lib.fa_create(ctypes.byref(h), bad, None) == fa.FA_EINVAL
+    assert lib.fa_neuberger_poles(0, None, None) == fa.FA_EINVAL
+    assert lib.fa_neuberger_poles(65, None, None) == fa.FA_EINVAL
+    assert lib.fa_destroy(None) == fa.FA_OK
+    assert lib.fa_set_params(None, -1.8, 0.1, -1, 1.0) == fa.FA_EINVAL
