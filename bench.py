@@ -50,6 +50,12 @@ def parse():
     p.add_argument("--workload", default="wilson_16x16x16x32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--switch-resid", type=float, default=0.0)
+    p.add_argument("--quick", action="store_true",
+                   help="headline solve only at tol 1e-9 (no comparisons, e2e or CPU baseline)")
+    p.add_argument("--hop-only", action="store_true",
+                   help="time D_w sweeps alone (FP32 and FP64) on --dims, for profiling")
+    p.add_argument("--dims", type=int, nargs=4, default=None)
+    p.add_argument("--reps", type=int, default=20)
     return p.parse_args()
 
 
@@ -177,12 +183,54 @@ def config_of(name, w):
             "target_rel_err": TARGET, "l2": "flushed before every timed step (512 MB write)"}
 
 
+# ------------------------------------------------------------------ hop kernels alone
+def run_hop_only(args):
+    """D_w sweeps on the workload's gauge recipe at --dims: CUDA-event mean per
+    launch and GB/s on the algorithmic bytes (FP32: 384 B/site, FP64: 960 B/site)."""
+    import torch
+    import inputs
+    import paper_1010_2592_gb300 as fa
+    w = inputs.make_workload(args.workload, tuple(args.dims) if args.dims else None)
+    dims = w["dims"]
+    V = int(np.prod(dims))
+    ctx = fa.Context(dims)
+    ctx.set_gauge(torch.from_numpy(w["U"]).cuda())
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], 1.0)
+    x = torch.from_numpy(w["b"]).cuda()
+    out = {}
+    for prec, bytes_site in (("f32", 384.0), ("f64", 960.0)):
+        ctx.hop_timing_reset()
+        y = ctx.empty_spinor()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(args.reps):
+            ctx.apply_dw(x, precision=prec, out=y)
+        e.record()
+        torch.cuda.synchronize()
+        ms_call = s.elapsed_time(e) / args.reps
+        out[prec] = {"ms_per_apply_dw_call_incl_pack": ms_call}
+    # the hop kernel alone: time a solve-free loop of hop launches via the solver's instrumentation
+    for prec in ("f32", "f64"):
+        ctx.hop_timing_reset()
+        ctx.set_poles(*fa.neuberger_poles(4))
+        ctx.apply_f(x, ell=1, tol=1e-30, max_outer=max(1, args.reps // 4), mode="double",
+                    precision=prec, hop_timing=True, check=False)
+        ms, n = ctx.hop_timing(prec)
+        bsite = 384.0 if prec == "f32" else 960.0
+        out[prec].update(hop_mean_ms=ms, hop_launches=n, hop_gbs=bsite * V / (ms * 1e-3) / 1e9 if ms else None)
+    print(json.dumps({"mode": "hop-only", "dims": list(dims), "sites": V, **out}), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.hop_only:
+        run_hop_only(args)
         return
 
     import torch
@@ -223,7 +271,13 @@ def main():
         "double_f32": dict(mode="double", precision="f32"),
     }
     chosen = {}
+    if args.quick:
+        variants = {"double_mixed": variants["double_mixed"]}
     for name, kw in variants.items():
+        if args.quick:
+            r = ctx.apply_f(b, ell=ell, tol=1e-9, max_outer=4000, **kw)
+            chosen[name] = (1e-9, err(r.y), r.stats)
+            continue
         pick = None
         for tol in TOLS:
             r = ctx.apply_f(b, ell=ell, tol=tol, max_outer=4000, check=False, **kw)
@@ -261,7 +315,9 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     ctx.hop_timing_reset()
+    torch.cuda.nvtx.range_push("timed")
     head_ms, head_launches, head_res = timed("double_mixed", args.steps, args.warmup, hop=True)
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     torch.cuda.synchronize()
     ms_step = statistics.mean(head_ms)
@@ -274,7 +330,7 @@ def main():
 
     # comparison variants (fewer steps)
     other = {}
-    for name in ("double_f64", "single_f64", "double_f32"):
+    for name in ([] if args.quick else ["double_f64", "single_f64", "double_f32"]):
         k = max(1, min(args.steps, 3))
         lst, _, res = timed(name, k, 1)
         tol, e, _ = chosen[name]
@@ -284,6 +340,15 @@ def main():
     other["double_mixed"] = {"ms": ms_step, "tol": tol_h, "rel_err": e_h,
                              "outer_iters": head_res.stats["outer_iters"],
                              "switch_outer": head_res.stats["switch_outer"], "meets_1e-8": e_h <= TARGET}
+
+    if args.quick:
+        print(json.dumps({"mode": "quick", "ms_per_solve": ms_step, "variant": other["double_mixed"],
+                          "hop_f32_ms": hop32_ms, "hop_f64_ms": hop64_ms,
+                          "hop_f32_gbs": 384.0 * V / (hop32_ms * 1e-3) / 1e9 if hop32_ms else None,
+                          "launches_per_solve": head_launches // max(1, args.steps), "clocks": clk}),
+              flush=True)
+        ctx.close()
+        return
 
     # end to end through the host-buffer entry point: pinned b in, pinned y out
     b_pin = torch.from_numpy(w["b"]).pin_memory()
@@ -320,6 +385,7 @@ def main():
         "config": config_of(args.workload, w),
         "variants": other,
         "speedup_double_mixed_vs_single_f64": other["single_f64"]["ms"] / ms_step,
+        "speedup_double_mixed_vs_double_f64": other["double_f64"]["ms"] / ms_step,
         "roofline": {"kernel": "hop_kernel<float> (one D_w sweep, FP32 12-real links)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
