@@ -125,6 +125,22 @@ int fa_apply_dw(fa_ctx* ctx, const double* in, double* out, int dagger, int prec
 /* out = A in (dagger = 0) or A^H in = A(-mu) in (dagger = 1). */
 int fa_apply_A(fa_ctx* ctx, const double* in, double* out, int dagger, int precision);
 
+/* out = A in (dagger = 0) or A^H in (dagger = 1) in FP64, like fa_apply_A
+ * with precision FA_F64, but without allocating any device memory: for
+ * callers that cannot let the library call cudaMalloc, such as code recording
+ * a CUDA graph under global stream-capture mode (where cudaMalloc is refused)
+ * or code whose device memory is owned by a framework allocator or a fixed
+ * budget.  The paper has no counterpart; this is a library convenience.
+ * The two working spinors live in one static device array sized for at most
+ * 8192 sites (3 MiB, resident on every GPU that loads the library until the
+ * process exits); larger lattices return FA_EINVAL.  The first call on a
+ * device looks up that array's device address (make it before any stream
+ * capture); the context's device must be current.  All calls share the array,
+ * so calls that overlap on one GPU race and must be serialised by the caller.
+ * Stream-ordered on the context's stream; in and out are canonical device
+ * spinors, in != out. */
+int fa_apply_A_noalloc(fa_ctx* ctx, const double* in, double* out, int dagger);
+
 /* Single-pass multi-shift solve (FP64): x_s = (A + sigma_s)^{-1} b for every
  * pole; x_s is an array of ns device spinors (canonical). */
 int fa_solve_multishift(fa_ctx* ctx, const double* b, double* const* x_s,

@@ -32,6 +32,7 @@ EXPORTS = (
     "fa_set_poles", "fa_neuberger_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
     "fa_apply_f", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
     "fa_hop_timing_reset", "fa_status_string", "fa_last_error", "fa_version",
+    "fa_apply_A_noalloc",
 )
 
 
@@ -89,6 +90,7 @@ def load_library(path=LIB_PATH):
         "fa_neuberger_poles": (I, [I, P, P]),
         "fa_apply_dw": (I, [P, P, P, I, I]),
         "fa_apply_A": (I, [P, P, P, I, I]),
+        "fa_apply_A_noalloc": (I, [P, P, P, I]),
         "fa_solve_multishift": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f_host": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
