@@ -115,8 +115,17 @@ __device__ __forceinline__ void hop_bwd(cx<R> acc[12], const SpinorView<R>& in, 
     recon_add<MU, -1>(acc, c);
 }
 
+// FP32: the kernel is bound by load latency (long-scoreboard stalls); the
+// register budget is set for FA_HOP_MINB resident blocks per SM.  Measured on
+// 32^3 x 64: 3 blocks/SM (79 registers) 5.02 TB/s, 4 blocks/SM (64 registers,
+// 132 B spilled) 4.78 TB/s.
+#ifndef FA_HOP_MINB
+#define FA_HOP_MINB 3
+#endif
+template <typename R> constexpr int hop_min_blocks() { return sizeof(R) == 4 ? FA_HOP_MINB : 1; }
+
 template <typename R, bool G5IN, bool G5OUT, bool DOT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, hop_min_blocks<R>())
 hop_kernel(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb,
            R bc, SpinorView<R> dotv, double2* partials, const int* done) {
     if (done != nullptr && *done) return;
