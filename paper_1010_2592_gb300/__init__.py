@@ -22,17 +22,18 @@ LIB_PATH = os.path.join(_HERE, "libfapath.so")
 
 FA_OK, FA_EINVAL, FA_ENOMEM, FA_ECUDA, FA_EBREAKDOWN, FA_ENOCONV, FA_ENONFINITE, FA_ETIMEOUT, \
     FA_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
-SINGLE, DOUBLE = 0, 1
+SINGLE, DOUBLE, PSEUDO = 0, 1, 2
 F64, F32, MIXED = 0, 1, 2
 _PREC = {"f64": F64, "f32": F32, "mixed": MIXED, F64: F64, F32: F32, MIXED: MIXED}
-_MODE = {"single": SINGLE, "double": DOUBLE, SINGLE: SINGLE, DOUBLE: DOUBLE}
+_MODE = {"single": SINGLE, "double": DOUBLE, "pseudo": PSEUDO, SINGLE: SINGLE, DOUBLE: DOUBLE,
+         PSEUDO: PSEUDO}
 
 EXPORTS = (
     "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
     "fa_set_poles", "fa_neuberger_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
     "fa_apply_f", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
     "fa_hop_timing_reset", "fa_status_string", "fa_last_error", "fa_version",
-    "fa_apply_A_noalloc",
+    "fa_apply_A_noalloc", "fa_grad",
 )
 
 
@@ -48,7 +49,8 @@ class FAError(RuntimeError):
 class SolverParams(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int), ("tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("mode", ctypes.c_int), ("precision", ctypes.c_int),
-                ("switch_resid", ctypes.c_double), ("flags", ctypes.c_int)]
+                ("switch_resid", ctypes.c_double), ("flags", ctypes.c_int),
+                ("store_gb", ctypes.c_double)]
 
 
 class SolverStats(ctypes.Structure):
@@ -56,7 +58,8 @@ class SolverStats(ctypes.Structure):
                 ("switch_outer", ctypes.c_int), ("ns", ctypes.c_int),
                 ("iters_per_shift", ctypes.c_int * 64), ("resid_recurrence", ctypes.c_double),
                 ("n_mv", ctypes.c_longlong), ("n_dot", ctypes.c_longlong),
-                ("n_launch", ctypes.c_longlong), ("t_pass1_ms", ctypes.c_double),
+                ("n_launch", ctypes.c_longlong), ("stored_outer", ctypes.c_int),
+                ("t_pass1_ms", ctypes.c_double),
                 ("t_sweep_ms", ctypes.c_double), ("t_pass2_ms", ctypes.c_double)]
 
     def as_dict(self):
@@ -64,7 +67,8 @@ class SolverStats(ctypes.Structure):
                     switch_outer=self.switch_outer,
                     iters_per_shift=list(self.iters_per_shift[:self.ns]),
                     resid_recurrence=self.resid_recurrence, n_mv=self.n_mv, n_dot=self.n_dot,
-                    n_launch=self.n_launch, t_pass1_ms=self.t_pass1_ms,
+                    n_launch=self.n_launch, stored_outer=self.stored_outer,
+                    t_pass1_ms=self.t_pass1_ms,
                     t_sweep_ms=self.t_sweep_ms, t_pass2_ms=self.t_pass2_ms)
 
 
@@ -94,6 +98,8 @@ def load_library(path=LIB_PATH):
         "fa_solve_multishift": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f_host": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+        "fa_grad": (I, [P, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P,
+                        ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_sync": (I, [P]),
         "fa_launch_count": (LL, [P]),
         "fa_hop_timing": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
@@ -225,9 +231,10 @@ class Context:
     # -- solvers
     @staticmethod
     def params(ell=2, tol=1e-10, max_outer=2000, mode="double", precision="f64",
-               switch_resid=0.0, timing=False, hop_timing=False):
+               switch_resid=0.0, timing=False, hop_timing=False, store_gb=0.0):
         return SolverParams(int(ell), float(tol), int(max_outer), _MODE[mode], _PREC[precision],
-                            float(switch_resid), (1 if timing else 0) | (2 if hop_timing else 0))
+                            float(switch_resid), (1 if timing else 0) | (2 if hop_timing else 0),
+                            float(store_gb))
 
     def apply_f(self, b, out=None, check=True, **kw):
         b = _spinor_check(b, self.spinor_shape, "b")
@@ -262,6 +269,21 @@ class Context:
         _check(self.lib.fa_solve_multishift(self.h, b.data_ptr(), ptrs, ctypes.byref(p),
                                             ctypes.byref(st)), "fa_solve_multishift")
         return Result(xs, st.as_dict())
+
+    def grad(self, b, eta, ell=2, tol=1e-12, max_outer=4000, want_db=True):
+        """(L, dL/dU, dL/dmu, dL/db, stats) for L = Re <eta, f(A) b> (single-pass FP64 solves)."""
+        torch = _torch()
+        b = _spinor_check(b, self.spinor_shape, "b")
+        eta = _spinor_check(eta, self.spinor_shape, "eta")
+        gU = torch.empty(self.gauge_shape, dtype=torch.complex128, device="cuda")
+        gb = self.empty_spinor() if want_db else None
+        dmu, L = ctypes.c_double(), ctypes.c_double()
+        p = self.params(ell=ell, tol=tol, max_outer=max_outer, mode="single", precision="f64")
+        st = SolverStats()
+        _check(self.lib.fa_grad(self.h, b.data_ptr(), eta.data_ptr(), gU.data_ptr(), ctypes.byref(dmu),
+                                ctypes.byref(L), gb.data_ptr() if want_db else None, ctypes.byref(p),
+                                ctypes.byref(st)), "fa_grad")
+        return L.value, gU, dmu.value, gb, st.as_dict()
 
     def sync(self):
         _check(self.lib.fa_sync(self.h), "fa_sync")

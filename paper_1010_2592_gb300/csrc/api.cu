@@ -239,6 +239,12 @@ int fa_apply_f_host(fa_ctx* c, const double* b_host, double* y_host, const fa_so
     return FA_OK;
 }
 
+int fa_grad(fa_ctx* c, const double* b, const double* eta, double* dLdU, double* dLdmu, double* L, double* dLdb,
+            const fa_solver_params* p, fa_solver_stats* stats) {
+    if (!c) return FA_EINVAL;
+    return grad(c, b, eta, dLdU, dLdmu, L, dLdb, p, stats);
+}
+
 int fa_sync(fa_ctx* c) {
     if (!c) return FA_EINVAL;
     CUDA_OR(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "fa_sync");

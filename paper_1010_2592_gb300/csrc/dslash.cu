@@ -214,6 +214,108 @@ int launch_hop_f32(const Geom& g, const float4* links, const float4* in, float4*
                                partials, done, st);
 }
 
+// ------------------------------------------------------------------ link force (adjoint)
+// For the bilinears B_p = <a_p, D_w(mu) b_p> (p = 1, 2) the variation under a
+// link change dU_nu(x) is sum_ij [dU_ij M_ij + conj(dU_ji) K_ij] with
+//   M_ij = -1/2 f+ sum_s conj(a_si(x))      ((1 - g_nu) b(x+nu))_sj   (forward hop at x)
+//   K_ij = -1/2 f- sum_s conj(a_si(x+nu))   ((1 + g_nu) b(x))_sj      (backward hop at x+nu)
+// so Re dB = Re tr(G^H dU) with G = conj(M) + K^T.  The kernel adds
+// w * (G_1 + G_2) to the canonical gradient array and writes per-block partials
+// of w * (dB_1/dmu + dB_2/dmu), dB/dmu = sum M_ij U_ij - sum K_ij conj(U_ji) on
+// time links.  a_1 enters as gamma_5 a_1 when G5A1 is set.
+template <int MU>
+__device__ __forceinline__ void force_dir(int s, int nb, double fp, double fm, const LinkView<double>& U,
+                                          const SpinorView<double> a[2], const SpinorView<double> b[2],
+                                          double w, double2* Gout, cx<double>& dmu) {
+    cx<double> Gm[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Gm[i][j] = czero<double>();
+    cx<double> Uc[3][3];
+    if (MU == 3) U.load(3, s, Uc);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        cx<double> ax[12], an[12], bx[12], bn[12], Pb[12], Qb[12], h[6];
+        a[p].load(s, ax);
+        a[p].load(nb, an);
+        b[p].load(s, bx);
+        b[p].load(nb, bn);
+        if (p == 0) {
+#pragma unroll
+            for (int k = 6; k < 12; ++k) { ax[k] = {-ax[k].r, -ax[k].i}; an[k] = {-an[k].r, -an[k].i}; }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) { Pb[k] = czero<double>(); Qb[k] = czero<double>(); }
+        project<MU, +1>(bn, h);
+        recon_add<MU, +1>(Pb, h);
+        project<MU, -1>(bx, h);
+        recon_add<MU, -1>(Qb, h);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                cx<double> m = czero<double>(), k = czero<double>();
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) {
+                    m = cjfma(ax[3 * sp + i], Pb[3 * sp + j], m);
+                    k = cjfma(an[3 * sp + i], Qb[3 * sp + j], k);
+                }
+                m = cscale(-0.5 * fp, m);
+                k = cscale(-0.5 * fm, k);
+                // G_ij += conj(M_ij); G_ji += K_ij
+                Gm[i][j] = cadd(Gm[i][j], cx<double>{m.r, -m.i});
+                Gm[j][i] = cadd(Gm[j][i], k);
+                if (MU == 3) {
+                    dmu = cfma(m, Uc[i][j], dmu);                                     // + M_ij U_ij
+                    dmu = cfma(cx<double>{-k.r, -k.i}, cx<double>{Uc[j][i].r, -Uc[j][i].i}, dmu);  // - K_ij conj(U_ji)
+                }
+            }
+    }
+    double2* g = Gout + ((size_t)s * 4 + MU) * 9;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        double2 v = g[e];
+        v.x = __fma_rn(w, Gm[e / 3][e % 3].r, v.x);
+        v.y = __fma_rn(w, Gm[e / 3][e % 3].i, v.y);
+        g[e] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_force(Geom g, LinkView<double> U, SpinorView<double> a1, SpinorView<double> b1, SpinorView<double> a2,
+        SpinorView<double> b2, double2* G, double w, double ef, double eb, double bc, double2* partials) {
+    const int s = blockIdx.x * kThreads + threadIdx.x;
+    cx<double> dm[1] = {czero<double>()};
+    if (s < g.V) {
+        const int X = g.X, Y = g.Y, Z = g.Z, T = g.T;
+        const int x = s % X, r1 = s / X, y = r1 % Y, r2 = r1 / Y, z = r2 % Z, t = r2 / Z;
+        const int sY = X, sZ = X * Y, sT = X * Y * Z;
+        const SpinorView<double> a[2] = {a1, a2};
+        const SpinorView<double> b[2] = {b1, b2};
+        force_dir<0>(s, (x == X - 1) ? s - (X - 1) : s + 1, 1.0, 1.0, U, a, b, w, G, dm[0]);
+        force_dir<1>(s, (y == Y - 1) ? s - (Y - 1) * sY : s + sY, 1.0, 1.0, U, a, b, w, G, dm[0]);
+        force_dir<2>(s, (z == Z - 1) ? s - (Z - 1) * sZ : s + sZ, 1.0, 1.0, U, a, b, w, G, dm[0]);
+        // forward hop at x crosses the boundary from t = T-1; so does the backward hop at x + t_hat
+        const double fp = (t == T - 1) ? ef * bc : ef;
+        const double fm = (t == T - 1) ? eb * bc : eb;
+        force_dir<3>(s, (t == T - 1) ? s - (T - 1) * sT : s + sT, fp, fm, U, a, b, w, G, dm[0]);
+        dm[0] = cscale(w, dm[0]);
+    }
+    block_reduce_store<1, double>(dm, partials, 0);
+}
+
+int launch_force(const Geom& g, const double2* links, const double2* a1, const double2* b1, const double2* a2,
+                 const double2* b2, double* G_canon, double w, double ef, double eb, double t_bc,
+                 double2* partials, cudaStream_t st) {
+    LinkView<double> U{links, g.V};
+    SpinorView<double> va1{const_cast<double2*>(a1), g.V}, vb1{const_cast<double2*>(b1), g.V};
+    SpinorView<double> va2{const_cast<double2*>(a2), g.V}, vb2{const_cast<double2*>(b2), g.V};
+    k_force<<<nblocks(g.V), kThreads, 0, st>>>(g, U, va1, vb1, va2, vb2, (double2*)G_canon, w, ef, eb, t_bc,
+                                                partials);
+    return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA;
+}
+
 // ------------------------------------------------------------------ layout conversions
 // canonical spinor: double [V][12][2]; element (s, k) at 2*(12 s + k)
 __global__ void pack_f64_kernel(int V, const double2* __restrict__ canon, double2* __restrict__ out) {

@@ -68,6 +68,9 @@ struct fa_ctx {
     fa::DevBuf y64;                      // accumulated result (FP64 internal)
     fa::DevBuf xs64, us64;               // single-pass shift vectors
     fa::DevBuf bhost_dev, yhost_dev;     // canonical staging for fa_apply_f_host
+    fa::DevBuf gx, gpart;                // gradient: saved x_s, force partials
+    fa::DevBuf store64, store32;         // pseudo-double-pass occurrence stores
+    fa::DevBuf snap64, snap32;           // seed state at the first unstored outer iteration
     void* pinned = nullptr;              // host copy of DevState
     size_t pinned_bytes = 0;
 
@@ -90,4 +93,6 @@ int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, b
 int solve(fa_ctx* c, const double* b_canon, double* y_canon, double* const* xs_canon,
           const fa_solver_params* p, fa_solver_stats* stats);
 int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out);
+int grad(fa_ctx* c, const double* b, const double* eta, double* dLdU, double* dLdmu, double* L, double* dLdb,
+         const fa_solver_params* p, fa_solver_stats* stats);
 }  // namespace fa

@@ -228,6 +228,12 @@ int launch_unpack_spinor_f32(const Geom& g, const float4* in, double* canon, cud
 int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, cudaStream_t st);
 int launch_convert_f64_to_f32(const Geom& g, const double2* in, float4* out, cudaStream_t st);
 
+// adjoint link force of <a1, D b1> + <a2, D b2> (a1 enters as gamma_5 a1), scaled by w,
+// added to the canonical gradient G; per-block partials of the mu-derivative.
+int launch_force(const Geom& g, const double2* links, const double2* a1, const double2* b1, const double2* a2,
+                 const double2* b2, double* G_canon, double w, double ef, double eb, double t_bc,
+                 double2* partials, cudaStream_t st);
+
 inline int nblocks(int V) { return (V + kThreads - 1) / kThreads; }
 
 }  // namespace fa

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <vector>
 
 #include "fa_context.h"
 #include "solver_kernels.cuh"
@@ -187,7 +188,8 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
 // kernels.  Pass 2 (pass2 = true): the same vector kernels with the recorded
 // scalars, no inner products, and y accumulation.  single: shift vectors too.
 template <typename R, int L>
-static int enqueue_outer(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool pass2, bool single, bool head) {
+static int enqueue_outer(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool pass2, bool single, bool head,
+                         void* store_v) {
     using T = typename Ch<R>::T;
     constexpr bool F64 = sizeof(R) == 8;
     T* r = F64 ? (T*)c->r64.p : (T*)c->r32.p;
@@ -195,6 +197,7 @@ static int enqueue_outer(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool p
     T* rt = F64 ? (T*)c->rt64.p : (T*)c->rt32.p;
     T* tmp = F64 ? (T*)c->tmp64.p : (T*)c->tmp32.p;
     const size_t vs = F64 ? Lo.vs64 : Lo.vs32;
+    T* store = static_cast<T*>(store_v);
     const int* done = pass2 ? nullptr : &d.st->done;
     double2* part = c->partials.as<double2>();
     double2* y = c->y64.as<double2>();
@@ -226,13 +229,15 @@ static int enqueue_outer(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool p
             FA_LAUNCHED(c, "k_sc_alpha");
         }
         if (pass2) {
-            k_update_r<R, true, false><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, y, nullptr, nullptr, svs, done);
+            k_update_r<R, true, false><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, y, nullptr, nullptr, svs, nullptr,
+                                                                done);
         } else if (single) {
             if constexpr (F64)
-                k_update_r<R, false, true><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, nullptr, xs, us, svs, done);
+                k_update_r<R, false, true><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, nullptr, xs, us, svs, nullptr,
+                                                                    done);
         } else {
             k_update_r<R, false, false><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, nullptr, nullptr, nullptr, svs,
-                                                                 done);
+                                                                 store, done);
         }
         FA_LAUNCHED(c, "k_update_r");
         FA_TRY(A(r + j * vs, r + (j + 1) * vs, (!pass2 && j < L - 1) ? rt : nullptr));
@@ -245,14 +250,15 @@ static int enqueue_outer(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool p
         FA_LAUNCHED(c, "k_sc_mr");
     }
     if (pass2) {
-        k_mr<R, L, true, false, false><<<rg, kThreads, 0, st>>>(d, r, u, rt, vs, y, nullptr, nullptr, svs, part,
-                                                                 done);
+        k_mr<R, L, true, false, false><<<rg, kThreads, 0, st>>>(d, r, u, rt, vs, y, nullptr, nullptr, svs, nullptr,
+                                                                 part, done);
     } else if (single) {
         if constexpr (F64)
-            k_mr<R, L, false, true, true><<<rg, kThreads, 0, st>>>(d, r, u, rt, vs, nullptr, xs, us, svs, part, done);
+            k_mr<R, L, false, true, true><<<rg, kThreads, 0, st>>>(d, r, u, rt, vs, nullptr, xs, us, svs, nullptr,
+                                                                   part, done);
     } else {
         k_mr<R, L, false, false, true><<<rg, kThreads, 0, st>>>(d, r, u, rt, vs, nullptr, nullptr, nullptr, svs,
-                                                                 part, done);
+                                                                 store, part, done);
     }
     FA_LAUNCHED(c, "k_mr");
     if (!pass2) {
@@ -267,19 +273,19 @@ static int enqueue_outer(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool p
 
 template <int L>
 static int enqueue_outer_p(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool f64, bool pass2, bool single,
-                           bool head) {
-    return f64 ? enqueue_outer<double, L>(c, Lo, d, pass2, single, head)
-               : enqueue_outer<float, L>(c, Lo, d, pass2, single, head);
+                           bool head, void* store) {
+    return f64 ? enqueue_outer<double, L>(c, Lo, d, pass2, single, head, store)
+               : enqueue_outer<float, L>(c, Lo, d, pass2, single, head, store);
 }
 
 static int enqueue_outer_any(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool f64, bool pass2, bool single,
-                             bool head) {
+                             bool head, void* store = nullptr) {
     switch (Lo.L) {
-        case 1: return enqueue_outer_p<1>(c, Lo, d, f64, pass2, single, head);
-        case 2: return enqueue_outer_p<2>(c, Lo, d, f64, pass2, single, head);
-        case 3: return enqueue_outer_p<3>(c, Lo, d, f64, pass2, single, head);
-        case 4: return enqueue_outer_p<4>(c, Lo, d, f64, pass2, single, head);
-        case 8: return enqueue_outer_p<8>(c, Lo, d, f64, pass2, single, head);
+        case 1: return enqueue_outer_p<1>(c, Lo, d, f64, pass2, single, head, store);
+        case 2: return enqueue_outer_p<2>(c, Lo, d, f64, pass2, single, head, store);
+        case 3: return enqueue_outer_p<3>(c, Lo, d, f64, pass2, single, head, store);
+        case 4: return enqueue_outer_p<4>(c, Lo, d, f64, pass2, single, head, store);
+        case 8: return enqueue_outer_p<8>(c, Lo, d, f64, pass2, single, head, store);
         default: return FA_EINVAL;
     }
 }
@@ -339,7 +345,8 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
     if (!(L == 1 || L == 2 || L == 3 || L == 4 || L == 8)) return FA_EINVAL;
     if (!(p->tol > 0.0) || p->max_outer < 1 || p->max_outer > 1000000) return FA_EINVAL;
     const bool single = p->mode == FA_SINGLE;
-    if (!single && p->mode != FA_DOUBLE) return FA_EINVAL;
+    const bool pseudo = p->mode == FA_PSEUDO;
+    if (!single && !pseudo && p->mode != FA_DOUBLE) return FA_EINVAL;
     const int prec = p->precision;
     if (prec != FA_F64 && prec != FA_F32 && prec != FA_MIXED) return FA_EINVAL;
     if (single && prec != FA_F64) return FA_EINVAL;
@@ -378,6 +385,59 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
         FA_CUDA(cudaMemsetAsync(c->xs64.p, 0, (size_t)Lo.ns * 12 * Lo.V * sizeof(double2), st), "zero xs");
         FA_CUDA(cudaMemsetAsync(c->us64.p, 0, (size_t)Lo.ns * (L + 1) * 12 * Lo.V * sizeof(double2), st), "zero us");
     }
+    // ---- pseudo-double-pass store (Sec. 2, option 2): pass 1 keeps the seed-vector
+    // occurrences of a contiguous prefix [0, K) of outer iterations, as many as
+    // the budget holds (FP64 slots while in FP64, FP32 slots after the switch)
+    const int NC = nc_slots(L);
+    const size_t s64 = Lo.vs64 * sizeof(double2), s32 = Lo.vs32 * sizeof(float4);
+    const size_t per64 = (size_t)NC * s64, per32 = (size_t)NC * s32;
+    long long cap64 = 0, cap32 = 0;
+    if (pseudo) {
+        size_t fb = 0, tb = 0;
+        FA_CUDA(cudaMemGetInfo(&fb, &tb), "memory info");
+        const double held = (double)c->store64.bytes + (double)c->store32.bytes;
+        double budget = p->store_gb > 0.0 ? p->store_gb * 1e9 : std::min(0.25 * ((double)fb + held), 16e9);
+        budget = std::min(budget, 0.9 * ((double)fb + held));
+        if (prec == FA_F64) {
+            cap64 = (long long)std::min<double>(Lo.max_outer, budget / per64);
+        } else if (prec == FA_F32) {
+            cap32 = (long long)std::min<double>(Lo.max_outer, budget / per32);
+        } else {
+            cap64 = (long long)std::min<double>(std::min(Lo.max_outer, 64), 0.4 * budget / per64);
+            cap32 = (long long)std::min<double>(Lo.max_outer, (budget - (double)cap64 * per64) / per32);
+        }
+        cap64 = std::max(0LL, cap64);
+        cap32 = std::max(0LL, cap32);
+        if (cap64 > 0) FA_CUDA(c->store64.ensure((size_t)cap64 * per64), "alloc occurrence store");
+        if (cap32 > 0) FA_CUDA(c->store32.ensure((size_t)cap32 * per32), "alloc occurrence store");
+        if (Lo.need64) FA_CUDA(c->snap64.ensure(3 * s64), "alloc snapshot");
+        if (Lo.need32) FA_CUDA(c->snap32.ensure(3 * s32), "alloc snapshot");
+    }
+    int K = pseudo ? -1 : 0;            // first outer iteration not stored (-1: still storing)
+    int m0_32 = prec == FA_F32 ? 0 : -1;  // first FP32 outer iteration
+    bool snap_f64 = true;
+    int snap_rc = FA_OK;
+    // r_0, u_0, rt of the current precision -> snapshot (pass 2 restarts from it)
+    auto snapshot = [&](bool f64now) {
+        snap_f64 = f64now;
+        const size_t sb = f64now ? s64 : s32;
+        char* dst = f64now ? c->snap64.as<char>() : c->snap32.as<char>();
+        void* src[3] = {f64now ? c->r64.p : c->r32.p, f64now ? c->u64.p : c->u32.p, f64now ? c->rt64.p : c->rt32.p};
+        for (int k = 0; k < 3; ++k)
+            if (cudaMemcpyAsync(dst + k * sb, src[k], sb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                snap_rc = cuda_fail(cudaGetLastError(), "snapshot");
+    };
+    auto store_for = [&](int m, bool f64now) -> void* {
+        if (K >= 0) return nullptr;
+        void* ptr = nullptr;
+        if (f64now && m < cap64) ptr = c->store64.as<char>() + (size_t)m * per64;
+        if (!f64now && m0_32 >= 0 && m - m0_32 < cap32) ptr = c->store32.as<char>() + (size_t)(m - m0_32) * per32;
+        if (!ptr) {
+            K = m;
+            snapshot(f64now);
+        }
+        return ptr;
+    };
     if (timing) cudaEventRecord(ev[0], st);
 
     // ---- pass 1
@@ -400,13 +460,14 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
     int enq = 0;
     // FP64 head of FA_MIXED: one outer iteration at a time until the switch
     while (head && enq < Lo.max_outer) {
-        FA_TRY(enqueue_outer_any(c, Lo, d, true, false, single, true));
+        FA_TRY(enqueue_outer_any(c, Lo, d, true, false, single, true, store_for(enq, true)));
         ++enq;
         FA_TRY(read_state(c, &hs));
         if (hs.done) break;
         if (hs.switch_req) {
             FA_TRY(switch_to_f32(c, Lo));
             switch_outer = hs.m;
+            m0_32 = switch_outer;
             head = false;
             f64 = false;
         }
@@ -423,7 +484,7 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
         int rc = FA_OK;
         while (!stop && enq < Lo.max_outer) {
             for (int i = 0; i < chunk && enq < Lo.max_outer; ++i, ++enq) {
-                rc = enqueue_outer_any(c, Lo, d, f64, false, single, false);
+                rc = enqueue_outer_any(c, Lo, d, f64, false, single, false, store_for(enq, f64));
                 if (rc != FA_OK) break;
             }
             if (rc != FA_OK) break;
@@ -445,7 +506,10 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
     int status = hs.status;
     if (status == FA_OK && !hs.done) status = FA_ENOCONV;
 
-    // ---- backward sweep and pass 2 (double-pass)
+    FA_TRY(snap_rc);
+    const int Kst = pseudo ? (K < 0 ? M : std::min(K, M)) : 0;   // stored prefix
+
+    // ---- backward sweep, gather of the stored prefix, pass 2 for the rest
     if (status == FA_OK && !single) {
         FA_CUDA(cudaMemsetAsync(c->cs.p, 0, (size_t)Lo.ns * Lo.max_outer * nc_slots(L) * sizeof(double2), st),
                 "zero sweep");
@@ -454,16 +518,43 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
         k_coef_reduce<<<(n + 255) / 256, 256, 0, st>>>(d, M);
         FA_LAUNCHED(c, "k_coef_reduce");
         if (timing) cudaEventRecord(ev[2], st);
-        bool p2f64 = prec != FA_F32;
-        FA_TRY(load_source(c, Lo, b, p2f64));
-        k_set_m<<<1, 1, 0, st>>>(d, 0);
-        FA_LAUNCHED(c, "k_set_m");
-        for (int m = 0; m < M; ++m) {
-            if (prec == FA_MIXED && m == switch_outer) {
-                FA_TRY(switch_to_f32(c, Lo));
-                p2f64 = false;
+        if (Kst > 0) {
+            // FP64 slots cover [0, end64), FP32 slots [m0_32, Kst)
+            const int end64 = prec == FA_F64 ? Kst : (prec == FA_MIXED ? (m0_32 >= 0 ? std::min(Kst, m0_32) : Kst) : 0);
+            if (end64 > 0) {
+                k_gather<double><<<Lo.nblk, kThreads, 0, st>>>(d, c->store64.as<double2>(), Lo.vs64, 0, end64, 0,
+                                                                c->y64.as<double2>());
+                FA_LAUNCHED(c, "k_gather<double>");
             }
-            FA_TRY(enqueue_outer_any(c, Lo, d, p2f64, true, false, false));
+            if (m0_32 >= 0 && Kst > m0_32) {
+                k_gather<float><<<Lo.nblk, kThreads, 0, st>>>(d, c->store32.as<float4>(), Lo.vs32, m0_32, Kst, m0_32,
+                                                               c->y64.as<double2>());
+                FA_LAUNCHED(c, "k_gather<float>");
+            }
+        }
+        const int mstart = Kst;
+        if (mstart < M) {
+            bool p2f64 = prec == FA_F64 || (prec == FA_MIXED && (switch_outer < 0 || mstart < switch_outer));
+            if (mstart == 0) {
+                FA_TRY(load_source(c, Lo, b, p2f64));
+            } else {
+                // restart from the snapshot taken before outer iteration K
+                if (snap_f64 != p2f64) return FA_ESTATE;
+                const size_t sb = p2f64 ? s64 : s32;
+                const char* src = p2f64 ? c->snap64.as<char>() : c->snap32.as<char>();
+                void* dst[3] = {p2f64 ? c->r64.p : c->r32.p, p2f64 ? c->u64.p : c->u32.p, p2f64 ? c->rt64.p : c->rt32.p};
+                for (int k = 0; k < 3; ++k)
+                    FA_CUDA(cudaMemcpyAsync(dst[k], src + k * sb, sb, cudaMemcpyDeviceToDevice, st), "restore");
+            }
+            k_set_m<<<1, 1, 0, st>>>(d, mstart);
+            FA_LAUNCHED(c, "k_set_m");
+            for (int m = mstart; m < M; ++m) {
+                if (p2f64 && prec == FA_MIXED && m == switch_outer) {
+                    FA_TRY(switch_to_f32(c, Lo));
+                    p2f64 = false;
+                }
+                FA_TRY(enqueue_outer_any(c, Lo, d, p2f64, true, false, false));
+            }
         }
         if (timing) cudaEventRecord(ev[3], st);
         FA_TRY(launch_unpack_spinor_f64(c->g, c->y64.as<double2>(), y_canon, st));
@@ -499,7 +590,8 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
         for (int s = 0; s < Lo.ns; ++s) stats->iters_per_shift[s] = iters[s];
         stats->resid_recurrence = std::sqrt(hs.rnorm2 / hs.bnorm2);
         const long long per = 2LL * L * M;
-        stats->n_mv = single ? per : 2 * per;
+        stats->n_mv = single ? per : per + 2LL * L * (M - Kst);
+        stats->stored_outer = Kst;
         stats->n_dot = (long long)M * (L * (L + 7) / 2 + 1);
         stats->n_launch = c->launches;
         if (timing) {
@@ -515,6 +607,82 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
     if (timing)
         for (auto& e : ev) cudaEventDestroy(e);
     return status;
+}
+
+// ------------------------------------------------------------------ adjoint gradient
+// L = Re <eta, y>, y = sum_s omega_s x_s, x_s = (A + sigma_s)^{-1} b.
+// dL = -Re sum_s omega_s <lambda_s, dA x_s>, lambda_s = (A^H + sigma_s)^{-1} eta with
+// A^H = A(-mu); <lambda, dA x> = c [<g5 lambda, dD (g5 D x)> + <D(-mu) lambda, dD x>]
+// (c held fixed).  x_s and lambda_s come from two single-pass FP64 solves (the
+// forward solution is recomputed here rather than stored by the forward call).
+int grad(fa_ctx* c, const double* b, const double* eta, double* dLdU, double* dLdmu, double* L, double* dLdb,
+         const fa_solver_params* p, fa_solver_stats* stats) {
+    if (!c->have_gauge || !c->have_params || !c->have_poles) return FA_ESTATE;
+    if (!b || !eta || !dLdU || !dLdmu || !L || !p) return FA_EINVAL;
+    fa_solver_params ps = *p;
+    ps.mode = FA_SINGLE;
+    ps.precision = FA_F64;
+    fa_solver_stats st1{}, st2{};
+    FA_TRY(solve(c, b, nullptr, nullptr, &ps, &st1));
+    const int V = c->g.V, ns = c->ns;
+    const size_t vs = (size_t)12 * V;
+    const size_t sb = vs * sizeof(double2);
+    cudaStream_t st = c->stream;
+    FA_CUDA(c->gx.ensure(ns * sb), "alloc gradient");
+    FA_CUDA(cudaMemcpyAsync(c->gx.p, c->xs64.p, ns * sb, cudaMemcpyDeviceToDevice, st), "save x_s");
+    const double mu0 = c->mu;
+    c->mu = -mu0;
+    const int rc2 = solve(c, eta, nullptr, nullptr, &ps, &st2);
+    c->mu = mu0;
+    FA_TRY(rc2);
+    const int nb = nblocks(V), rg = red_grid_for(V);
+    FA_CUDA(c->io64a.ensure(sb), "alloc");
+    FA_CUDA(c->io64b.ensure(sb), "alloc");
+    FA_CUDA(c->gpart.ensure(((size_t)ns * nb + 2 * (size_t)rg) * sizeof(double2)), "alloc");
+    FA_CUDA(cudaMemsetAsync(dLdU, 0, (size_t)V * 72 * sizeof(double), st), "zero dL/dU");
+    double2* gxs = c->gx.as<double2>();
+    double2* lam = c->xs64.as<double2>();
+    double2* t1 = c->io64a.as<double2>();
+    double2* t2 = c->io64b.as<double2>();
+    double2* part = c->gpart.as<double2>();
+    for (int s = 0; s < ns; ++s) {
+        const double2* xs = gxs + s * vs;
+        const double2* ls = lam + s * vs;
+        FA_TRY(hop_f64(c, xs, t1, 1.0, false, true, false, nullptr, nullptr, nullptr));   // g5 D x
+        FA_TRY(hop_f64(c, ls, t2, 1.0, false, false, true, nullptr, nullptr, nullptr));   // D(-mu) lambda
+        FA_TRY(launch_force(c->g, c->links64.as<double2>(), ls, t1, t2, xs, dLdU, -c->scale_c * c->omega[s],
+                            std::exp(c->mu), std::exp(-c->mu), c->t_bc, part + (size_t)s * nb, st));
+        c->launches++;
+    }
+    // y = sum omega x, L = Re <eta, y>; dL/db = sum omega lambda
+    // the pole weights omega were uploaded by the solves (shift buffer, after sigma)
+    const double* om_dev = reinterpret_cast<const double*>(c->shiftbuf.as<char>() + kMaxShifts * sizeof(double));
+    k_combine<<<(12 * V + kThreads - 1) / kThreads, kThreads, 0, st>>>(V, ns, om_dev, gxs, vs, c->y64.as<double2>());
+    FA_LAUNCHED(c, "k_combine");
+    FA_TRY(launch_pack_spinor_f64(c->g, eta, t1, st));
+    k_dot2<double><<<rg, kThreads, 0, st>>>(V, t1, c->y64.as<double2>(), part + (size_t)ns * nb);
+    FA_LAUNCHED(c, "k_dot2");
+    if (dLdb) {
+        k_combine<<<(12 * V + kThreads - 1) / kThreads, kThreads, 0, st>>>(V, ns, om_dev, lam, vs, t2);
+        FA_LAUNCHED(c, "k_combine");
+        FA_TRY(launch_unpack_spinor_f64(c->g, t2, dLdb, st));
+    }
+    std::vector<double2> h((size_t)ns * nb + 2 * (size_t)rg);
+    FA_CUDA(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, st), "read partials");
+    FA_CUDA(cudaStreamSynchronize(st), "sync gradient");
+    double dmu = 0.0, lre = 0.0;
+    for (size_t k = 0; k < (size_t)ns * nb; ++k) dmu += h[k].x;
+    for (int k = 0; k < rg; ++k) lre += h[(size_t)ns * nb + k].x;
+    *dLdmu = dmu;
+    *L = lre;
+    if (stats) {
+        *stats = st1;
+        stats->n_mv += st2.n_mv;
+        stats->n_dot += st2.n_dot;
+        stats->outer_iters = st1.outer_iters + st2.outer_iters;
+        stats->n_launch = c->launches;
+    }
+    return FA_OK;
 }
 
 // ------------------------------------------------------------------ power iteration for the scale c

@@ -144,7 +144,7 @@ k_update_u(SolverDev d, int j, const typename Ch<R>::T* r, typename Ch<R>::T* u,
 template <typename R, bool ACC, bool SHIFTS>
 __global__ void __launch_bounds__(kThreads)
 k_update_r(SolverDev d, int j, typename Ch<R>::T* r, const typename Ch<R>::T* u, size_t vs, double2* y,
-           double2* xs, double2* us, size_t svs, const int* done) {
+           double2* xs, double2* us, size_t svs, typename Ch<R>::T* store, const int* done) {
     if (done != nullptr && *done) return;
     const int s = blockIdx.x * kThreads + threadIdx.x;
     if (s >= d.V) return;
@@ -160,6 +160,7 @@ k_update_r(SolverDev d, int j, typename Ch<R>::T* r, const typename Ch<R>::T* u,
         for (int i = 0; i <= j; ++i) {
             typename Ch<R>::T* ri = r + i * vs;
             Ch<R> a = Ch<R>::ld(ri, q, d.V, s), b = Ch<R>::ld(u + (i + 1) * vs, q, d.V, s);
+            if (store != nullptr) a.stv(store + slot_old(j, i) * vs, q, d.V, s);
             if (ACC) {
                 const cx<R> c = tocx<R>(cf[slot_old(j, i)]);
 #pragma unroll
@@ -251,7 +252,8 @@ k_gram(SolverDev d, const typename Ch<R>::T* r, size_t vs, double2* partials, co
 template <typename R, int L, bool ACC, bool SHIFTS, bool DOT>
 __global__ void __launch_bounds__(kThreads)
 k_mr(SolverDev d, typename Ch<R>::T* r, typename Ch<R>::T* u, const typename Ch<R>::T* rt, size_t vs,
-     double2* y, double2* xs, double2* us, size_t svs, double2* partials, const int* done) {
+     double2* y, double2* xs, double2* us, size_t svs, typename Ch<R>::T* store, double2* partials,
+     const int* done) {
     if (done != nullptr && *done) return;
     const int m = d.st->m;
     cx<R> ng[L + 1];
@@ -266,6 +268,10 @@ k_mr(SolverDev d, typename Ch<R>::T* r, typename Ch<R>::T* u, const typename Ch<
             Ch<R> rv[L + 1];
 #pragma unroll
             for (int i = 0; i <= L; ++i) rv[i] = Ch<R>::ld(r + i * vs, q, d.V, s);
+            if (store != nullptr) {
+#pragma unroll
+                for (int k = 0; k < L; ++k) rv[k].stv(store + slot_mr(L, k) * vs, q, d.V, s);
+            }
             if (ACC) {
                 cx<R> t[Ch<R>::W];
 #pragma unroll
@@ -603,6 +609,53 @@ __global__ void k_sc_conv(SolverDev d, const double2* part, int nblk, int head) 
     const dcx beta = ld(S->alpha) * rtr / rho0;
     S->rho0 = pk(rtr);
     d.rec_beta[(m + 1) * d.L] = pk(beta);
+}
+
+// ------------------------------------------------------------------ pseudo-double-pass gather
+// y += sum_{m in [m_begin, m_end)} sum_k coef[m][k] v(m, k), the stored seed-vector
+// occurrences of pass 1 (store slot (m - m0) * NC + k).  Terms are summed in R
+// in groups of four, each group added to y in FP64.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_gather(SolverDev d, const typename Ch<R>::T* store, size_t vs, int m_begin, int m_end, int m0, double2* y) {
+    const int s = blockIdx.x * kThreads + threadIdx.x;
+    if (s >= d.V) return;
+    const int NC = nc_slots(d.L);
+    const int n = (m_end - m_begin) * NC;
+    const double2* cf = d.coef + (size_t)m_begin * NC;
+    const typename Ch<R>::T* base = store + (size_t)(m_begin - m0) * NC * vs;
+    double acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = 0.0;
+    for (int k0 = 0; k0 < n; k0 += 4) {
+        cx<R> t[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) t[k] = czero<R>();
+        const int k1 = min(n, k0 + 4);
+        for (int k = k0; k < k1; ++k) {
+            const cx<R> c = tocx<R>(cf[k]);
+            const typename Ch<R>::T* v = base + (size_t)k * vs;
+#pragma unroll
+            for (int q = 0; q < Ch<R>::N; ++q) {
+                Ch<R> a = Ch<R>::ld(v, q, d.V, s);
+#pragma unroll
+                for (int w = 0; w < Ch<R>::W; ++w) t[q * Ch<R>::W + w] = cfma(c, a.c[w], t[q * Ch<R>::W + w]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            acc[2 * k] = __dadd_rn(acc[2 * k], (double)t[k].r);
+            acc[2 * k + 1] = __dadd_rn(acc[2 * k + 1], (double)t[k].i);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2* p = y + (size_t)k * d.V + s;
+        double2 a = *p;
+        a.x = __dadd_rn(a.x, acc[2 * k]);
+        a.y = __dadd_rn(a.y, acc[2 * k + 1]);
+        *p = a;
+    }
 }
 
 // pass 2: advance the outer-iteration counter

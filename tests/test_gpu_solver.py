@@ -173,3 +173,38 @@ def test_full_size_workload_against_stored_oracle_samples():
         y = to_host(r.y)
         assert rel(y[idx], want) < tol, precision
         assert abs(np.linalg.norm(y) - g["y_norm"]) < tol * g["y_norm"]
+
+
+@pytest.mark.parametrize("precision,ell", [("f64", 2), ("f64", 4), ("f32", 2), ("mixed", 2), ("mixed", 4)])
+def test_pseudo_double_pass(precision, ell):
+    """Sec. 2 option 2: occurrences stored in pass 1, no regeneration."""
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    b = to_dev(w["b"])
+    if precision == "f64":
+        y_o, _ = oracle_double(C1, None, ell, 1e-10)
+        ref = ctx.apply_f(b, ell=ell, tol=1e-10, mode="double", precision="f64")
+    else:
+        y_o, _ = oracle_double(C1, None, ell, 1e-12)
+    r = ctx.apply_f(b, ell=ell, tol=1e-10, mode="pseudo", precision=precision)
+    assert r.stats["stored_outer"] == r.stats["outer_iters"]
+    assert r.stats["n_mv"] == 2 * ell * r.stats["outer_iters"]
+    assert rel(to_host(r.y), y_o) < tol_for(precision, ell)
+    if precision == "f64":
+        assert rel(to_host(r.y), to_host(ref.y)) < 1e-13
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_pseudo_double_pass_partial_store(precision):
+    """A budget for only a few outer iterations: the rest is regenerated by a
+    pass 2 that restarts from the snapshot taken before the first unstored one."""
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    b = to_dev(w["b"])
+    y_o, _ = oracle_double(C1, None, 2, 1e-12 if precision == "mixed" else 1e-10)
+    per64 = 5 * 512 * 192 / 1e9                     # one outer iteration of FP64 occurrences
+    r = ctx.apply_f(b, ell=2, tol=1e-10, mode="pseudo", precision=precision, store_gb=6.5 * per64)
+    M, K = r.stats["outer_iters"], r.stats["stored_outer"]
+    assert 0 < K < M
+    assert r.stats["n_mv"] == 2 * 2 * M + 2 * 2 * (M - K)   # pass 1 + regenerated remainder
+    assert rel(to_host(r.y), y_o) < TOL[precision]
