@@ -161,3 +161,21 @@ def make_workload(name, dims=None):
     v0 = gaussian_spinor(w["dims"], seeds["power"])
     w.update(U=U, b=b, v0=v0, seeds=seeds)
     return w
+
+
+def make_batched_workload(name="wilson_batched_72"):
+    """The batched workload: for lattice k (seeded 100*gauge_seed + k) its gauge
+    field, mu_k ~ U[mu_range] (seeded by gauge_seed + 5), the power-iteration
+    start vector and its 12 spin-colour point sources at the origin."""
+    w = dict(WORKLOADS[name])
+    gs = 1000 + w["index"]
+    mus = np.random.default_rng(gs + 5).uniform(*w["mu_range"], size=len(w["lattices"]))
+    lattices = []
+    for k, dims in enumerate(w["lattices"]):
+        seed = 100 * gs + k
+        lattices.append(dict(
+            dims=tuple(dims), mu=float(mus[k]), U=su3_exp_gauge(dims, w["eps"], seed),
+            v0=gaussian_spinor(dims, seed + 50),
+            sources=[point_source(dims, s, c) for s in range(4) for c in range(3)]))
+    w["lattice_systems"] = lattices
+    return w

@@ -33,7 +33,7 @@ EXPORTS = (
     "fa_set_poles", "fa_neuberger_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
     "fa_apply_f", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
     "fa_hop_timing_reset", "fa_status_string", "fa_last_error", "fa_version",
-    "fa_apply_A_noalloc", "fa_grad",
+    "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
 )
 
 
@@ -50,7 +50,7 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int), ("tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("switch_resid", ctypes.c_double), ("flags", ctypes.c_int),
-                ("store_gb", ctypes.c_double)]
+                ("store_gb", ctypes.c_double), ("reliable_every", ctypes.c_int)]
 
 
 class SolverStats(ctypes.Structure):
@@ -88,6 +88,7 @@ def load_library(path=LIB_PATH):
         "fa_create": (I, [ctypes.POINTER(P), ctypes.POINTER(I), P]),
         "fa_destroy": (I, [P]),
         "fa_set_gauge": (I, [P, P, I]),
+        "fa_share_gauge": (I, [P, P]),
         "fa_set_params": (I, [P, D, D, I, D]),
         "fa_estimate_scale": (I, [P, P, I, ctypes.POINTER(D)]),
         "fa_set_poles": (I, [P, I, P, P]),
@@ -98,6 +99,7 @@ def load_library(path=LIB_PATH):
         "fa_solve_multishift": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f_host": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+        "fa_apply_f_batched": (I, [P, I, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_grad": (I, [P, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P,
                         ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_sync": (I, [P]),
@@ -127,6 +129,25 @@ def neuberger_poles(ns):
     sg = np.empty(ns, dtype=np.float64)
     _check(lib.fa_neuberger_poles(ns, om.ctypes.data, sg.ctypes.data), "fa_neuberger_poles")
     return om, sg
+
+
+def apply_f_batched(contexts, sources, check=True, **kw):
+    """y_i = f(A_i) b_i for a list of contexts (systems of equal lattice shape
+    share every kernel launch).  Returns (list of y, list of stats dicts)."""
+    lib = load_library()
+    n = len(contexts)
+    for c, b in zip(contexts, sources):
+        _spinor_check(b, c.spinor_shape, "b")
+    ys = [c.empty_spinor() for c in contexts]
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in contexts])
+    bs = (ctypes.c_void_p * n)(*[b.data_ptr() for b in sources])
+    yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+    p = Context.params(**kw)
+    st = (SolverStats * n)()
+    rc = lib.fa_apply_f_batched(hs, n, bs, yp, ctypes.byref(p), st)
+    if check:
+        _check(rc, "fa_apply_f_batched")
+    return ys, [s.as_dict() for s in st]
 
 
 def _torch():
@@ -196,6 +217,11 @@ class Context:
                 raise ValueError("gauge field: contiguous complex128 CUDA tensor expected")
             _check(self.lib.fa_set_gauge(self.h, U.data_ptr(), 1), "fa_set_gauge")
 
+    def share_gauge(self, owner):
+        """Use owner's packed gauge field (same lattice) instead of a copy."""
+        _check(self.lib.fa_share_gauge(self.h, owner.h), "fa_share_gauge")
+        self._gauge_owner = owner      # keep the owner alive
+
     def set_params(self, mass, mu, t_bc=-1, scale=1.0):
         _check(self.lib.fa_set_params(self.h, float(mass), float(mu), int(t_bc), float(scale)),
                "fa_set_params")
@@ -231,10 +257,12 @@ class Context:
     # -- solvers
     @staticmethod
     def params(ell=2, tol=1e-10, max_outer=2000, mode="double", precision="f64",
-               switch_resid=0.0, timing=False, hop_timing=False, store_gb=0.0):
+               switch_resid=0.0, timing=False, hop_timing=False, store_gb=0.0, graph=False,
+               reliable_every=0):
         return SolverParams(int(ell), float(tol), int(max_outer), _MODE[mode], _PREC[precision],
-                            float(switch_resid), (1 if timing else 0) | (2 if hop_timing else 0),
-                            float(store_gb))
+                            float(switch_resid),
+                            (1 if timing else 0) | (2 if hop_timing else 0) | (4 if graph else 0),
+                            float(store_gb), int(reliable_every))
 
     def apply_f(self, b, out=None, check=True, **kw):
         b = _spinor_check(b, self.spinor_shape, "b")

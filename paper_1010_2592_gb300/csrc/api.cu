@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "fa_context.h"
 
@@ -90,6 +91,8 @@ int fa_destroy(fa_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     for (cudaEvent_t e : c->hop_ev) cudaEventDestroy(e);
+    for (auto& g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (c->pinned) cudaFreeHost(c->pinned);
     delete c;
     return FA_OK;
@@ -111,6 +114,20 @@ int fa_set_gauge(fa_ctx* c, const double* U, int on_device) {
     TRY(launch_pack_links(c->g, src, c->links64.as<double2>(), c->links32.as<float4>(), c->stream));
     c->launches++;
     CUDA_OR(cudaStreamSynchronize(c->stream), "fa_set_gauge: sync");
+    c->links_owner = nullptr;
+    c->have_gauge = true;
+    return FA_OK;
+}
+
+int fa_share_gauge(fa_ctx* c, const fa_ctx* owner) {
+    if (!c || !owner || c == owner || owner->links_owner) return FA_EINVAL;
+    if (!owner->have_gauge) return FA_ESTATE;
+    if (c->g.X != owner->g.X || c->g.Y != owner->g.Y || c->g.Z != owner->g.Z || c->g.T != owner->g.T ||
+        c->device != owner->device)
+        return FA_EINVAL;
+    c->links64.release();
+    c->links32.release();
+    c->links_owner = owner;
     c->have_gauge = true;
     return FA_OK;
 }
@@ -223,6 +240,46 @@ int fa_solve_multishift(fa_ctx* c, const double* b, double* const* x_s, const fa
 int fa_apply_f(fa_ctx* c, const double* b, double* y, const fa_solver_params* p, fa_solver_stats* stats) {
     if (!c || !b || !y || !p || b == y) return FA_EINVAL;
     return solve(c, b, y, nullptr, p, stats);
+}
+
+int fa_apply_f_batched(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y,
+                       const fa_solver_params* p, fa_solver_stats* stats) {
+    if (!ctxs || !b || !y || !p || n < 1 || n > 4096) return FA_EINVAL;
+    // group the systems by lattice shape; each group shares every launch
+    std::vector<int> done(n, 0);
+    int rc_all = FA_OK;
+    for (int i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        if (!ctxs[i]) return FA_EINVAL;
+        std::vector<int> idx;
+        for (int k = i; k < n; ++k) {
+            if (!ctxs[k]) return FA_EINVAL;
+            const Geom& a = ctxs[i]->g;
+            const Geom& g = ctxs[k]->g;
+            if (!done[k] && a.X == g.X && a.Y == g.Y && a.Z == g.Z && a.T == g.T) {
+                idx.push_back(k);
+                done[k] = 1;
+            }
+        }
+        std::vector<fa_ctx*> cs;
+        std::vector<const double*> bs;
+        std::vector<double*> ys;
+        for (int k : idx) {
+            cs.push_back(ctxs[k]);
+            bs.push_back(b[k]);
+            ys.push_back(y[k]);
+        }
+        std::vector<fa_solver_stats> st(idx.size());
+        // an explicit store budget covers the whole call: each group gets its share
+        fa_solver_params pg = *p;
+        if (pg.store_gb > 0.0) pg.store_gb = p->store_gb * (double)idx.size() / (double)n;
+        const int rc = solve_batch(cs.data(), (int)cs.size(), bs.data(), ys.data(), nullptr, &pg, st.data());
+        if (stats)
+            for (size_t j = 0; j < idx.size(); ++j) stats[idx[j]] = st[j];
+        if (rc != FA_OK && rc_all == FA_OK) rc_all = rc;
+        if (rc == FA_EINVAL || rc == FA_ECUDA || rc == FA_ESTATE || rc == FA_ENOMEM) return rc;
+    }
+    return rc_all;
 }
 
 int fa_apply_f_host(fa_ctx* c, const double* b_host, double* y_host, const fa_solver_params* p,

@@ -36,6 +36,15 @@ struct DevBuf {
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
+// an instantiated outer iteration, keyed by what its launches depend on
+struct GraphEntry {
+    int key, L;
+    void* dev;
+    int n, V;
+    cudaGraphExec_t exec;
+    long long kernels;
+};
+
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 
@@ -46,8 +55,9 @@ struct fa_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
 
-    // gauge field
+    // gauge field (own packed copy, or the packed copy of another context)
     fa::DevBuf links64, links32;
+    const fa_ctx* links_owner = nullptr;
     bool have_gauge = false;
     // operator parameters
     double mass = 0.0, mu = 0.0, t_bc = -1.0, scale_c = 1.0;
@@ -71,6 +81,9 @@ struct fa_ctx {
     fa::DevBuf gx, gpart;                // gradient: saved x_s, force partials
     fa::DevBuf store64, store32;         // pseudo-double-pass occurrence stores
     fa::DevBuf snap64, snap32;           // seed state at the first unstored outer iteration
+    fa::DevBuf descbuf, flagbuf;         // batch descriptors and done flags (first context of a batch)
+    fa::DevBuf xrel, brel, snapx;        // reliable updates: seed solution, packed source, snapshot
+    std::vector<fa::GraphEntry> graphs;  // captured outer iterations
     void* pinned = nullptr;              // host copy of DevState
     size_t pinned_bytes = 0;
 
@@ -85,6 +98,12 @@ struct fa_ctx {
 };
 
 namespace fa {
+inline const double2* links64_of(const fa_ctx* c) {
+    return c->links_owner ? c->links_owner->links64.as<double2>() : c->links64.as<double2>();
+}
+inline const float4* links32_of(const fa_ctx* c) {
+    return c->links_owner ? c->links_owner->links32.as<float4>() : c->links32.as<float4>();
+}
 // operator application on internal layouts (used by the C-ABI and the solver)
 int hop_f64(fa_ctx* c, const double2* in, double2* out, double scale, bool g5in, bool g5out, bool dagger_mu,
             const double2* dot_with, double2* partials, const int* done);
@@ -92,6 +111,8 @@ int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, b
             const float4* dot_with, double2* partials, const int* done);
 int solve(fa_ctx* c, const double* b_canon, double* y_canon, double* const* xs_canon,
           const fa_solver_params* p, fa_solver_stats* stats);
+int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y_canon,
+                double* const* xs_canon, const fa_solver_params* p, fa_solver_stats* stats);
 int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out);
 int grad(fa_ctx* c, const double* b, const double* eta, double* dLdU, double* dLdmu, double* L, double* dLdb,
          const fa_solver_params* p, fa_solver_stats* stats);

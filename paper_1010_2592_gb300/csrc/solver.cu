@@ -65,7 +65,7 @@ int hop_f64(fa_ctx* c, const double2* in, double2* out, double scale, bool g5in,
             const double2* dot_with, double2* partials, const int* done) {
     const double mu = dagger_mu ? -c->mu : c->mu;
     hop_timing_begin(c, 0);
-    int rc = launch_hop_f64(c->g, c->links64.as<double2>(), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu),
+    int rc = launch_hop_f64(c->g, links64_of(c), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu),
                             c->t_bc, scale, g5in, g5out, dot_with, partials, done, c->stream);
     hop_timing_end(c);
     c->launches++;
@@ -77,7 +77,7 @@ int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, b
             const float4* dot_with, double2* partials, const int* done) {
     const double mu = dagger_mu ? -c->mu : c->mu;
     hop_timing_begin(c, 1);
-    int rc = launch_hop_f32(c->g, c->links32.as<float4>(), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu),
+    int rc = launch_hop_f32(c->g, links32_of(c), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu),
                             c->t_bc, scale, g5in, g5out, dot_with, partials, done, c->stream);
     hop_timing_end(c);
     c->launches++;
@@ -91,12 +91,6 @@ static int apply_A_64(fa_ctx* c, const double2* in, double2* out, double2* tmp, 
     FA_TRY(hop_f64(c, in, tmp, 1.0, false, true, false, nullptr, nullptr, done));
     return hop_f64(c, tmp, out, scale, false, true, false, dot_with, partials, done);
 }
-static int apply_A_32(fa_ctx* c, const float4* in, float4* out, float4* tmp, const float4* dot_with,
-                      double2* partials, const int* done, double scale) {
-    FA_TRY(hop_f32(c, in, tmp, 1.0, false, true, false, nullptr, nullptr, done));
-    return hop_f32(c, tmp, out, scale, false, true, false, dot_with, partials, done);
-}
-
 // ------------------------------------------------------------------ small FP64 kernels
 __global__ void k_sc_invnorm(const double2* part, int nblk, double* out) {
     const dcx v = reduce_partials(part, 1, nblk);
@@ -124,7 +118,7 @@ struct Layout {
 static int red_grid_for(int V) { return std::min(nblocks(V), 8 * 152); }
 
 static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
-    const int V = Lo.V, L = Lo.L, ns = Lo.ns, MO = Lo.max_outer;
+    const int V = Lo.V, L = Lo.L, ns = c->ns, MO = Lo.max_outer;
     const size_t s64 = (size_t)12 * V * sizeof(double2), s32 = (size_t)6 * V * sizeof(float4);
     FA_CUDA(c->partials.ensure((size_t)std::max(Lo.nblk, Lo.red_grid) * Lo.part_slots * sizeof(double2)),
             "alloc partials");
@@ -153,8 +147,8 @@ static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
         FA_CUDA(c->us64.ensure((size_t)ns * (L + 1) * s64), "alloc shift directions");
     }
     if (!c->pinned) {
-        FA_CUDA(cudaMallocHost(&c->pinned, 2 * sizeof(DevState)), "alloc pinned");
-        c->pinned_bytes = 2 * sizeof(DevState);
+        FA_CUDA(cudaMallocHost(&c->pinned, 4096), "alloc pinned");
+        c->pinned_bytes = 4096;
     }
     return FA_OK;
 }
@@ -162,10 +156,18 @@ static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
 static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     SolverDev d{};
     d.st = c->state.as<DevState>();
-    d.ns = Lo.ns;
+    d.ns = c->ns;
     d.L = Lo.L;
     d.max_outer = Lo.max_outer;
     d.V = Lo.V;
+    d.g = c->g;
+    d.links64 = links64_of(c);
+    d.links32 = links32_of(c);
+    d.diag = 4.0 + c->mass;
+    d.ef = std::exp(c->mu);
+    d.eb = std::exp(-c->mu);
+    d.bc = c->t_bc;
+    d.scale = c->scale_c;
     char* sb = c->shiftbuf.as<char>();
     d.sigma = reinterpret_cast<const double*>(sb);
     d.omega = reinterpret_cast<const double*>(sb + kMaxShifts * sizeof(double));
@@ -180,167 +182,300 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     d.prec = c->prec.as<double2>();
     d.coef = c->coef.as<double2>();
     d.cs = Lo.single ? nullptr : c->cs.as<double2>();
+    d.r64 = c->r64.as<double2>();
+    d.u64 = c->u64.as<double2>();
+    d.rt64 = c->rt64.as<double2>();
+    d.tmp64 = c->tmp64.as<double2>();
+    d.r32 = c->r32.as<float4>();
+    d.u32 = c->u32.as<float4>();
+    d.rt32 = c->rt32.as<float4>();
+    d.tmp32 = c->tmp32.as<float4>();
+    d.y = c->y64.as<double2>();
+    d.xs = Lo.single ? c->xs64.as<double2>() : nullptr;
+    d.us = Lo.single ? c->us64.as<double2>() : nullptr;
+    d.store64 = nullptr;
+    d.store32 = nullptr;
+    d.cap64 = d.cap32 = 0;
+    d.m0_32 = -1;
+    d.nblk = Lo.nblk;
+    d.red_grid = Lo.red_grid;
+    d.part = c->partials.as<double2>();
+    d.x64 = nullptr;
+    d.b64 = nullptr;
     return d;
+}
+
+// A batch: systems of one lattice shape whose kernels share each launch.
+struct Batch {
+    fa_ctx* c0 = nullptr;                 // owner of the stream and the descriptor array
+    std::vector<fa_ctx*> sys;
+    std::vector<SolverDev> host;          // host copy of the descriptors
+    SolverDev* dev = nullptr;             // device array
+    int* flags = nullptr;                 // device done flags
+    Layout Lo{};
+    int n = 0;
+    bool use_graph = false;
+};
+
+static int upload(Batch& B) {
+    FA_CUDA(cudaMemcpyAsync(B.dev, B.host.data(), B.n * sizeof(SolverDev), cudaMemcpyHostToDevice, B.c0->stream),
+            "upload descriptors");
+    return FA_OK;
 }
 
 // ------------------------------------------------------------------ one outer iteration
 // Pass 1 (pass2 = false): seed recurrence with inner products and the scalar
 // kernels.  Pass 2 (pass2 = true): the same vector kernels with the recorded
 // scalars, no inner products, and y accumulation.  single: shift vectors too.
+// Each launch covers the whole batch (grid.y = systems, or one block per
+// system for the scalar kernels).
 template <typename R, int L>
-static int enqueue_outer(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool pass2, bool single, bool head,
-                         void* store_v) {
-    using T = typename Ch<R>::T;
-    constexpr bool F64 = sizeof(R) == 8;
-    T* r = F64 ? (T*)c->r64.p : (T*)c->r32.p;
-    T* u = F64 ? (T*)c->u64.p : (T*)c->u32.p;
-    T* rt = F64 ? (T*)c->rt64.p : (T*)c->rt32.p;
-    T* tmp = F64 ? (T*)c->tmp64.p : (T*)c->tmp32.p;
-    const size_t vs = F64 ? Lo.vs64 : Lo.vs32;
-    T* store = static_cast<T*>(store_v);
-    const int* done = pass2 ? nullptr : &d.st->done;
-    double2* part = c->partials.as<double2>();
-    double2* y = c->y64.as<double2>();
-    double2* xs = single ? c->xs64.as<double2>() : nullptr;
-    double2* us = single ? c->us64.as<double2>() : nullptr;
-    const size_t svs = Lo.vs64;
-    const int nb = Lo.nblk;
+static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reliable) {
+    fa_ctx* c = B.c0;
+    const int n = B.n, nb = B.Lo.nblk, rg = B.Lo.red_grid;
+    const int p2 = pass2 ? 1 : 0;
+    const dim3 gs(nb, n), gr(rg, n);
+    const SolverDev* ds = B.dev;
     cudaStream_t st = c->stream;
-
-    auto A = [&](const T* in, T* out, const T* dotw) -> int {
-        if constexpr (F64)
-            return apply_A_64(c, (const double2*)in, (double2*)out, (double2*)tmp, (const double2*)dotw, part, done,
-                              c->scale_c);
-        else
-            return apply_A_32(c, (const float4*)in, (float4*)out, (float4*)tmp, (const float4*)dotw, part, done,
-                              c->scale_c);
+    constexpr int kind = sizeof(R) == 8 ? 0 : 1;
+    const bool timing = c->hop_timing && !B.use_graph;
+    // One system: the stand-alone hop kernel with its pointers as kernel
+    // parameters (no descriptor fields held in registers).  A batch: the
+    // descriptor-driven hop, one launch for all systems.
+    using T = typename Ch<R>::T;
+    const SolverDev& h0 = B.host[0];
+    auto vsel = [&](int sel, int j) -> T* {
+        T* base = sizeof(R) == 8 ? (T*)(sel == 0 ? (void*)h0.u64 : sel == 1 ? (void*)h0.r64 : (void*)h0.tmp64)
+                                 : (T*)(sel == 0 ? (void*)h0.u32 : sel == 1 ? (void*)h0.r32 : (void*)h0.tmp32);
+        return base + (size_t)j * (size_t)Ch<R>::N * h0.V;
     };
-
+    auto hop = [&](int in_sel, int in_j, int out_sel, int out_j, int second, bool dot) -> int {
+        if (timing) hop_timing_begin(c, kind);
+        if (n == 1) {
+            const T* rt = sizeof(R) == 8 ? (const T*)(const void*)h0.rt64 : (const T*)(const void*)h0.rt32;
+            const int* done = pass2 ? nullptr : &h0.st->done;
+            const double sc = second ? h0.scale : 1.0;
+            int rc;
+            if constexpr (sizeof(R) == 8)
+                rc = launch_hop_f64(h0.g, h0.links64, vsel(in_sel, in_j), vsel(out_sel, out_j), h0.diag, h0.ef, h0.eb,
+                                    h0.bc, sc, false, true, dot ? rt : nullptr, h0.part, done, st);
+            else
+                rc = launch_hop_f32(h0.g, h0.links32, vsel(in_sel, in_j), vsel(out_sel, out_j), h0.diag, h0.ef, h0.eb,
+                                    h0.bc, sc, false, true, dot ? rt : nullptr, h0.part, done, st);
+            if (timing) hop_timing_end(c);
+            c->launches++;
+            if (rc != FA_OK) return cuda_fail(cudaGetLastError(), "hop_kernel");
+            return FA_OK;
+        }
+        if (dot) k_hop_sys<R, true><<<gs, kThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2);
+        else k_hop_sys<R, false><<<gs, kThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2);
+        if (timing) hop_timing_end(c);
+        FA_LAUNCHED(c, "k_hop_sys");
+        return FA_OK;
+    };
     for (int j = 0; j < L; ++j) {
         if (!pass2 && j > 0) {
-            k_sc_beta<<<1, kScalarThreads, 0, st>>>(d, j, part, nb);
+            k_sc_beta<<<n, kScalarThreads, 0, st>>>(ds, j, nb);
             FA_LAUNCHED(c, "k_sc_beta");
         }
-        k_update_u<R><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, done);
+        k_update_u<R><<<gs, kThreads, 0, st>>>(ds, j, p2);
         FA_LAUNCHED(c, "k_update_u");
-        FA_TRY(A(u + j * vs, u + (j + 1) * vs, pass2 ? nullptr : rt));
+        FA_TRY(hop(0, j, 2, 0, 0, false));          // tmp = g5 D u_j
+        FA_TRY(hop(2, 0, 0, j + 1, 1, !pass2));     // u_{j+1} = c g5 D tmp, <rt, u_{j+1}>
         if (!pass2) {
-            k_sc_alpha<<<1, kScalarThreads, 0, st>>>(d, j, part, nb);
+            k_sc_alpha<<<n, kScalarThreads, 0, st>>>(ds, j, nb);
             FA_LAUNCHED(c, "k_sc_alpha");
         }
         if (pass2) {
-            k_update_r<R, true, false><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, y, nullptr, nullptr, svs, nullptr,
-                                                                done);
+            k_update_r<R, true, false><<<gs, kThreads, 0, st>>>(ds, j, p2);
         } else if (single) {
-            if constexpr (F64)
-                k_update_r<R, false, true><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, nullptr, xs, us, svs, nullptr,
-                                                                    done);
+            if constexpr (sizeof(R) == 8) k_update_r<R, false, true><<<gs, kThreads, 0, st>>>(ds, j, p2);
         } else {
-            k_update_r<R, false, false><<<nb, kThreads, 0, st>>>(d, j, r, u, vs, nullptr, nullptr, nullptr, svs,
-                                                                 store, done);
+            k_update_r<R, false, false><<<gs, kThreads, 0, st>>>(ds, j, p2);
         }
         FA_LAUNCHED(c, "k_update_r");
-        FA_TRY(A(r + j * vs, r + (j + 1) * vs, (!pass2 && j < L - 1) ? rt : nullptr));
+        FA_TRY(hop(1, j, 2, 0, 0, false));                      // tmp = g5 D r_j
+        FA_TRY(hop(2, 0, 1, j + 1, 1, !pass2 && j < L - 1));    // r_{j+1} = c g5 D tmp
     }
-    const int rg = Lo.red_grid;
     if (!pass2) {
-        k_gram<R, L><<<rg, kThreads, 0, st>>>(d, r, vs, part, done);
+        k_gram<R, L><<<gr, kThreads, 0, st>>>(ds);
         FA_LAUNCHED(c, "k_gram");
-        k_sc_mr<L><<<1, kScalarThreads, 0, st>>>(d, part, rg);
+        k_sc_mr<L><<<n, kScalarThreads, 0, st>>>(ds, rg);
         FA_LAUNCHED(c, "k_sc_mr");
     }
     if (pass2) {
-        k_mr<R, L, true, false, false><<<rg, kThreads, 0, st>>>(d, r, u, rt, vs, y, nullptr, nullptr, svs, nullptr,
-                                                                 part, done);
+        k_mr<R, L, true, false, false><<<gr, kThreads, 0, st>>>(ds, p2);
     } else if (single) {
-        if constexpr (F64)
-            k_mr<R, L, false, true, true><<<rg, kThreads, 0, st>>>(d, r, u, rt, vs, nullptr, xs, us, svs, nullptr,
-                                                                   part, done);
+        if constexpr (sizeof(R) == 8) k_mr<R, L, false, true, true><<<gr, kThreads, 0, st>>>(ds, p2);
     } else {
-        k_mr<R, L, false, false, true><<<rg, kThreads, 0, st>>>(d, r, u, rt, vs, nullptr, nullptr, nullptr, svs,
-                                                                 store, part, done);
+        k_mr<R, L, false, false, true><<<gr, kThreads, 0, st>>>(ds, p2);
     }
     FA_LAUNCHED(c, "k_mr");
+    if (reliable) {
+        // r_0 <- b - A x in FP64 (one system): A x through two FP64 hops, then the
+        // replacement and fresh <rt, r_0>, |r_0|^2 for the convergence kernel
+        double2* t1 = c->io64a.as<double2>();
+        double2* t2 = c->io64b.as<double2>();
+        const int* done = pass2 ? nullptr : &h0.st->done;
+        int rc = launch_hop_f64(h0.g, h0.links64, h0.x64, t1, h0.diag, h0.ef, h0.eb, h0.bc, 1.0, false, true,
+                                nullptr, nullptr, done, st);
+        if (rc == FA_OK)
+            rc = launch_hop_f64(h0.g, h0.links64, t1, t2, h0.diag, h0.ef, h0.eb, h0.bc, h0.scale, false, true,
+                                nullptr, nullptr, done, st);
+        c->launches += 2;
+        if (rc != FA_OK) return cuda_fail(cudaGetLastError(), "reliable update");
+        k_reliable<R><<<gr, kThreads, 0, st>>>(ds, t2, p2);
+        FA_LAUNCHED(c, "k_reliable");
+    }
     if (!pass2) {
-        k_sc_conv<<<1, kScalarThreads, 0, st>>>(d, part, rg, head ? 1 : 0);
+        k_sc_conv<<<n, kScalarThreads, 0, st>>>(ds, rg, head ? 1 : 0);
         FA_LAUNCHED(c, "k_sc_conv");
     } else {
-        k_advance<<<1, 1, 0, st>>>(d);
+        k_advance<<<n, 1, 0, st>>>(ds);
         FA_LAUNCHED(c, "k_advance");
     }
     return FA_OK;
 }
 
 template <int L>
-static int enqueue_outer_p(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool f64, bool pass2, bool single,
-                           bool head, void* store) {
-    return f64 ? enqueue_outer<double, L>(c, Lo, d, pass2, single, head, store)
-               : enqueue_outer<float, L>(c, Lo, d, pass2, single, head, store);
+static int enqueue_outer_p(Batch& B, bool f64, bool pass2, bool single, bool head, bool rel) {
+    return f64 ? enqueue_outer<double, L>(B, pass2, single, head, rel)
+               : enqueue_outer<float, L>(B, pass2, single, head, rel);
 }
 
-static int enqueue_outer_any(fa_ctx* c, const Layout& Lo, const SolverDev& d, bool f64, bool pass2, bool single,
-                             bool head, void* store = nullptr) {
-    switch (Lo.L) {
-        case 1: return enqueue_outer_p<1>(c, Lo, d, f64, pass2, single, head, store);
-        case 2: return enqueue_outer_p<2>(c, Lo, d, f64, pass2, single, head, store);
-        case 3: return enqueue_outer_p<3>(c, Lo, d, f64, pass2, single, head, store);
-        case 4: return enqueue_outer_p<4>(c, Lo, d, f64, pass2, single, head, store);
-        case 8: return enqueue_outer_p<8>(c, Lo, d, f64, pass2, single, head, store);
+static int enqueue_outer_direct(Batch& B, bool f64, bool pass2, bool single, bool head, bool rel) {
+    switch (B.Lo.L) {
+        case 1: return enqueue_outer_p<1>(B, f64, pass2, single, head, rel);
+        case 2: return enqueue_outer_p<2>(B, f64, pass2, single, head, rel);
+        case 3: return enqueue_outer_p<3>(B, f64, pass2, single, head, rel);
+        case 4: return enqueue_outer_p<4>(B, f64, pass2, single, head, rel);
+        case 8: return enqueue_outer_p<8>(B, f64, pass2, single, head, rel);
         default: return FA_EINVAL;
     }
 }
 
-static int launch_sweep(fa_ctx* c, const Layout& Lo, const SolverDev& d) {
-    const int th = 32;
-    const int bl = (Lo.ns + th - 1) / th;
-    switch (Lo.L) {
-        case 1: k_sweep<1><<<bl, th, 0, c->stream>>>(d); break;
-        case 2: k_sweep<2><<<bl, th, 0, c->stream>>>(d); break;
-        case 3: k_sweep<3><<<bl, th, 0, c->stream>>>(d); break;
-        case 4: k_sweep<4><<<bl, th, 0, c->stream>>>(d); break;
-        case 8: k_sweep<8><<<bl, th, 0, c->stream>>>(d); break;
-        default: return FA_EINVAL;
+// One outer iteration, replayed from a captured CUDA graph when the batch
+// uses graphs (every argument of every launch is iteration-independent: the
+// kernels read m and their scalars from the device).
+static int enqueue_outer_any(Batch& B, bool f64, bool pass2, bool single, bool head, bool rel = false) {
+    if (!B.use_graph) return enqueue_outer_direct(B, f64, pass2, single, head, rel);
+    fa_ctx* c = B.c0;
+    const int key = (f64 ? 1 : 0) | (pass2 ? 2 : 0) | (single ? 4 : 0) | (head ? 8 : 0) | (rel ? 16 : 0);
+    GraphEntry* ge = nullptr;
+    for (auto& e : c->graphs)
+        if (e.key == key && e.L == B.Lo.L && e.dev == (void*)B.dev && e.n == B.n && e.V == B.Lo.V && e.exec)
+            ge = &e;
+    if (!ge) {
+        const long long n0 = c->launches;
+        cudaGraph_t g = nullptr;
+        FA_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int rc = enqueue_outer_direct(B, f64, pass2, single, head, rel);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc != FA_OK) { if (g) cudaGraphDestroy(g); return rc; }
+        FA_CUDA(e, "end capture");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        FA_CUDA(e, "instantiate graph");
+        c->graphs.push_back(GraphEntry{key, B.Lo.L, (void*)B.dev, B.n, B.Lo.V, ex, c->launches - n0});
+        c->launches = n0;
+        ge = &c->graphs.back();
     }
-    FA_LAUNCHED(c, "k_sweep");
+    FA_CUDA(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
+    c->launches += ge->kernels;
     return FA_OK;
 }
 
-// b (canonical) -> r_0 and rt of the requested precision, u_0 = 0
-static int load_source(fa_ctx* c, const Layout& Lo, const double* b, bool f64) {
-    if (f64) {
-        FA_TRY(launch_pack_spinor_f64(c->g, b, c->r64.as<double2>(), c->stream));
-        FA_CUDA(cudaMemcpyAsync(c->rt64.p, c->r64.p, (size_t)12 * Lo.V * sizeof(double2), cudaMemcpyDeviceToDevice,
-                                c->stream), "copy rt");
-        FA_CUDA(cudaMemsetAsync(c->u64.p, 0, (size_t)12 * Lo.V * sizeof(double2), c->stream), "zero u");
-    } else {
-        FA_TRY(launch_pack_spinor_f32(c->g, b, c->r32.as<float4>(), c->stream));
-        FA_CUDA(cudaMemcpyAsync(c->rt32.p, c->r32.p, (size_t)6 * Lo.V * sizeof(float4), cudaMemcpyDeviceToDevice,
-                                c->stream), "copy rt");
-        FA_CUDA(cudaMemsetAsync(c->u32.p, 0, (size_t)6 * Lo.V * sizeof(float4), c->stream), "zero u");
+static int launch_sweep(Batch& B) {
+    const int th = 32;
+    int maxns = 0;
+    for (auto* c : B.sys) maxns = std::max(maxns, c->ns);
+    const dim3 g((maxns + th - 1) / th, B.n);
+    cudaStream_t st = B.c0->stream;
+    switch (B.Lo.L) {
+        case 1: k_sweep<1><<<g, th, 0, st>>>(B.dev); break;
+        case 2: k_sweep<2><<<g, th, 0, st>>>(B.dev); break;
+        case 3: k_sweep<3><<<g, th, 0, st>>>(B.dev); break;
+        case 4: k_sweep<4><<<g, th, 0, st>>>(B.dev); break;
+        case 8: k_sweep<8><<<g, th, 0, st>>>(B.dev); break;
+        default: return FA_EINVAL;
     }
-    c->launches += 3;
+    FA_LAUNCHED(B.c0, "k_sweep");
+    return FA_OK;
+}
+
+// b (canonical) -> r_0 and rt of the requested precision, u_0 = 0, for system i
+static int load_source(Batch& B, int i, const double* b, bool f64) {
+    fa_ctx* c = B.sys[i];
+    cudaStream_t st = B.c0->stream;
+    const int V = B.Lo.V;
+    if (f64) {
+        FA_TRY(launch_pack_spinor_f64(c->g, b, c->r64.as<double2>(), st));
+        FA_CUDA(cudaMemcpyAsync(c->rt64.p, c->r64.p, (size_t)12 * V * sizeof(double2), cudaMemcpyDeviceToDevice, st),
+                "copy rt");
+        FA_CUDA(cudaMemsetAsync(c->u64.p, 0, (size_t)12 * V * sizeof(double2), st), "zero u");
+    } else {
+        FA_TRY(launch_pack_spinor_f32(c->g, b, c->r32.as<float4>(), st));
+        FA_CUDA(cudaMemcpyAsync(c->rt32.p, c->r32.p, (size_t)6 * V * sizeof(float4), cudaMemcpyDeviceToDevice, st),
+                "copy rt");
+        FA_CUDA(cudaMemsetAsync(c->u32.p, 0, (size_t)6 * V * sizeof(float4), st), "zero u");
+    }
+    B.c0->launches += 1;
     return FA_OK;
 }
 
 // FP64 -> FP32 hand-over of the live seed vectors (r_0, u_0, rt) at an outer-iteration boundary
-static int switch_to_f32(fa_ctx* c, const Layout& Lo) {
-    FA_TRY(launch_convert_f64_to_f32(c->g, c->r64.as<double2>(), c->r32.as<float4>(), c->stream));
-    FA_TRY(launch_convert_f64_to_f32(c->g, c->u64.as<double2>(), c->u32.as<float4>(), c->stream));
-    FA_TRY(launch_convert_f64_to_f32(c->g, c->rt64.as<double2>(), c->rt32.as<float4>(), c->stream));
-    c->launches += 3;
+static int switch_to_f32(Batch& B, int i) {
+    fa_ctx* c = B.sys[i];
+    cudaStream_t st = B.c0->stream;
+    FA_TRY(launch_convert_f64_to_f32(c->g, c->r64.as<double2>(), c->r32.as<float4>(), st));
+    FA_TRY(launch_convert_f64_to_f32(c->g, c->u64.as<double2>(), c->u32.as<float4>(), st));
+    FA_TRY(launch_convert_f64_to_f32(c->g, c->rt64.as<double2>(), c->rt32.as<float4>(), st));
+    B.c0->launches += 3;
     return FA_OK;
 }
 
-static int read_state(fa_ctx* c, DevState* out) {
-    FA_CUDA(cudaMemcpyAsync(out, c->state.p, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "read state");
-    FA_CUDA(cudaStreamSynchronize(c->stream), "sync state");
+// r_0, u_0, rt of system i <-> its snapshot buffer
+static int snapshot(Batch& B, int i, bool f64, bool restore) {
+    fa_ctx* c = B.sys[i];
+    const size_t sb = f64 ? B.Lo.vs64 * sizeof(double2) : B.Lo.vs32 * sizeof(float4);
+    char* snap = f64 ? c->snap64.as<char>() : c->snap32.as<char>();
+    void* v[3] = {f64 ? c->r64.p : c->r32.p, f64 ? c->u64.p : c->u32.p, f64 ? c->rt64.p : c->rt32.p};
+    for (int k = 0; k < 3; ++k) {
+        void* dst = restore ? v[k] : (void*)(snap + k * sb);
+        const void* src = restore ? (const void*)(snap + k * sb) : v[k];
+        FA_CUDA(cudaMemcpyAsync(dst, src, sb, cudaMemcpyDeviceToDevice, B.c0->stream), "snapshot");
+    }
+    if (B.host[i].x64) {   // reliable updates: the seed solution belongs to the state
+        const size_t xb = B.Lo.vs64 * sizeof(double2);
+        void* dst = restore ? (void*)B.host[i].x64 : c->snapx.p;
+        const void* src = restore ? c->snapx.p : (const void*)B.host[i].x64;
+        FA_CUDA(cudaMemcpyAsync(dst, src, xb, cudaMemcpyDeviceToDevice, B.c0->stream), "snapshot x");
+    }
     return FA_OK;
 }
 
-// ------------------------------------------------------------------ the solve
-int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, const fa_solver_params* p,
-          fa_solver_stats* stats) {
-    if (!c->have_gauge || !c->have_params || !c->have_poles) return FA_ESTATE;
+static int read_states(Batch& B, std::vector<DevState>& hs) {
+    hs.resize(B.n);
+    for (int i = 0; i < B.n; ++i)
+        FA_CUDA(cudaMemcpyAsync(&hs[i], B.sys[i]->state.p, sizeof(DevState), cudaMemcpyDeviceToHost, B.c0->stream),
+                "read state");
+    FA_CUDA(cudaStreamSynchronize(B.c0->stream), "sync state");
+    return FA_OK;
+}
+
+// ------------------------------------------------------------------ the solve (a batch of n systems)
+int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y_canon, double* const* xs_canon,
+                const fa_solver_params* p, fa_solver_stats* stats) {
+    if (n < 1 || !ctxs || !b || !p) return FA_EINVAL;
+    fa_ctx* c0 = ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        fa_ctx* c = ctxs[i];
+        if (!c || !b[i]) return FA_EINVAL;
+        if (!c->have_gauge || !c->have_params || !c->have_poles) return FA_ESTATE;
+        if (c->g.X != c0->g.X || c->g.Y != c0->g.Y || c->g.Z != c0->g.Z || c->g.T != c0->g.T) return FA_EINVAL;
+        if (c->device != c0->device) return FA_EINVAL;
+    }
     const int L = p->ell;
     if (!(L == 1 || L == 2 || L == 3 || L == 4 || L == 8)) return FA_EINVAL;
     if (!(p->tol > 0.0) || p->max_outer < 1 || p->max_outer > 1000000) return FA_EINVAL;
@@ -350,16 +485,22 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
     const int prec = p->precision;
     if (prec != FA_F64 && prec != FA_F32 && prec != FA_MIXED) return FA_EINVAL;
     if (single && prec != FA_F64) return FA_EINVAL;
+    if (prec == FA_MIXED && n != 1) return FA_EINVAL;   // per-system switch points: one system at a time
+    const int rel_every = p->reliable_every;
+    if (rel_every < 0 || (rel_every > 0 && n != 1)) return FA_EINVAL;
     // FA_MIXED: switch_resid <= 0 selects the default 0.04 / l^2 (the FP32
     // error of the power-basis recurrence grows with l)
     const double switch_resid = (p->switch_resid > 0.0) ? p->switch_resid : 0.04 / ((double)L * L);
     if (prec == FA_MIXED && !(switch_resid < 1.0)) return FA_EINVAL;
 
-    Layout Lo{};
+    Batch B;
+    B.c0 = c0;
+    B.n = n;
+    B.sys.assign(ctxs, ctxs + n);
+    Layout& Lo = B.Lo;
     Lo.L = L;
-    Lo.ns = c->ns;
     Lo.max_outer = p->max_outer;
-    Lo.V = c->g.V;
+    Lo.V = c0->g.V;
     Lo.single = single;
     Lo.need64 = prec != FA_F32;
     Lo.need32 = prec != FA_F64;
@@ -368,26 +509,31 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
     Lo.nblk = nblocks(Lo.V);
     Lo.red_grid = red_grid_for(Lo.V);
     Lo.part_slots = std::max(n_gram(L), 2);
-    FA_TRY(ensure_workspace(c, Lo));
-    SolverDev d = make_dev(c, Lo);
-    cudaStream_t st = c->stream;
+    for (auto* c : B.sys) FA_TRY(ensure_workspace(c, Lo));
+    FA_CUDA(c0->descbuf.ensure((size_t)n * sizeof(SolverDev)), "alloc descriptors");
+    FA_CUDA(c0->flagbuf.ensure((size_t)2 * n * sizeof(int)), "alloc flags");
+    if (c0->pinned_bytes < 2 * n * sizeof(int) + 64) {
+        if (c0->pinned) cudaFreeHost(c0->pinned);
+        c0->pinned = nullptr;
+        c0->pinned_bytes = 0;
+        FA_CUDA(cudaMallocHost(&c0->pinned, 2 * n * sizeof(int) + 4096), "alloc pinned");
+        c0->pinned_bytes = 2 * n * sizeof(int) + 4096;
+    }
+    B.dev = c0->descbuf.as<SolverDev>();
+    B.flags = c0->flagbuf.as<int>();
+    // graphs need a capturable stream (not the legacy default stream)
+    B.use_graph = (p->flags & 4) != 0 && c0->stream != nullptr && c0->stream != cudaStreamLegacy;
+    for (auto* c : B.sys) B.host.push_back(make_dev(c, Lo));
+    cudaStream_t st = c0->stream;
     const bool timing = (p->flags & 1) != 0;
-    c->hop_timing = (p->flags & 2) != 0;
+    c0->hop_timing = (p->flags & 2) != 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (timing)
         for (auto& e : ev) FA_CUDA(cudaEventCreate(&e), "event");
 
-    // poles
-    FA_CUDA(cudaMemcpyAsync((void*)d.sigma, c->sigma, Lo.ns * sizeof(double), cudaMemcpyHostToDevice, st), "poles");
-    FA_CUDA(cudaMemcpyAsync((void*)d.omega, c->omega, Lo.ns * sizeof(double), cudaMemcpyHostToDevice, st), "poles");
-    FA_CUDA(cudaMemsetAsync(c->y64.p, 0, (size_t)12 * Lo.V * sizeof(double2), st), "zero y");
-    if (single) {
-        FA_CUDA(cudaMemsetAsync(c->xs64.p, 0, (size_t)Lo.ns * 12 * Lo.V * sizeof(double2), st), "zero xs");
-        FA_CUDA(cudaMemsetAsync(c->us64.p, 0, (size_t)Lo.ns * (L + 1) * 12 * Lo.V * sizeof(double2), st), "zero us");
-    }
-    // ---- pseudo-double-pass store (Sec. 2, option 2): pass 1 keeps the seed-vector
-    // occurrences of a contiguous prefix [0, K) of outer iterations, as many as
-    // the budget holds (FP64 slots while in FP64, FP32 slots after the switch)
+    // ---- pseudo-double-pass stores (Sec. 2, option 2): pass 1 keeps the seed-vector
+    // occurrences of a contiguous prefix [0, K) of outer iterations, as many as the
+    // budget holds (FP64 slots while in FP64, FP32 slots after the switch)
     const int NC = nc_slots(L);
     const size_t s64 = Lo.vs64 * sizeof(double2), s32 = Lo.vs32 * sizeof(float4);
     const size_t per64 = (size_t)NC * s64, per32 = (size_t)NC * s32;
@@ -395,9 +541,10 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
     if (pseudo) {
         size_t fb = 0, tb = 0;
         FA_CUDA(cudaMemGetInfo(&fb, &tb), "memory info");
-        const double held = (double)c->store64.bytes + (double)c->store32.bytes;
+        double held = 0.0;
+        for (auto* c : B.sys) held += (double)c->store64.bytes + (double)c->store32.bytes;
         double budget = p->store_gb > 0.0 ? p->store_gb * 1e9 : std::min(0.25 * ((double)fb + held), 16e9);
-        budget = std::min(budget, 0.9 * ((double)fb + held));
+        budget = std::min(budget, 0.9 * ((double)fb + held)) / n;     // per system
         if (prec == FA_F64) {
             cap64 = (long long)std::min<double>(Lo.max_outer, budget / per64);
         } else if (prec == FA_F32) {
@@ -408,74 +555,101 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
         }
         cap64 = std::max(0LL, cap64);
         cap32 = std::max(0LL, cap32);
-        if (cap64 > 0) FA_CUDA(c->store64.ensure((size_t)cap64 * per64), "alloc occurrence store");
-        if (cap32 > 0) FA_CUDA(c->store32.ensure((size_t)cap32 * per32), "alloc occurrence store");
-        if (Lo.need64) FA_CUDA(c->snap64.ensure(3 * s64), "alloc snapshot");
-        if (Lo.need32) FA_CUDA(c->snap32.ensure(3 * s32), "alloc snapshot");
-    }
-    int K = pseudo ? -1 : 0;            // first outer iteration not stored (-1: still storing)
-    int m0_32 = prec == FA_F32 ? 0 : -1;  // first FP32 outer iteration
-    bool snap_f64 = true;
-    int snap_rc = FA_OK;
-    // r_0, u_0, rt of the current precision -> snapshot (pass 2 restarts from it)
-    auto snapshot = [&](bool f64now) {
-        snap_f64 = f64now;
-        const size_t sb = f64now ? s64 : s32;
-        char* dst = f64now ? c->snap64.as<char>() : c->snap32.as<char>();
-        void* src[3] = {f64now ? c->r64.p : c->r32.p, f64now ? c->u64.p : c->u32.p, f64now ? c->rt64.p : c->rt32.p};
-        for (int k = 0; k < 3; ++k)
-            if (cudaMemcpyAsync(dst + k * sb, src[k], sb, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-                snap_rc = cuda_fail(cudaGetLastError(), "snapshot");
-    };
-    auto store_for = [&](int m, bool f64now) -> void* {
-        if (K >= 0) return nullptr;
-        void* ptr = nullptr;
-        if (f64now && m < cap64) ptr = c->store64.as<char>() + (size_t)m * per64;
-        if (!f64now && m0_32 >= 0 && m - m0_32 < cap32) ptr = c->store32.as<char>() + (size_t)(m - m0_32) * per32;
-        if (!ptr) {
-            K = m;
-            snapshot(f64now);
+        for (int i = 0; i < n; ++i) {
+            fa_ctx* c = B.sys[i];
+            if (cap64 > 0) FA_CUDA(c->store64.ensure((size_t)cap64 * per64), "alloc occurrence store");
+            if (cap32 > 0) FA_CUDA(c->store32.ensure((size_t)cap32 * per32), "alloc occurrence store");
+            if (Lo.need64) FA_CUDA(c->snap64.ensure(3 * s64), "alloc snapshot");
+            if (Lo.need32) FA_CUDA(c->snap32.ensure(3 * s32), "alloc snapshot");
+            B.host[i].store64 = c->store64.as<char>();
+            B.host[i].store32 = c->store32.as<char>();
+            B.host[i].cap64 = (int)cap64;
+            B.host[i].cap32 = (int)cap32;
+            B.host[i].m0_32 = prec == FA_F32 ? 0 : -1;
         }
-        return ptr;
+    }
+    if (rel_every > 0) {
+        fa_ctx* c = B.sys[0];
+        FA_CUDA(c->xrel.ensure(s64), "alloc x");
+        FA_CUDA(c->brel.ensure(s64), "alloc b");
+        FA_CUDA(c->io64a.ensure(s64), "alloc");
+        FA_CUDA(c->io64b.ensure(s64), "alloc");
+        if (pseudo) FA_CUDA(c->snapx.ensure(s64), "alloc snapshot x");
+        FA_TRY(launch_pack_spinor_f64(c->g, b[0], c->brel.as<double2>(), st));
+        FA_CUDA(cudaMemsetAsync(c->xrel.p, 0, s64, st), "zero x");
+        B.host[0].x64 = c->xrel.as<double2>();
+        B.host[0].b64 = c->brel.as<double2>();
+    }
+    // outer iteration m ends with a reliable update
+    auto reliable_at = [&](int m) { return rel_every > 0 && (m + 1) % rel_every == 0; };
+    FA_TRY(upload(B));
+    int K = pseudo ? -1 : 0;                // first outer iteration not stored (-1: still storing)
+    int m0_32 = prec == FA_F32 ? 0 : -1;    // first FP32 outer iteration (one value for the batch)
+    bool snap_f64 = true;
+    // called before outer iteration m is enqueued: at the first unstored one,
+    // snapshot the seed state so that a pass 2 can restart there
+    auto before_outer = [&](int m, bool f64now) -> int {
+        if (K >= 0) return FA_OK;
+        const bool stored = f64now ? (m < cap64) : (m0_32 >= 0 && m - m0_32 < cap32);
+        if (stored) return FA_OK;
+        K = m;
+        snap_f64 = f64now;
+        for (int i = 0; i < n; ++i) FA_TRY(snapshot(B, i, f64now, false));
+        return FA_OK;
     };
+
+    // poles, y, shift vectors
+    for (int i = 0; i < n; ++i) {
+        fa_ctx* c = B.sys[i];
+        const SolverDev& d = B.host[i];
+        FA_CUDA(cudaMemcpyAsync((void*)d.sigma, c->sigma, c->ns * sizeof(double), cudaMemcpyHostToDevice, st), "poles");
+        FA_CUDA(cudaMemcpyAsync((void*)d.omega, c->omega, c->ns * sizeof(double), cudaMemcpyHostToDevice, st), "poles");
+        FA_CUDA(cudaMemsetAsync(d.y, 0, (size_t)12 * Lo.V * sizeof(double2), st), "zero y");
+        if (single) {
+            FA_CUDA(cudaMemsetAsync(d.xs, 0, (size_t)c->ns * 12 * Lo.V * sizeof(double2), st), "zero xs");
+            FA_CUDA(cudaMemsetAsync(d.us, 0, (size_t)c->ns * (L + 1) * 12 * Lo.V * sizeof(double2), st), "zero us");
+        }
+    }
     if (timing) cudaEventRecord(ev[0], st);
 
     // ---- pass 1
     bool f64 = prec != FA_F32;
     bool head = prec == FA_MIXED;
-    FA_TRY(load_source(c, Lo, b, f64));
-    if (f64)
-        k_dot2<double><<<Lo.red_grid, kThreads, 0, st>>>(Lo.V, c->rt64.as<double2>(), c->r64.as<double2>(),
-                                                          c->partials.as<double2>());
-    else
-        k_dot2<float><<<Lo.red_grid, kThreads, 0, st>>>(Lo.V, c->rt32.as<float4>(), c->r32.as<float4>(),
-                                                         c->partials.as<double2>());
-    FA_LAUNCHED(c, "k_dot2");
-    k_sc_init<<<1, kScalarThreads, 0, st>>>(d, c->partials.as<double2>(), Lo.red_grid, p->tol,
-                                            prec == FA_MIXED ? switch_resid : 0.0);
-    FA_LAUNCHED(c, "k_sc_init");
+    for (int i = 0; i < n; ++i) FA_TRY(load_source(B, i, b[i], f64));
+    const dim3 gr(Lo.red_grid, n);
+    if (f64) k_dot2_sys<double><<<gr, kThreads, 0, st>>>(B.dev);
+    else k_dot2_sys<float><<<gr, kThreads, 0, st>>>(B.dev);
+    FA_LAUNCHED(c0, "k_dot2_sys");
+    k_sc_init<<<n, kScalarThreads, 0, st>>>(B.dev, Lo.red_grid, p->tol, prec == FA_MIXED ? switch_resid : 0.0);
+    FA_LAUNCHED(c0, "k_sc_init");
 
-    DevState hs{};
+    std::vector<DevState> hs(n);
     int switch_outer = -1;
     int enq = 0;
-    // FP64 head of FA_MIXED: one outer iteration at a time until the switch
+    bool all_done = false;
+    // FP64 head of FA_MIXED (one system): one outer iteration at a time until the switch
     while (head && enq < Lo.max_outer) {
-        FA_TRY(enqueue_outer_any(c, Lo, d, true, false, single, true, store_for(enq, true)));
+        FA_TRY(before_outer(enq, true));
+        FA_TRY(enqueue_outer_any(B, true, false, single, true, reliable_at(enq)));
         ++enq;
-        FA_TRY(read_state(c, &hs));
-        if (hs.done) break;
-        if (hs.switch_req) {
-            FA_TRY(switch_to_f32(c, Lo));
-            switch_outer = hs.m;
+        FA_TRY(read_states(B, hs));
+        if (hs[0].done) { all_done = true; break; }
+        if (hs[0].switch_req) {
+            FA_TRY(switch_to_f32(B, 0));
+            switch_outer = hs[0].m;
             m0_32 = switch_outer;
+            // the stored prefix must stay contiguous: no FP32 slots if the head outran its slots
+            B.host[0].m0_32 = m0_32;
+            if (K >= 0) B.host[0].cap32 = 0, cap32 = 0;
+            FA_TRY(upload(B));
             head = false;
             f64 = false;
         }
     }
-    if (!hs.done) {
-        // main loop: chunks of outer iterations, polling the previous chunk's flag
-        const int chunk = Lo.V >= (1 << 17) ? 2 : 8;
-        DevState* pin = static_cast<DevState*>(c->pinned);
+    if (!all_done) {
+        // main loop: chunks of outer iterations; poll the previous chunk's done flags
+        const int chunk = (Lo.V * (long long)n) >= (1 << 17) ? 2 : 8;
+        int* pin = static_cast<int*>(c0->pinned);
         cudaEvent_t pe[2];
         FA_CUDA(cudaEventCreateWithFlags(&pe[0], cudaEventDisableTiming), "event");
         FA_CUDA(cudaEventCreateWithFlags(&pe[1], cudaEventDisableTiming), "event");
@@ -484,129 +658,146 @@ int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, 
         int rc = FA_OK;
         while (!stop && enq < Lo.max_outer) {
             for (int i = 0; i < chunk && enq < Lo.max_outer; ++i, ++enq) {
-                rc = enqueue_outer_any(c, Lo, d, f64, false, single, false, store_for(enq, f64));
+                rc = before_outer(enq, f64);
+                if (rc == FA_OK) rc = enqueue_outer_any(B, f64, false, single, false, reliable_at(enq));
                 if (rc != FA_OK) break;
             }
             if (rc != FA_OK) break;
-            cudaMemcpyAsync(&pin[k & 1], c->state.p, sizeof(DevState), cudaMemcpyDeviceToHost, st);
+            k_flags<<<(n + 127) / 128, 128, 0, st>>>(B.dev, n, B.flags + (k & 1) * n);
+            cudaMemcpyAsync(pin + (k & 1) * n, B.flags + (k & 1) * n, n * sizeof(int), cudaMemcpyDeviceToHost, st);
             cudaEventRecord(pe[k & 1], st);
             if (k > 0) {
                 cudaEventSynchronize(pe[(k - 1) & 1]);
-                if (pin[(k - 1) & 1].done) stop = true;
+                bool all = true;
+                for (int i = 0; i < n; ++i) all = all && pin[((k - 1) & 1) * n + i] != 0;
+                if (all) stop = true;
             }
             ++k;
         }
         cudaEventDestroy(pe[0]);
         cudaEventDestroy(pe[1]);
         FA_TRY(rc);
-        FA_TRY(read_state(c, &hs));
+        FA_TRY(read_states(B, hs));
     }
     if (timing) cudaEventRecord(ev[1], st);
-    const int M = hs.n_outer;
-    int status = hs.status;
-    if (status == FA_OK && !hs.done) status = FA_ENOCONV;
-
-    FA_TRY(snap_rc);
-    const int Kst = pseudo ? (K < 0 ? M : std::min(K, M)) : 0;   // stored prefix
+    std::vector<int> status(n);
+    int M = 0, rc_all = FA_OK;
+    for (int i = 0; i < n; ++i) {
+        status[i] = hs[i].status;
+        if (status[i] == FA_OK && !hs[i].done) status[i] = FA_ENOCONV;
+        if (status[i] != FA_OK && rc_all == FA_OK) rc_all = status[i];
+        M = std::max(M, hs[i].n_outer);
+    }
+    const int Kst = pseudo ? (K < 0 ? M : std::min(K, M)) : 0;   // stored prefix (all systems)
 
     // ---- backward sweep, gather of the stored prefix, pass 2 for the rest
-    if (status == FA_OK && !single) {
-        FA_CUDA(cudaMemsetAsync(c->cs.p, 0, (size_t)Lo.ns * Lo.max_outer * nc_slots(L) * sizeof(double2), st),
-                "zero sweep");
-        FA_TRY(launch_sweep(c, Lo, d));
-        const int n = M * nc_slots(L);
-        k_coef_reduce<<<(n + 255) / 256, 256, 0, st>>>(d, M);
-        FA_LAUNCHED(c, "k_coef_reduce");
+    if (rc_all == FA_OK && !single) {
+        for (int i = 0; i < n; ++i)
+            FA_CUDA(cudaMemsetAsync(B.host[i].cs, 0, (size_t)B.sys[i]->ns * Lo.max_outer * NC * sizeof(double2), st),
+                    "zero sweep");
+        FA_TRY(launch_sweep(B));
+        k_coef_reduce<<<dim3((M * NC + 255) / 256, n), 256, 0, st>>>(B.dev);
+        FA_LAUNCHED(c0, "k_coef_reduce");
         if (timing) cudaEventRecord(ev[2], st);
-        if (Kst > 0) {
-            // FP64 slots cover [0, end64), FP32 slots [m0_32, Kst)
-            const int end64 = prec == FA_F64 ? Kst : (prec == FA_MIXED ? (m0_32 >= 0 ? std::min(Kst, m0_32) : Kst) : 0);
-            if (end64 > 0) {
-                k_gather<double><<<Lo.nblk, kThreads, 0, st>>>(d, c->store64.as<double2>(), Lo.vs64, 0, end64, 0,
-                                                                c->y64.as<double2>());
-                FA_LAUNCHED(c, "k_gather<double>");
+        const dim3 gs(Lo.nblk, n);
+        if (pseudo && Kst > 0) {
+            if (cap64 > 0) {
+                k_gather<double><<<gs, kThreads, 0, st>>>(B.dev);
+                FA_LAUNCHED(c0, "k_gather<double>");
             }
-            if (m0_32 >= 0 && Kst > m0_32) {
-                k_gather<float><<<Lo.nblk, kThreads, 0, st>>>(d, c->store32.as<float4>(), Lo.vs32, m0_32, Kst, m0_32,
-                                                               c->y64.as<double2>());
-                FA_LAUNCHED(c, "k_gather<float>");
+            if (cap32 > 0 && m0_32 >= 0) {
+                k_gather<float><<<gs, kThreads, 0, st>>>(B.dev);
+                FA_LAUNCHED(c0, "k_gather<float>");
             }
         }
         const int mstart = Kst;
         if (mstart < M) {
             bool p2f64 = prec == FA_F64 || (prec == FA_MIXED && (switch_outer < 0 || mstart < switch_outer));
-            if (mstart == 0) {
-                FA_TRY(load_source(c, Lo, b, p2f64));
-            } else {
-                // restart from the snapshot taken before outer iteration K
-                if (snap_f64 != p2f64) return FA_ESTATE;
-                const size_t sb = p2f64 ? s64 : s32;
-                const char* src = p2f64 ? c->snap64.as<char>() : c->snap32.as<char>();
-                void* dst[3] = {p2f64 ? c->r64.p : c->r32.p, p2f64 ? c->u64.p : c->u32.p, p2f64 ? c->rt64.p : c->rt32.p};
-                for (int k = 0; k < 3; ++k)
-                    FA_CUDA(cudaMemcpyAsync(dst[k], src + k * sb, sb, cudaMemcpyDeviceToDevice, st), "restore");
+            for (int i = 0; i < n; ++i) {
+                if (mstart == 0) {
+                    FA_TRY(load_source(B, i, b[i], p2f64));
+                    if (B.host[i].x64)
+                        FA_CUDA(cudaMemsetAsync(B.host[i].x64, 0, s64, st), "zero x");
+                } else {
+                    if (snap_f64 != p2f64) return FA_ESTATE;
+                    FA_TRY(snapshot(B, i, p2f64, true));
+                }
             }
-            k_set_m<<<1, 1, 0, st>>>(d, mstart);
-            FA_LAUNCHED(c, "k_set_m");
+            k_set_m<<<n, 1, 0, st>>>(B.dev, mstart);
+            FA_LAUNCHED(c0, "k_set_m");
             for (int m = mstart; m < M; ++m) {
                 if (p2f64 && prec == FA_MIXED && m == switch_outer) {
-                    FA_TRY(switch_to_f32(c, Lo));
+                    FA_TRY(switch_to_f32(B, 0));
                     p2f64 = false;
                 }
-                FA_TRY(enqueue_outer_any(c, Lo, d, p2f64, true, false, false));
+                FA_TRY(enqueue_outer_any(B, p2f64, true, false, false, reliable_at(m)));
             }
         }
         if (timing) cudaEventRecord(ev[3], st);
-        FA_TRY(launch_unpack_spinor_f64(c->g, c->y64.as<double2>(), y_canon, st));
-        c->launches++;
-    } else if (status == FA_OK && single) {
+        if (y_canon)
+            for (int i = 0; i < n; ++i) {
+                FA_TRY(launch_unpack_spinor_f64(B.sys[i]->g, B.host[i].y, y_canon[i], st));
+                c0->launches++;
+            }
+    } else if (rc_all == FA_OK && single) {
         if (timing) { cudaEventRecord(ev[2], st); cudaEventRecord(ev[3], st); }
         if (y_canon) {
-            k_combine<<<(12 * Lo.V + kThreads - 1) / kThreads, kThreads, 0, st>>>(
-                Lo.V, Lo.ns, d.omega, c->xs64.as<double2>(), Lo.vs64, c->y64.as<double2>());
-            FA_LAUNCHED(c, "k_combine");
-            FA_TRY(launch_unpack_spinor_f64(c->g, c->y64.as<double2>(), y_canon, st));
-            c->launches++;
+            k_combine_sys<<<dim3((12 * Lo.V + kThreads - 1) / kThreads, n), kThreads, 0, st>>>(B.dev);
+            FA_LAUNCHED(c0, "k_combine_sys");
+            for (int i = 0; i < n; ++i) {
+                FA_TRY(launch_unpack_spinor_f64(B.sys[i]->g, B.host[i].y, y_canon[i], st));
+                c0->launches++;
+            }
         }
-        if (xs_canon) {
-            for (int s = 0; s < Lo.ns; ++s) {
-                FA_TRY(launch_unpack_spinor_f64(c->g, c->xs64.as<double2>() + (size_t)s * Lo.vs64, xs_canon[s], st));
-                c->launches++;
+        if (xs_canon && n == 1) {
+            for (int s = 0; s < c0->ns; ++s) {
+                FA_TRY(launch_unpack_spinor_f64(c0->g, B.host[0].xs + (size_t)s * Lo.vs64, xs_canon[s], st));
+                c0->launches++;
             }
         }
     }
     FA_CUDA(cudaStreamSynchronize(st), "sync solve");
-    if (c->hop_timing) hop_timing_collect(c);
-    c->hop_timing = false;
+    if (c0->hop_timing) hop_timing_collect(c0);
+    c0->hop_timing = false;
 
     if (stats) {
-        std::memset(stats, 0, sizeof(*stats));
-        stats->status = status;
-        stats->outer_iters = M;
-        stats->switch_outer = switch_outer;
-        stats->ns = Lo.ns;
-        int iters[kMaxShifts];
-        FA_CUDA(cudaMemcpy(iters, d.iters, Lo.ns * sizeof(int), cudaMemcpyDeviceToHost), "read iters");
-        for (int s = 0; s < Lo.ns; ++s) stats->iters_per_shift[s] = iters[s];
-        stats->resid_recurrence = std::sqrt(hs.rnorm2 / hs.bnorm2);
-        const long long per = 2LL * L * M;
-        stats->n_mv = single ? per : per + 2LL * L * (M - Kst);
-        stats->stored_outer = Kst;
-        stats->n_dot = (long long)M * (L * (L + 7) / 2 + 1);
-        stats->n_launch = c->launches;
-        if (timing) {
-            float a = 0.f, b2 = 0.f, c2 = 0.f;
-            cudaEventElapsedTime(&a, ev[0], ev[1]);
-            cudaEventElapsedTime(&b2, ev[1], ev[2]);
-            cudaEventElapsedTime(&c2, ev[2], ev[3]);
-            stats->t_pass1_ms = a;
-            stats->t_sweep_ms = b2;
-            stats->t_pass2_ms = c2;
+        for (int i = 0; i < n; ++i) {
+            fa_solver_stats& S = stats[i];
+            std::memset(&S, 0, sizeof(S));
+            const int Mi = hs[i].n_outer;
+            S.status = status[i];
+            S.outer_iters = Mi;
+            S.switch_outer = switch_outer;
+            S.ns = B.sys[i]->ns;
+            int iters[kMaxShifts];
+            FA_CUDA(cudaMemcpy(iters, B.host[i].iters, S.ns * sizeof(int), cudaMemcpyDeviceToHost), "read iters");
+            for (int s = 0; s < S.ns; ++s) S.iters_per_shift[s] = iters[s];
+            S.resid_recurrence = std::sqrt(hs[i].rnorm2 / hs[i].bnorm2);
+            const int Ki = std::min(Kst, Mi);
+            const long long per = 2LL * L * Mi;
+            S.n_mv = single ? per : per + 2LL * L * (Mi - (pseudo ? Ki : 0));
+            S.stored_outer = pseudo ? Ki : 0;
+            S.n_dot = (long long)Mi * (L * (L + 7) / 2 + 1);
+            S.n_launch = c0->launches;
+            if (timing) {
+                float a = 0.f, b2 = 0.f, c2 = 0.f;
+                cudaEventElapsedTime(&a, ev[0], ev[1]);
+                cudaEventElapsedTime(&b2, ev[1], ev[2]);
+                cudaEventElapsedTime(&c2, ev[2], ev[3]);
+                S.t_pass1_ms = a;
+                S.t_sweep_ms = b2;
+                S.t_pass2_ms = c2;
+            }
         }
     }
     if (timing)
         for (auto& e : ev) cudaEventDestroy(e);
-    return status;
+    return rc_all;
+}
+
+int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, const fa_solver_params* p,
+          fa_solver_stats* stats) {
+    return solve_batch(&c, 1, &b, y_canon ? &y_canon : nullptr, xs_canon, p, stats);
 }
 
 // ------------------------------------------------------------------ adjoint gradient
@@ -650,7 +841,7 @@ int grad(fa_ctx* c, const double* b, const double* eta, double* dLdU, double* dL
         const double2* ls = lam + s * vs;
         FA_TRY(hop_f64(c, xs, t1, 1.0, false, true, false, nullptr, nullptr, nullptr));   // g5 D x
         FA_TRY(hop_f64(c, ls, t2, 1.0, false, false, true, nullptr, nullptr, nullptr));   // D(-mu) lambda
-        FA_TRY(launch_force(c->g, c->links64.as<double2>(), ls, t1, t2, xs, dLdU, -c->scale_c * c->omega[s],
+        FA_TRY(launch_force(c->g, links64_of(c), ls, t1, t2, xs, dLdU, -c->scale_c * c->omega[s],
                             std::exp(c->mu), std::exp(-c->mu), c->t_bc, part + (size_t)s * nb, st));
         c->launches++;
     }

@@ -22,7 +22,7 @@
 // arithmetic (explicit fma intrinsics, no contraction by the compiler).
 #pragma once
 
-#include "fa_internal.cuh"
+#include "hop_device.cuh"
 
 namespace fa {
 
@@ -52,9 +52,17 @@ __host__ __device__ constexpr int slot_old(int j, int i) { return j * (j + 1) / 
 __host__ __device__ constexpr int slot_mr(int L, int k) { return L * (L + 1) / 2 + k; }
 __host__ __device__ constexpr int n_gram(int L) { return (L + 1) * (L + 2) / 2; }
 
+// Everything one system needs on the device.  Kernels read their system's
+// descriptor from an array (ds[blockIdx.y] for site kernels, ds[blockIdx.x]
+// for the single-block scalar kernels), so one launch serves a batch of
+// systems of the same lattice shape; a single solve is a batch of one.
 struct SolverDev {
     DevState* st;
     int ns, L, max_outer, V;
+    Geom g;
+    const double2* links64;
+    const float4* links32;
+    double diag, ef, eb, bc, scale;   // 4+m, e^{+mu}, e^{-mu}, time-boundary sign, c
     const double* sigma;   // [ns]
     const double* omega;   // [ns]
     double2* zeta;         // [ns]
@@ -67,7 +75,48 @@ struct SolverDev {
     double2* prec;         // [ns][max_outer][ps_stride]
     double2* coef;         // [max_outer][nc_slots]
     double2* cs;           // [ns][max_outer][nc_slots]   per-shift sweep output
+    // seed vectors: r_0..r_l and u_0..u_l contiguous, the shadow vector, scratch
+    double2 *r64, *u64, *rt64, *tmp64;
+    float4 *r32, *u32, *rt32, *tmp32;
+    double2* y;            // FP64 [12][V] result
+    double2* xs;           // single-pass x_s   [ns][12][V]
+    double2* us;           // single-pass u^s_i [ns][l+1][12][V]
+    // pseudo-double-pass occurrence stores: outer iteration m is stored in the
+    // FP64 store if m < cap64, in the FP32 store if 0 <= m - m0_32 < cap32
+    char* store64;
+    char* store32;
+    int cap64, cap32, m0_32;
+    int nblk, red_grid;    // hop partials per launch, grid of the reduction kernels
+    double2* part;         // this system's reduction partials
+    // reliable updates: seed solution x (FP64, [12][V], accumulated alongside the
+    // recurrence when not null) and the packed source b (FP64)
+    double2* x64;
+    const double2* b64;
 };
+
+template <typename R> struct Vec;
+template <> struct Vec<double> {
+    using T = double2;
+    __device__ static T* r(const SolverDev& d) { return d.r64; }
+    __device__ static T* u(const SolverDev& d) { return d.u64; }
+    __device__ static T* rt(const SolverDev& d) { return d.rt64; }
+    __device__ static T* tmp(const SolverDev& d) { return d.tmp64; }
+    __device__ static LinkView<double> links(const SolverDev& d) { return {d.links64, d.V}; }
+};
+template <> struct Vec<float> {
+    using T = float4;
+    __device__ static T* r(const SolverDev& d) { return d.r32; }
+    __device__ static T* u(const SolverDev& d) { return d.u32; }
+    __device__ static T* rt(const SolverDev& d) { return d.rt32; }
+    __device__ static T* tmp(const SolverDev& d) { return d.tmp32; }
+    __device__ static LinkView<float> links(const SolverDev& d) { return {d.links32, d.V}; }
+};
+
+// pass 1: the system has finished (converged, failed or max_outer);
+// pass 2: the system has replayed all its outer iterations.
+__device__ __forceinline__ bool sys_idle(const SolverDev& d, int pass2) {
+    return pass2 ? (d.st->m >= d.st->n_outer) : (d.st->done != 0);
+}
 
 // ------------------------------------------------------------------ chunk IO
 // A chunk is the vector unit of one load: FP64 one complex (double2, 12 per
@@ -98,6 +147,23 @@ template <> struct Ch<float> {
     }
 };
 
+template <typename R> __device__ __forceinline__ size_t vstride(const SolverDev& d) {
+    return (size_t)Ch<R>::N * d.V;
+}
+
+// store slots of outer iteration m, or nullptr when m is not stored
+template <typename R>
+__device__ __forceinline__ typename Ch<R>::T* store_at(const SolverDev& d, int m) {
+    const size_t per = (size_t)nc_slots(d.L) * vstride<R>(d) * sizeof(typename Ch<R>::T);
+    if (sizeof(R) == 8) {
+        if (m < d.cap64) return reinterpret_cast<typename Ch<R>::T*>(d.store64 + (size_t)m * per);
+    } else {
+        const int k = m - d.m0_32;
+        if (d.m0_32 >= 0 && k >= 0 && k < d.cap32) return reinterpret_cast<typename Ch<R>::T*>(d.store32 + (size_t)k * per);
+    }
+    return nullptr;
+}
+
 template <typename R> __device__ __forceinline__ cx<R> tocx(double2 v) { return {(R)v.x, (R)v.y}; }
 template <typename R> __device__ __forceinline__ cx<R> negcx(double2 v) { return {(R)(-v.x), (R)(-v.y)}; }
 
@@ -114,14 +180,34 @@ __device__ __forceinline__ void acc_y(double2* y, int q, int V, int s, const cx<
     }
 }
 
+// x (FP64) += a v for the W components of chunk q
+template <typename R>
+__device__ __forceinline__ void acc_x(double2* x, int q, int V, int s, double2 a, const Ch<R>& v) {
+#pragma unroll
+    for (int w = 0; w < Ch<R>::W; ++w) {
+        double2* p = x + (size_t)(q * Ch<R>::W + w) * V + s;
+        double2 t = *p;
+        const double vr = (double)v.c[w].r, vi = (double)v.c[w].i;
+        t.x = __fma_rn(a.x, vr, t.x);
+        t.x = __fma_rn(-a.y, vi, t.x);
+        t.y = __fma_rn(a.x, vi, t.y);
+        t.y = __fma_rn(a.y, vr, t.y);
+        *p = t;
+    }
+}
+
 // ------------------------------------------------------------------ BiCG sub-step kernels
 // u_i <- r_i - beta u_i, i = 0..j (r, u: l+1 spinors each, contiguous, stride vs)
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_update_u(SolverDev d, int j, const typename Ch<R>::T* r, typename Ch<R>::T* u, size_t vs, const int* done) {
-    if (done != nullptr && *done) return;
+k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
+    const SolverDev& d = ds[blockIdx.y];
+    if (sys_idle(d, pass2)) return;
     const int s = blockIdx.x * kThreads + threadIdx.x;
     if (s >= d.V) return;
+    const typename Ch<R>::T* r = Vec<R>::r(d);
+    typename Ch<R>::T* u = Vec<R>::u(d);
+    const size_t vs = vstride<R>(d);
     const int m = d.st->m;
     const cx<R> nb = negcx<R>(d.rec_beta[m * d.L + j]);
     for (int i = 0; i <= j; ++i) {
@@ -143,12 +229,20 @@ k_update_u(SolverDev d, int j, const typename Ch<R>::T* r, typename Ch<R>::T* u,
 // reading each seed vector once for all active shifts.
 template <typename R, bool ACC, bool SHIFTS>
 __global__ void __launch_bounds__(kThreads)
-k_update_r(SolverDev d, int j, typename Ch<R>::T* r, const typename Ch<R>::T* u, size_t vs, double2* y,
-           double2* xs, double2* us, size_t svs, typename Ch<R>::T* store, const int* done) {
-    if (done != nullptr && *done) return;
+k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
+    const SolverDev& d = ds[blockIdx.y];
+    if (sys_idle(d, pass2)) return;
     const int s = blockIdx.x * kThreads + threadIdx.x;
     if (s >= d.V) return;
     const int m = d.st->m;
+    typename Ch<R>::T* r = Vec<R>::r(d);
+    const typename Ch<R>::T* u = Vec<R>::u(d);
+    const size_t vs = vstride<R>(d);
+    double2* y = d.y;
+    double2* xs = d.xs;
+    double2* us = d.us;
+    const size_t svs = (size_t)12 * d.V;
+    typename Ch<R>::T* store = pass2 ? nullptr : store_at<R>(d, m);
     const int L = d.L;
     const cx<R> na = negcx<R>(d.rec_alpha[m * L + j]);
     const double2* cf = d.coef + (size_t)m * nc_slots(L);
@@ -212,6 +306,7 @@ k_update_r(SolverDev d, int j, typename Ch<R>::T* r, const typename Ch<R>::T* u,
             }
         }
         if (ACC) acc_y<R>(y, q, d.V, s, t);
+        if (d.x64 != nullptr) acc_x<R>(d.x64, q, d.V, s, d.rec_alpha[m * L + j], Ch<R>::ld(u, q, d.V, s));
     }
 }
 
@@ -219,8 +314,12 @@ k_update_r(SolverDev d, int j, typename Ch<R>::T* r, const typename Ch<R>::T* u,
 // Gram matrix <r_i, r_k>, 0 <= i <= k <= L, grid-stride, per-block partials.
 template <typename R, int L>
 __global__ void __launch_bounds__(kThreads)
-k_gram(SolverDev d, const typename Ch<R>::T* r, size_t vs, double2* partials, const int* done) {
-    if (done != nullptr && *done) return;
+k_gram(const SolverDev* __restrict__ ds) {
+    const SolverDev& d = ds[blockIdx.y];
+    if (sys_idle(d, 0)) return;
+    const typename Ch<R>::T* r = Vec<R>::r(d);
+    const size_t vs = vstride<R>(d);
+    double2* partials = d.part;
     constexpr int NG = n_gram(L);
     cx<R> acc[NG];
 #pragma unroll
@@ -251,11 +350,20 @@ k_gram(SolverDev d, const typename Ch<R>::T* r, size_t vs, double2* partials, co
 // DOT: per-block partials of <rt, r_0> (slot 0) and |r_0|^2 (slot 1), grid-stride.
 template <typename R, int L, bool ACC, bool SHIFTS, bool DOT>
 __global__ void __launch_bounds__(kThreads)
-k_mr(SolverDev d, typename Ch<R>::T* r, typename Ch<R>::T* u, const typename Ch<R>::T* rt, size_t vs,
-     double2* y, double2* xs, double2* us, size_t svs, typename Ch<R>::T* store, double2* partials,
-     const int* done) {
-    if (done != nullptr && *done) return;
+k_mr(const SolverDev* __restrict__ ds, int pass2) {
+    const SolverDev& d = ds[blockIdx.y];
+    if (sys_idle(d, pass2)) return;
     const int m = d.st->m;
+    typename Ch<R>::T* r = Vec<R>::r(d);
+    typename Ch<R>::T* u = Vec<R>::u(d);
+    const typename Ch<R>::T* rt = Vec<R>::rt(d);
+    const size_t vs = vstride<R>(d);
+    double2* y = d.y;
+    double2* xs = d.xs;
+    double2* us = d.us;
+    const size_t svs = (size_t)12 * d.V;
+    typename Ch<R>::T* store = pass2 ? nullptr : store_at<R>(d, m);
+    double2* partials = d.part;
     cx<R> ng[L + 1];
     ng[0] = czero<R>();
 #pragma unroll
@@ -311,6 +419,10 @@ k_mr(SolverDev d, typename Ch<R>::T* r, typename Ch<R>::T* u, const typename Ch<
                     u0.stv((typename Ch<R>::T*)(us + (size_t)sh * (L + 1) * svs), q, d.V, s);
                 }
             }
+            if (d.x64 != nullptr) {
+#pragma unroll
+                for (int j = 1; j <= L; ++j) acc_x<R>(d.x64, q, d.V, s, d.rec_gamma[m * (L + 1) + j], rv[j - 1]);
+            }
             Ch<R> r0 = rv[0];
             Ch<R> u0 = Ch<R>::ld(u, q, d.V, s);
 #pragma unroll
@@ -340,8 +452,8 @@ k_mr(SolverDev d, typename Ch<R>::T* r, typename Ch<R>::T* u, const typename Ch<
 
 // <rt, r0> (slot 0) and |r0|^2 (slot 1), grid-stride (start of a solve)
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
-k_dot2(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0, double2* partials) {
+__device__ __forceinline__ void k_dot2_body(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0,
+                                            double2* partials) {
     cx<R> dots[2] = {czero<R>(), czero<R>()};
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < V; s += gridDim.x * kThreads) {
 #pragma unroll
@@ -356,6 +468,56 @@ k_dot2(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0, double2*
         }
     }
     block_reduce_store<2, R>(dots, partials, gridDim.x);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_dot2(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0, double2* partials) {
+    k_dot2_body<R>(V, rt, r0, partials);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_dot2_sys(const SolverDev* __restrict__ ds) {
+    const SolverDev& d = ds[blockIdx.y];
+    k_dot2_body<R>(d.V, Vec<R>::rt(d), Vec<R>::r(d), d.part);
+}
+
+// A application inside the solver: out = scale * g5 D in on the system's own
+// links, mu and scale (scale = 1 for the first hop of A, c for the second).
+// Vector selectors: 0 = u family, 1 = r family, 2 = scratch.  DOT: per-block
+// partials of <rt, out> into the system's partial buffer.
+template <typename R>
+__device__ __forceinline__ typename Ch<R>::T* select_vec(const SolverDev& d, int sel, int j) {
+    typename Ch<R>::T* base = sel == 0 ? Vec<R>::u(d) : (sel == 1 ? Vec<R>::r(d) : Vec<R>::tmp(d));
+    return base + (size_t)j * vstride<R>(d);
+}
+
+template <typename R, bool DOT>
+__global__ void __launch_bounds__(kThreads, hop_min_blocks<R>())
+k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2) {
+    const SolverDev& d = ds[blockIdx.y];
+    if (sys_idle(d, pass2)) return;
+    const int s = blockIdx.x * kThreads + threadIdx.x;
+    cx<R> dres[1] = {czero<R>()};
+    if (s < d.V) {
+        const double sc = second ? d.scale : 1.0;
+        SpinorView<R> in{select_vec<R>(d, in_sel, in_j), d.V};
+        SpinorView<R> out{select_vec<R>(d, out_sel, out_j), d.V};
+        cx<R> p[12];
+        hop_site<R, false, true>(d.g, Vec<R>::links(d), in, s, (R)(sc * d.diag), (R)(-0.5 * sc), (R)d.ef, (R)d.eb,
+                                 (R)d.bc, p);
+        out.store(s, p);
+        if (DOT) {
+            SpinorView<R> rt{Vec<R>::rt(d), d.V};
+            cx<R> q[12];
+            rt.load(s, q);
+            cx<R> a = czero<R>();
+#pragma unroll
+            for (int k = 0; k < 12; ++k) a = cjfma(q[k], p[k], a);
+            dres[0] = a;
+        }
+    }
+    if (DOT) block_reduce_store<1, R>(dres, d.part, 0);
 }
 
 // ------------------------------------------------------------------ single-block scalar kernels
@@ -388,7 +550,9 @@ __device__ __forceinline__ void fail(DevState* S, int code) {
 }
 
 // start of pass 1: partials hold <rt, r0> and |r0|^2 with r0 = rt = b
-__global__ void k_sc_init(SolverDev d, const double2* part, int nblk, double tol, double theta) {
+__global__ void k_sc_init(const SolverDev* __restrict__ ds, int nblk, double tol, double theta) {
+    const SolverDev& d = ds[blockIdx.x];
+    const double2* part = d.part;
     DevState* S = d.st;
     const dcx rtr = reduce_partials(part, 0, nblk);
     const dcx bb = reduce_partials(part, 1, nblk);
@@ -421,7 +585,9 @@ __global__ void k_sc_init(SolverDev d, const double2* part, int nblk, double tol
 }
 
 // beta of BiCG sub-step j >= 1 from partials of <rt, r_j>
-__global__ void k_sc_beta(SolverDev d, int j, const double2* part, int nblk) {
+__global__ void k_sc_beta(const SolverDev* __restrict__ ds, int j, int nblk) {
+    const SolverDev& d = ds[blockIdx.x];
+    const double2* part = d.part;
     DevState* S = d.st;
     if (S->done) return;
     const dcx rho1 = reduce_partials(part, 0, nblk);
@@ -436,7 +602,9 @@ __global__ void k_sc_beta(SolverDev d, int j, const double2* part, int nblk) {
 }
 
 // alpha of BiCG sub-step j from partials of <rt, u_{j+1}>, and the shift scalars
-__global__ void k_sc_alpha(SolverDev d, int j, const double2* part, int nblk) {
+__global__ void k_sc_alpha(const SolverDev* __restrict__ ds, int j, int nblk) {
+    const SolverDev& d = ds[blockIdx.x];
+    const double2* part = d.part;
     DevState* S = d.st;
     if (S->done) return;
     const dcx den = reduce_partials(part, 0, nblk);
@@ -478,7 +646,9 @@ __global__ void k_sc_alpha(SolverDev d, int j, const double2* part, int nblk) {
 // MR coefficients: gamma from the Gram partials (diagonally scaled normal
 // equations, pivoted elimination), then the shift polynomials p_s(-sigma), c_k.
 template <int L>
-__global__ void k_sc_mr(SolverDev d, const double2* part, int nblk) {
+__global__ void k_sc_mr(const SolverDev* __restrict__ ds, int nblk) {
+    const SolverDev& d = ds[blockIdx.x];
+    const double2* part = d.part;
     DevState* S = d.st;
     if (S->done) return;
     constexpr int NG = n_gram(L);
@@ -575,7 +745,9 @@ __global__ void k_sc_mr(SolverDev d, const double2* part, int nblk) {
 }
 
 // end of an outer iteration: convergence and freezing of shifts, next beta
-__global__ void k_sc_conv(SolverDev d, const double2* part, int nblk, int head) {
+__global__ void k_sc_conv(const SolverDev* __restrict__ ds, int nblk, int head) {
+    const SolverDev& d = ds[blockIdx.x];
+    const double2* part = d.part;
     DevState* S = d.st;
     if (S->done) return;
     const dcx rtr = reduce_partials(part, 0, nblk);
@@ -611,15 +783,69 @@ __global__ void k_sc_conv(SolverDev d, const double2* part, int nblk, int head) 
     d.rec_beta[(m + 1) * d.L] = pk(beta);
 }
 
+// ------------------------------------------------------------------ reliable update
+// r_0 <- b - A x with A x (FP64) already in ax; the new r_0 is rounded to R.
+// Rewrites the partials of <rt, r_0> (slot 0) and |r_0|^2 (slot 1) that the
+// convergence kernel reads, grid-stride like k_mr.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_reliable(const SolverDev* __restrict__ ds, const double2* ax, int pass2) {
+    const SolverDev& d = ds[blockIdx.y];
+    if (sys_idle(d, pass2)) return;
+    typename Ch<R>::T* r0 = Vec<R>::r(d);
+    const typename Ch<R>::T* rt = Vec<R>::rt(d);
+    cx<R> dots[2] = {czero<R>(), czero<R>()};
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < d.V; s += gridDim.x * kThreads) {
+#pragma unroll
+        for (int q = 0; q < Ch<R>::N; ++q) {
+            Ch<R> v;
+#pragma unroll
+            for (int w = 0; w < Ch<R>::W; ++w) {
+                const size_t k = (size_t)(q * Ch<R>::W + w) * d.V + s;
+                const double2 bb = d.b64[k], aa = ax[k];
+                v.c[w] = {(R)__dsub_rn(bb.x, aa.x), (R)__dsub_rn(bb.y, aa.y)};
+            }
+            v.stv(r0, q, d.V, s);
+            Ch<R> tv = Ch<R>::ld(rt, q, d.V, s);
+#pragma unroll
+            for (int w = 0; w < Ch<R>::W; ++w) {
+                dots[0] = cjfma(tv.c[w], v.c[w], dots[0]);
+                dots[1].r = fmaR(v.c[w].r, v.c[w].r, dots[1].r);
+                dots[1].r = fmaR(v.c[w].i, v.c[w].i, dots[1].r);
+            }
+        }
+    }
+    block_reduce_store<2, R>(dots, d.part, gridDim.x);
+}
+
 // ------------------------------------------------------------------ pseudo-double-pass gather
 // y += sum_{m in [m_begin, m_end)} sum_k coef[m][k] v(m, k), the stored seed-vector
 // occurrences of pass 1 (store slot (m - m0) * NC + k).  Terms are summed in R
 // in groups of four, each group added to y in FP64.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_gather(SolverDev d, const typename Ch<R>::T* store, size_t vs, int m_begin, int m_end, int m0, double2* y) {
+k_gather(const SolverDev* __restrict__ ds) {
+    const SolverDev& d = ds[blockIdx.y];
     const int s = blockIdx.x * kThreads + threadIdx.x;
     if (s >= d.V) return;
+    const int M = d.st->n_outer;
+    int m_begin, m_end, m0;
+    const typename Ch<R>::T* store;
+    if (sizeof(R) == 8) {
+        m_begin = 0;
+        m_end = min(M, d.cap64);
+        if (d.m0_32 >= 0) m_end = min(m_end, d.m0_32);
+        m0 = 0;
+        store = reinterpret_cast<const typename Ch<R>::T*>(d.store64);
+    } else {
+        if (d.m0_32 < 0) return;
+        m_begin = d.m0_32;
+        m_end = min(M, d.m0_32 + d.cap32);
+        m0 = d.m0_32;
+        store = reinterpret_cast<const typename Ch<R>::T*>(d.store32);
+    }
+    if (m_end <= m_begin) return;
+    const size_t vs = vstride<R>(d);
+    double2* y = d.y;
     const int NC = nc_slots(d.L);
     const int n = (m_end - m_begin) * NC;
     const double2* cf = d.coef + (size_t)m_begin * NC;
@@ -659,8 +885,21 @@ k_gather(SolverDev d, const typename Ch<R>::T* store, size_t vs, int m_begin, in
 }
 
 // pass 2: advance the outer-iteration counter
-__global__ void k_advance(SolverDev d) { d.st->m += 1; }
-__global__ void k_set_m(SolverDev d, int m) { d.st->m = m; d.st->done = 0; }
+__global__ void k_advance(const SolverDev* __restrict__ ds) {
+    DevState* S = ds[blockIdx.x].st;
+    if (S->m < S->n_outer) S->m += 1;
+}
+// pass 2 starts at outer iteration min(m, M) of each system
+__global__ void k_set_m(const SolverDev* __restrict__ ds, int m) {
+    DevState* S = ds[blockIdx.x].st;
+    S->m = m < S->n_outer ? m : S->n_outer;
+    S->done = 0;
+}
+// done flag of every system (polled by the host)
+__global__ void k_flags(const SolverDev* __restrict__ ds, int n, int* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ds[i].st->done;
+}
 
 // ------------------------------------------------------------------ backward sweep
 // One thread per shift walks its recorded linear operations backwards
@@ -669,7 +908,8 @@ __global__ void k_set_m(SolverDev d, int m) { d.st->m = m; d.st->done = 0; }
 // occurrence is that occurrence's weight in x_s.  The weighted sum over shifts
 // is formed by k_coef_reduce.
 template <int L>
-__global__ void k_sweep(SolverDev d) {
+__global__ void k_sweep(const SolverDev* __restrict__ ds) {
+    const SolverDev& d = ds[blockIdx.y];
     const int sh = blockIdx.x * blockDim.x + threadIdx.x;
     if (sh >= d.ns) return;
     constexpr int NC = nc_slots(L);
@@ -721,7 +961,9 @@ __global__ void k_sweep(SolverDev d) {
 }
 
 // coef[m][k] = sum_s omega_s cs[s][m][k] for m < M (fixed order over s)
-__global__ void k_coef_reduce(SolverDev d, int M) {
+__global__ void k_coef_reduce(const SolverDev* __restrict__ ds) {
+    const SolverDev& d = ds[blockIdx.y];
+    const int M = d.st->n_outer;
     const int NC = nc_slots(d.L);
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * NC) return;
@@ -732,6 +974,21 @@ __global__ void k_coef_reduce(SolverDev d, int M) {
         a = a + d.omega[sh] * ld(d.cs[((size_t)sh * d.max_outer + m) * NC + k]);
     }
     d.coef[(size_t)m * NC + k] = pk(a);
+}
+
+// single-pass result y = sum_s omega_s x_s (FP64 [12][V]) of each system
+__global__ void k_combine_sys(const SolverDev* __restrict__ ds) {
+    const SolverDev& d = ds[blockIdx.y];
+    const int idx = blockIdx.x * kThreads + threadIdx.x;
+    if (idx >= 12 * d.V) return;
+    const size_t svs = (size_t)12 * d.V;
+    double a = 0.0, b = 0.0;
+    for (int sh = 0; sh < d.ns; ++sh) {
+        const double2 v = d.xs[sh * svs + idx];
+        a = __fma_rn(d.omega[sh], v.x, a);
+        b = __fma_rn(d.omega[sh], v.y, b);
+    }
+    d.y[idx] = make_double2(a, b);
 }
 
 // single-pass result y = sum_s omega_s x_s (FP64 [12][V])

@@ -1,0 +1,118 @@
+"""Batched multi-shift solves (fa_apply_f_batched) and CUDA-graph replay.
+
+Systems of one lattice shape share every kernel launch; each keeps its own
+gauge field (or shares one), mu, scale, poles, scalars and convergence.  The
+batched result of every system must equal the one-at-a-time solve of the same
+system (same kernels, same per-system reductions), and match the oracle."""
+import numpy as np
+import pytest
+
+import inputs
+import paper_1010_2592_gb300 as fa
+from fa_cases import oracle_double, rel, to_dev, to_host, workload_case
+from oracle import dirac, scale
+
+pytestmark = pytest.mark.gpu
+
+
+def lattice_systems(dims, gauge_seed, mu, sources, stream=None, poles=10):
+    """One owner context with the gauge field and one context per source sharing it."""
+    U = inputs.su3_exp_gauge(dims, 0.5, gauge_seed)
+    c = scale.power_scale(dirac.Operator(U, -1.8, mu).A, inputs.gaussian_spinor(dims, gauge_seed + 3), 100)
+    om, sg = fa.neuberger_poles(poles)
+    owner = fa.Context(dims, stream)
+    owner.set_gauge(to_dev(U))
+    ctxs = []
+    for k in range(len(sources)):
+        ctx = owner if k == 0 else fa.Context(dims, stream)
+        if k > 0:
+            ctx.share_gauge(owner)
+        ctx.set_params(-1.8, mu, -1, c)
+        ctx.set_poles(om, sg)
+        ctxs.append(ctx)
+    return ctxs, [to_dev(s) for s in sources], (U, c, om, sg)
+
+
+def build_batch(stream=None):
+    d1, d2 = (4, 4, 4, 8), (3, 3, 3, 6)
+    srcs1 = [inputs.point_source(d1, 0, 0), inputs.point_source(d1, 2, 1), inputs.gaussian_spinor(d1, 9)]
+    srcs2 = [inputs.gaussian_spinor(d2, 11), inputs.point_source(d2, 3, 2)]
+    srcs3 = [inputs.gaussian_spinor(d1, 12)]
+    a, ba, ia = lattice_systems(d1, 301, 0.05, srcs1, stream)
+    b, bb, ib = lattice_systems(d2, 302, 0.12, srcs2, stream)
+    c, bc, ic = lattice_systems(d1, 303, 0.18, srcs3, stream)
+    # interleave shapes on purpose: the batch groups them itself
+    ctxs = [a[0], b[0], a[1], c[0], b[1], a[2]]
+    srcs = [ba[0], bb[0], ba[1], bc[0], bb[1], ba[2]]
+    return ctxs, srcs, (a, b, c)
+
+
+@pytest.mark.parametrize("mode,precision", [("double", "f64"), ("pseudo", "f64"), ("single", "f64"),
+                                            ("double", "f32"), ("pseudo", "f32")])
+def test_batched_equals_one_at_a_time(mode, precision):
+    ctxs, srcs, _ = build_batch()
+    kw = dict(ell=2, tol=1e-10, mode=mode, precision=precision)
+    ys, stats = fa.apply_f_batched(ctxs, srcs, **kw)
+    for i, (ctx, b) in enumerate(zip(ctxs, srcs)):
+        r = ctx.apply_f(b, **kw)
+        assert np.array_equal(to_host(ys[i]), to_host(r.y)), i
+        assert stats[i]["outer_iters"] == r.stats["outer_iters"]
+        assert stats[i]["iters_per_shift"] == r.stats["iters_per_shift"]
+
+
+def test_batched_against_oracle():
+    ctxs, srcs, (a, _, _) = build_batch()
+    ys, _ = fa.apply_f_batched(ctxs, srcs, ell=2, tol=1e-10, mode="pseudo", precision="f64")
+    d1 = (4, 4, 4, 8)
+    U = inputs.su3_exp_gauge(d1, 0.5, 301)
+    c = scale.power_scale(dirac.Operator(U, -1.8, 0.05).A, inputs.gaussian_spinor(d1, 304), 100)
+    om, sg = fa.neuberger_poles(10)
+    from oracle import msbicgstab as ms
+    op = dirac.Operator(U, -1.8, 0.05, c)
+    y_o = ms.multishift_double(op.A, inputs.gaussian_spinor(d1, 9), sg, om, 2, 1e-10)
+    assert rel(to_host(ys[5]), y_o) < 1e-10
+
+
+@pytest.mark.parametrize("mode,precision", [("double", "f64"), ("pseudo", "mixed"), ("double", "f32")])
+def test_graph_replay_equals_direct_launches(mode, precision):
+    import torch
+    w = workload_case("wilson_4x4x4x8")
+    stream = torch.cuda.Stream()
+    ctx = fa.Context(w["dims"], stream)
+    ctx.set_gauge(to_dev(w["U"]))
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], w["c"])
+    ctx.set_poles(w["omega"], w["sigma"])
+    with torch.cuda.stream(stream):
+        b = to_dev(w["b"])
+    stream.synchronize()
+    kw = dict(ell=2, tol=1e-10, mode=mode, precision=precision)
+    r0 = ctx.apply_f(b, **kw)
+    r1 = ctx.apply_f(b, graph=True, **kw)
+    r2 = ctx.apply_f(b, graph=True, **kw)
+    stream.synchronize()
+    assert np.array_equal(to_host(r0.y), to_host(r1.y))
+    assert np.array_equal(to_host(r1.y), to_host(r2.y))
+    assert r1.stats["outer_iters"] == r0.stats["outer_iters"]
+    y_o, _ = oracle_double("wilson_4x4x4x8", None, 2, 1e-12)
+    tol = {"f64": 1e-9, "mixed": 1e-8, "f32": 1e-6}[precision]
+    assert rel(to_host(r1.y), y_o) < tol
+
+
+def test_batched_graph_mode():
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctxs, srcs, _ = build_batch(stream)
+    stream.synchronize()
+    ys0, _ = fa.apply_f_batched(ctxs, srcs, ell=2, tol=1e-10, mode="pseudo", precision="f32")
+    ys1, _ = fa.apply_f_batched(ctxs, srcs, ell=2, tol=1e-10, mode="pseudo", precision="f32", graph=True)
+    stream.synchronize()
+    for a, b in zip(ys0, ys1):
+        assert np.array_equal(to_host(a), to_host(b))
+
+
+def test_batch_rejects_mixed_precision_for_several_systems():
+    ctxs, srcs, _ = build_batch()
+    with pytest.raises(fa.FAError) as e:
+        fa.apply_f_batched(ctxs[:3], srcs[:3], ell=2, precision="mixed")
+    assert e.value.status == fa.FA_EINVAL

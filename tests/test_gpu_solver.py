@@ -208,3 +208,26 @@ def test_pseudo_double_pass_partial_store(precision):
     assert 0 < K < M
     assert r.stats["n_mv"] == 2 * 2 * M + 2 * 2 * (M - K)   # pass 1 + regenerated remainder
     assert rel(to_host(r.y), y_o) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "mixed"])
+def test_reliable_updates(precision):
+    """r_0 replaced by the FP64 true residual b - A x every 5 outer iterations
+    (and replayed in pass 2): the result still matches the oracle, and the
+    double-pass and pseudo-double-pass forms (full and partial store) agree."""
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    b = to_dev(w["b"])
+    y_o, _ = oracle_double(C1, None, 2, 1e-12 if precision != "f64" else 1e-10)
+    kw = dict(ell=2, tol=1e-10, precision=precision, reliable_every=5)
+    rd = ctx.apply_f(b, mode="double", **kw)
+    rp = ctx.apply_f(b, mode="pseudo", **kw)
+    per64 = 5 * 512 * 192 / 1e9
+    rq = ctx.apply_f(b, mode="pseudo", store_gb=6.5 * per64, **kw)
+    assert 0 < rq.stats["stored_outer"] < rq.stats["outer_iters"]
+    for r in (rd, rp, rq):
+        assert rel(to_host(r.y), y_o) < tol_for(precision, 2)
+    assert rel(to_host(rp.y), to_host(rd.y)) < (1e-13 if precision == "f64" else 1e-7)
+    assert rel(to_host(rq.y), to_host(rd.y)) < (1e-13 if precision == "f64" else 1e-7)
+    with pytest.raises(fa.FAError):
+        fa.apply_f_batched([ctx, ctx_for(w)], [b, b], ell=2, precision="f64", reliable_every=5)
