@@ -58,6 +58,8 @@ def parse():
                    help="time D_w sweeps alone (FP32 and FP64) on --dims, for profiling")
     p.add_argument("--dims", type=int, nargs=4, default=None)
     p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--head", default="mixed_df", choices=["mixed_df", "mixed"],
+                   help="precision of the head of the headline solve: double-float or FP64")
     p.add_argument("--store-gb", type=float, default=0.0,
                    help="pseudo-double-pass store budget (0: the library default)")
     return p.parse_args()
@@ -202,7 +204,7 @@ def run_hop_only(args):
     ctx.set_params(w["mass"], w["mu"], w["t_bc"], 1.0)
     x = torch.from_numpy(w["b"]).cuda()
     out = {}
-    for prec, bytes_site in (("f32", 384.0), ("f64", 960.0)):
+    for prec, bytes_site in (("f32", 384.0), ("f64", 960.0), ("df", 960.0)):
         ctx.hop_timing_reset()
         y = ctx.empty_spinor()
         torch.cuda.synchronize()
@@ -215,11 +217,12 @@ def run_hop_only(args):
         ms_call = s.elapsed_time(e) / args.reps
         out[prec] = {"ms_per_apply_dw_call_incl_pack": ms_call}
     # the hop kernel alone: time a solve-free loop of hop launches via the solver's instrumentation
-    for prec in ("f32", "f64"):
+    solver_prec = {"f32": "f32", "f64": "f64", "df": "mixed_df"}
+    for prec in ("f32", "f64", "df"):
         ctx.hop_timing_reset()
         ctx.set_poles(*fa.neuberger_poles(4))
         ctx.apply_f(x, ell=1, tol=1e-30, max_outer=max(1, args.reps // 4), mode="double",
-                    precision=prec, hop_timing=True, check=False)
+                    precision=solver_prec[prec], switch_resid=1e-300, hop_timing=True, check=False)
         ms, n = ctx.hop_timing(prec)
         bsite = 384.0 if prec == "f32" else 960.0
         out[prec].update(hop_mean_ms=ms, hop_launches=n, hop_gbs=bsite * V / (ms * 1e-3) / 1e9 if ms else None)
@@ -344,8 +347,10 @@ def main():
         return (torch.linalg.vector_norm(y - yref) / yref_norm).item()
 
     variants = {
-        "pseudo_mixed": dict(mode="pseudo", precision="mixed", switch_resid=args.switch_resid, graph=True,
+        "pseudo_mixed": dict(mode="pseudo", precision=args.head, switch_resid=args.switch_resid, graph=True,
                              store_gb=args.store_gb),
+        "pseudo_mixed_fp64head": dict(mode="pseudo", precision="mixed", switch_resid=args.switch_resid, graph=True,
+                                      store_gb=args.store_gb),
         "double_mixed": dict(mode="double", precision="mixed", switch_resid=args.switch_resid),
         "double_f64": dict(mode="double", precision="f64"),
         "single_f64": dict(mode="single", precision="f64"),
@@ -354,6 +359,8 @@ def main():
     chosen = {}
     if args.quick:
         variants = {"pseudo_mixed": variants["pseudo_mixed"]}
+    if args.head == "mixed":
+        variants.pop("pseudo_mixed_fp64head", None)
     for name, kw in variants.items():
         if args.quick:
             r = ctx.apply_f(b, ell=ell, tol=1e-9, max_outer=4000, **kw)
@@ -414,10 +421,12 @@ def main():
         ms_step = t.item()
     hop32_ms, hop32_n = ctx.hop_timing("f32")
     hop64_ms, hop64_n = ctx.hop_timing("f64")
+    hopdf_ms, hopdf_n = ctx.hop_timing("df")
 
     # comparison variants (fewer steps)
     other = {}
-    for name in ([] if args.quick else ["double_mixed", "double_f64", "single_f64", "double_f32"]):
+    for name in ([] if args.quick else ["pseudo_mixed_fp64head", "double_mixed", "double_f64", "single_f64",
+                                        "double_f32"]):
         k = max(1, min(args.steps, 3))
         lst, _, res = timed(name, k, 1)
         tol, e, _ = chosen[name]
@@ -432,7 +441,7 @@ def main():
 
     if args.quick:
         print(json.dumps({"mode": "quick", "ms_per_solve": ms_step, "variant": other["pseudo_mixed"],
-                          "hop_f32_ms": hop32_ms, "hop_f64_ms": hop64_ms,
+                          "hop_f32_ms": hop32_ms, "hop_f64_ms": hop64_ms, "hop_df_ms": hopdf_ms,
                           "hop_f32_gbs": 384.0 * V / (hop32_ms * 1e-3) / 1e9 if hop32_ms else None,
                           "launches_per_solve": head_launches // max(1, args.steps), "clocks": clk}),
               flush=True)
@@ -485,7 +494,21 @@ def main():
               "frac": (hop64_tflops / 1.25) if hop64_tflops else None, "traffic": None,
               "peak_source": "nominal GB300 FP64 (no measured FP64 peak)", "algorithmic_flops_per_launch": hop64_flops,
               "mean_launch_ms": hop64_ms, "launches_timed": hop64_n, "total_ms": hop64_ms * hop64_n}
-    dominant64 = roof64["total_ms"] > roof32["total_ms"]
+    #   double-float hop: ALU-bound on the FP32 pipes; 15,400 FP32 instructions per
+    #   site counted from the source (8 hops x (24 double-float adds of 11 instructions
+    #   in the projection + 6 x (one complex product, 50, + two complex fma, 72 each)
+    #   + 36 adds in the reconstruction) + 2 time-weight scalings of 84 + centre 600),
+    #   against 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3 T instructions/s.
+    hopdf_instr = 15400.0 * V
+    hopdf_t = hopdf_instr / (hopdf_ms * 1e-3) / 1e12 if hopdf_ms > 0 else None
+    roofdf = {"kernel": "hop_kernel<df> (one D_w sweep, double-float head)", "bound": "alu",
+              "measured_over": over, "achieved": hopdf_t, "peak": 40.3, "unit": "T FP32-instructions/s",
+              "frac": (hopdf_t / 40.3) if hopdf_t else None, "traffic": None,
+              "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal)",
+              "algorithmic_instructions_per_launch": hopdf_instr, "mean_launch_ms": hopdf_ms,
+              "launches_timed": hopdf_n, "total_ms": hopdf_ms * hopdf_n}
+    roofs = [roof32, roof64, roofdf]
+    dominant = max(roofs, key=lambda r: r["total_ms"])
 
     line = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": ws, "steps": args.steps,
@@ -495,9 +518,10 @@ def main():
         "variants": other,
         "speedup_vs_single_f64": other["single_f64"]["ms"] / ms_step,
         "speedup_vs_double_f64": other["double_f64"]["ms"] / ms_step,
-        "roofline": roof64 if dominant64 else roof32,
+        "roofline": dominant,
         "roofline_hop_f32": roof32,
         "roofline_hop_f64": roof64,
+        "roofline_hop_df": roofdf,
         "stencil_gbs": achieved,
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": int(b_pin.numel() * 16),
                 "d2h_bytes_per_step": int(y_pin.numel() * 16), "rel_err": e2e_err},

@@ -23,8 +23,9 @@ LIB_PATH = os.path.join(_HERE, "libfapath.so")
 FA_OK, FA_EINVAL, FA_ENOMEM, FA_ECUDA, FA_EBREAKDOWN, FA_ENOCONV, FA_ENONFINITE, FA_ETIMEOUT, \
     FA_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 SINGLE, DOUBLE, PSEUDO = 0, 1, 2
-F64, F32, MIXED = 0, 1, 2
-_PREC = {"f64": F64, "f32": F32, "mixed": MIXED, F64: F64, F32: F32, MIXED: MIXED}
+F64, F32, MIXED, DF, MIXED_DF = 0, 1, 2, 3, 4
+_PREC = {"f64": F64, "f32": F32, "mixed": MIXED, "df": DF, "mixed_df": MIXED_DF,
+         F64: F64, F32: F32, MIXED: MIXED, DF: DF, MIXED_DF: MIXED_DF}
 _MODE = {"single": SINGLE, "double": DOUBLE, "pseudo": PSEUDO, SINGLE: SINGLE, DOUBLE: DOUBLE,
          PSEUDO: PSEUDO}
 

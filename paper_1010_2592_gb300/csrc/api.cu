@@ -104,6 +104,7 @@ int fa_set_gauge(fa_ctx* c, const double* U, int on_device) {
     const size_t canon_bytes = (size_t)V * 72 * sizeof(double);
     CUDA_OR(c->links64.ensure((size_t)36 * V * sizeof(double2)), "fa_set_gauge: alloc FP64 links");
     CUDA_OR(c->links32.ensure((size_t)12 * V * sizeof(float4)), "fa_set_gauge: alloc FP32 links");
+    CUDA_OR(c->linksdf.ensure((size_t)36 * V * sizeof(float4)), "fa_set_gauge: alloc double-float links");
     const double* src = U;
     DevBuf stage;
     if (!on_device) {
@@ -111,7 +112,8 @@ int fa_set_gauge(fa_ctx* c, const double* U, int on_device) {
         CUDA_OR(cudaMemcpyAsync(stage.p, U, canon_bytes, cudaMemcpyHostToDevice, c->stream), "fa_set_gauge: copy");
         src = stage.as<double>();
     }
-    TRY(launch_pack_links(c->g, src, c->links64.as<double2>(), c->links32.as<float4>(), c->stream));
+    TRY(launch_pack_links(c->g, src, c->links64.as<double2>(), c->links32.as<float4>(), c->linksdf.as<float4>(),
+                          c->stream));
     c->launches++;
     CUDA_OR(cudaStreamSynchronize(c->stream), "fa_set_gauge: sync");
     c->links_owner = nullptr;
@@ -127,6 +129,7 @@ int fa_share_gauge(fa_ctx* c, const fa_ctx* owner) {
         return FA_EINVAL;
     c->links64.release();
     c->links32.release();
+    c->linksdf.release();
     c->links_owner = owner;
     c->have_gauge = true;
     return FA_OK;
@@ -213,6 +216,21 @@ static int apply_op(fa_ctx* c, const double* in, double* out, int dagger, int pr
             TRY(hop_f32(c, a, o, 1.0, dg, dg, dg, nullptr, nullptr, nullptr));
         }
         TRY(launch_unpack_spinor_f32(c->g, o, out, st));
+    } else if (precision == FA_DF) {
+        const size_t b = (size_t)12 * V * sizeof(float4);
+        CUDA_OR(c->io64a.ensure(b), "alloc");
+        CUDA_OR(c->io64b.ensure(b), "alloc");
+        float4 *a = c->io64a.as<float4>(), *o = c->io64b.as<float4>();
+        TRY(launch_pack_spinor_df(c->g, in, a, st));
+        if (is_A) {
+            CUDA_OR(c->tmp64.ensure(b), "alloc");
+            float4* t = c->tmp64.as<float4>();
+            TRY(hop_df(c, a, t, 1.0, false, true, dg, nullptr, nullptr, nullptr));
+            TRY(hop_df(c, t, o, c->scale_c, false, true, dg, nullptr, nullptr, nullptr));
+        } else {
+            TRY(hop_df(c, a, o, 1.0, dg, dg, dg, nullptr, nullptr, nullptr));
+        }
+        TRY(launch_unpack_spinor_df(c->g, o, out, st));
     } else {
         return FA_EINVAL;
     }
@@ -312,8 +330,9 @@ int fa_sync(fa_ctx* c) {
 long long fa_launch_count(const fa_ctx* c) { return c ? c->launches : -1; }
 
 int fa_hop_timing(const fa_ctx* c, int precision, double* mean_ms, long long* count) {
-    if (!c || !mean_ms || !count || (precision != FA_F64 && precision != FA_F32)) return FA_EINVAL;
-    const int k = precision == FA_F64 ? 0 : 1;
+    if (!c || !mean_ms || !count || (precision != FA_F64 && precision != FA_F32 && precision != FA_DF))
+        return FA_EINVAL;
+    const int k = precision == FA_F64 ? 0 : (precision == FA_F32 ? 1 : 2);
     *count = c->hop_count[k];
     *mean_ms = c->hop_count[k] ? c->hop_ms[k] / (double)c->hop_count[k] : 0.0;
     return FA_OK;
@@ -321,8 +340,8 @@ int fa_hop_timing(const fa_ctx* c, int precision, double* mean_ms, long long* co
 
 int fa_hop_timing_reset(fa_ctx* c) {
     if (!c) return FA_EINVAL;
-    c->hop_ms[0] = c->hop_ms[1] = 0.0;
-    c->hop_count[0] = c->hop_count[1] = 0;
+    c->hop_ms[0] = c->hop_ms[1] = c->hop_ms[2] = 0.0;
+    c->hop_count[0] = c->hop_count[1] = c->hop_count[2] = 0;
     return FA_OK;
 }
 

@@ -41,6 +41,11 @@ hop_kernel(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, 
     if (DOT) block_reduce_store<1, R>(dres, partials, 0);
 }
 
+static df fromdbl_host(double x) {
+    const float h = (float)x;
+    return df(h, (float)(x - (double)h));
+}
+
 template <typename R, typename LP, typename SP>
 static int launch_hop_t(const Geom& g, const LP* links, const SP* in, SP* out, double diag, double ef,
                         double eb, double t_bc, double scale, bool g5in, bool g5out, const SP* dot_with,
@@ -69,6 +74,28 @@ int launch_hop_f64(const Geom& g, const double2* links, const double2* in, doubl
                    const double2* dot_with, double2* partials, const int* done, cudaStream_t st) {
     return launch_hop_t<double>(g, links, in, out, diag, ef, eb, t_bc, scale, g5in, g5out, dot_with,
                                 partials, done, st);
+}
+
+int launch_hop_df(const Geom& g, const float4* links, const float4* in, float4* out, double diag, double ef,
+                  double eb, double t_bc, double scale, bool g5in, bool g5out, const float4* dot_with,
+                  double2* partials, const int* done, cudaStream_t st) {
+    LinkView<df> U{links, g.V};
+    SpinorView<df> vin{const_cast<float4*>(in), g.V};
+    SpinorView<df> vout{out, g.V};
+    SpinorView<df> vd{const_cast<float4*>(dot_with), g.V};
+    const df cdiag = fromdbl_host(scale * diag), chop = fromdbl_host(-0.5 * scale);
+    const df ref = fromdbl_host(ef), reb = fromdbl_host(eb), rbc = fromdbl_host(t_bc);
+    const int nb = nblocks(g.V);
+    const bool dot = dot_with != nullptr;
+#define FA_HOPD(A, B, C) hop_kernel<df, A, B, C><<<nb, kThreads, 0, st>>>(g, U, vin, vout, cdiag, chop, ref, reb, rbc, vd, partials, done)
+    if (!g5in && !g5out && !dot) FA_HOPD(false, false, false);
+    else if (!g5in && g5out && !dot) FA_HOPD(false, true, false);
+    else if (!g5in && g5out && dot) FA_HOPD(false, true, true);
+    else if (g5in && g5out && !dot) FA_HOPD(true, true, false);
+    else if (!g5in && !g5out && dot) FA_HOPD(false, false, true);
+    else return FA_EINVAL;
+#undef FA_HOPD
+    return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA;
 }
 
 int launch_hop_f32(const Geom& g, const float4* links, const float4* in, float4* out, double diag,
@@ -222,8 +249,14 @@ __global__ void convert_f64_f32_kernel(int V, const double2* __restrict__ in, fl
 }
 
 // canonical links: double [V][4][3][3][2]
+__device__ __forceinline__ float4 to_df4(double2 v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, __double2float_rn(__dsub_rn(v.x, (double)rh)), ih,
+                       __double2float_rn(__dsub_rn(v.y, (double)ih)));
+}
+
 __global__ void pack_links_kernel(int V, const double2* __restrict__ canon, double2* __restrict__ l64,
-                                  float4* __restrict__ l32) {
+                                  float4* __restrict__ l32, float4* __restrict__ ldf) {
     const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = mu*V + s
     if (idx >= 4 * V) return;
     const int mu = idx / V, s = idx - mu * V;
@@ -233,6 +266,10 @@ __global__ void pack_links_kernel(int V, const double2* __restrict__ canon, doub
     for (int k = 0; k < 9; ++k) e[k] = src[k];
 #pragma unroll
     for (int k = 0; k < 9; ++k) l64[((size_t)mu * 9 + k) * V + s] = e[k];
+    if (ldf != nullptr) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ldf[((size_t)mu * 9 + k) * V + s] = to_df4(e[k]);
+    }
     if (l32 != nullptr) {
 #pragma unroll
         for (int q = 0; q < 3; ++q)
@@ -260,8 +297,45 @@ int launch_unpack_spinor_f32(const Geom& g, const float4* in, double* canon, cud
     unpack_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, in, (double2*)canon);
     return last_status();
 }
-int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, cudaStream_t st) {
-    pack_links_kernel<<<grid_for((size_t)4 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, l64, l32);
+int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, float4* ldf, cudaStream_t st) {
+    pack_links_kernel<<<grid_for((size_t)4 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, l64, l32, ldf);
+    return last_status();
+}
+
+__global__ void pack_df_kernel(int V, const double2* __restrict__ canon, float4* __restrict__ out) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = k*V + s
+    if (idx >= 12 * V) return;
+    const int k = idx / V, s = idx - k * V;
+    out[idx] = to_df4(canon[(size_t)s * 12 + k]);
+}
+
+__global__ void unpack_df_kernel(int V, const float4* __restrict__ in, double2* __restrict__ canon) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = 12*s + k
+    if (idx >= 12 * V) return;
+    const int s = idx / 12, k = idx - s * 12;
+    const float4 a = in[(size_t)k * V + s];
+    canon[idx] = make_double2(__dadd_rn((double)a.x, (double)a.y), __dadd_rn((double)a.z, (double)a.w));
+}
+
+// double-float -> FP32 ([12][V] float4 -> [6][V] float4): hi + lo rounded once
+__global__ void convert_df_f32_kernel(int V, const float4* __restrict__ in, float4* __restrict__ out) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;   // idx = q*V + s
+    if (idx >= 6 * V) return;
+    const int q = idx / V, s = idx - q * V;
+    const float4 a = in[(size_t)(2 * q) * V + s], b = in[(size_t)(2 * q + 1) * V + s];
+    out[idx] = make_float4(__fadd_rn(a.x, a.y), __fadd_rn(a.z, a.w), __fadd_rn(b.x, b.y), __fadd_rn(b.z, b.w));
+}
+
+int launch_pack_spinor_df(const Geom& g, const double* canon, float4* out, cudaStream_t st) {
+    pack_df_kernel<<<grid_for((size_t)12 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, out);
+    return last_status();
+}
+int launch_unpack_spinor_df(const Geom& g, const float4* in, double* canon, cudaStream_t st) {
+    unpack_df_kernel<<<grid_for((size_t)12 * g.V), kThreads, 0, st>>>(g.V, in, (double2*)canon);
+    return last_status();
+}
+int launch_convert_df_to_f32(const Geom& g, const float4* in, float4* out, cudaStream_t st) {
+    convert_df_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, in, out);
     return last_status();
 }
 int launch_convert_f64_to_f32(const Geom& g, const double2* in, float4* out, cudaStream_t st) {

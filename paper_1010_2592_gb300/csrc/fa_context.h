@@ -56,7 +56,7 @@ struct fa_ctx {
     int device = 0;
 
     // gauge field (own packed copy, or the packed copy of another context)
-    fa::DevBuf links64, links32;
+    fa::DevBuf links64, links32, linksdf;
     const fa_ctx* links_owner = nullptr;
     bool have_gauge = false;
     // operator parameters
@@ -89,8 +89,8 @@ struct fa_ctx {
 
     long long launches = 0;
     // hop-kernel timing (index 0: FP64, 1: FP32)
-    double hop_ms[2] = {0.0, 0.0};
-    long long hop_count[2] = {0, 0};
+    double hop_ms[3] = {0.0, 0.0, 0.0};   // FP64, FP32, double-float
+    long long hop_count[3] = {0, 0, 0};
     bool hop_timing = false;
     std::vector<cudaEvent_t> hop_ev;     // start/stop pairs, reused across solves
     std::vector<int> hop_ev_kind;        // precision index of each recorded pair
@@ -104,11 +104,16 @@ inline const double2* links64_of(const fa_ctx* c) {
 inline const float4* links32_of(const fa_ctx* c) {
     return c->links_owner ? c->links_owner->links32.as<float4>() : c->links32.as<float4>();
 }
+inline const float4* linksdf_of(const fa_ctx* c) {
+    return c->links_owner ? c->links_owner->linksdf.as<float4>() : c->linksdf.as<float4>();
+}
 // operator application on internal layouts (used by the C-ABI and the solver)
 int hop_f64(fa_ctx* c, const double2* in, double2* out, double scale, bool g5in, bool g5out, bool dagger_mu,
             const double2* dot_with, double2* partials, const int* done);
 int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, bool g5out, bool dagger_mu,
             const float4* dot_with, double2* partials, const int* done);
+int hop_df(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, bool g5out, bool dagger_mu,
+           const float4* dot_with, double2* partials, const int* done);
 int solve(fa_ctx* c, const double* b_canon, double* y_canon, double* const* xs_canon,
           const fa_solver_params* p, fa_solver_stats* stats);
 int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y_canon,

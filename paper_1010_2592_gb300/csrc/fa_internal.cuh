@@ -38,6 +38,58 @@ __device__ __forceinline__ double addR(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ float subR(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double subR(double a, double b) { return __dsub_rn(a, b); }
 
+// ------------------------------------------------------------------ double-float
+// A "double-float" value is the unevaluated sum hi + lo of two FP32 numbers
+// with |lo| <= ulp(hi)/2: about 44-48 significant bits computed on the FP32
+// pipes (GB300 runs FP32 at many times its FP64 rate).  Sums use Knuth's
+// TwoSum (the exact rounding error of an addition) and products Dekker's
+// TwoProduct in its FMA form (e = fma(a, b, -a*b) is exact); the result is
+// renormalised with Fast-TwoSum.  Additions use the short form (one TwoSum on
+// the high parts): the error is about 2^-44 of the larger operand.
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(float h, float l = 0.0f) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df addR(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df subR(df a, df b) { return addR(a, df(-b.hi, -b.lo)); }
+__device__ __forceinline__ df mulR(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df fmaR(df a, df b, df c) { return addR(mulR(a, b), c); }
+__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator+(df a, df b) { return addR(a, b); }
+__device__ __forceinline__ df operator-(df a, df b) { return subR(a, b); }
+// sign factors of the projectors (exact)
+__device__ __forceinline__ df operator*(int s, df a) { return {(float)s * a.hi, (float)s * a.lo}; }
+
+// conversions between the working precisions and FP64
+__device__ __forceinline__ double todbl(float x) { return (double)x; }
+__device__ __forceinline__ double todbl(double x) { return x; }
+__device__ __forceinline__ double todbl(df x) { return __dadd_rn((double)x.hi, (double)x.lo); }
+template <typename R> __device__ __forceinline__ R fromdbl(double x) { return (R)x; }
+template <> __device__ __forceinline__ df fromdbl<df>(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(__dsub_rn(x, (double)h))};
+}
+
 template <typename R> __device__ __forceinline__ cx<R> czero() { return {R(0), R(0)}; }
 template <typename R> __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return {addR(a.r, b.r), addR(a.i, b.i)}; }
 template <typename R> __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return {subR(a.r, b.r), subR(a.i, b.i)}; }
@@ -125,6 +177,22 @@ template <> struct SpinorView<float> {
     }
 };
 
+template <> struct SpinorView<df> {
+    float4* p;
+    int V;
+    __device__ __forceinline__ void load(int s, cx<df> v[12]) const {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float4 t = __ldg(p + (size_t)k * V + s);
+            v[k] = {df(t.x, t.y), df(t.z, t.w)};
+        }
+    }
+    __device__ __forceinline__ void store(int s, const cx<df> v[12]) const {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[(size_t)k * V + s] = make_float4(v[k].r.hi, v[k].r.lo, v[k].i.hi, v[k].i.lo);
+    }
+};
+
 // bytes of one internal spinor
 template <typename R> constexpr size_t spinor_bytes(int V) { return (size_t)V * 12 * 2 * sizeof(R); }
 
@@ -163,17 +231,36 @@ template <> struct LinkView<float> {
     }
 };
 
+template <> struct LinkView<df> {
+    const float4* p;
+    int V;
+    __device__ __forceinline__ void load(int mu, int s, cx<df> U[3][3]) const {
+        const float4* b = p + (size_t)mu * 9 * V + s;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            float4 t = __ldg(b + (size_t)e * V);
+            U[e / 3][e % 3] = {df(t.x, t.y), df(t.z, t.w)};
+        }
+    }
+};
+
 // ------------------------------------------------------------------ block reduction
 // Sum K complex values over the block (FP32 values are summed in FP32 within a
-// warp and in FP64 across warps); thread 0 writes them to out[k*stride] as
-// double2.  Deterministic for a fixed launch shape.
+// warp, FP64 and double-float values in FP64; FP64 across warps); thread 0
+// writes them to out[k*stride] as double2.  Deterministic for a fixed launch shape.
+template <typename R> struct WarpSum { using T = double; };
+template <> struct WarpSum<float> { using T = float; };
+
 template <int K, typename R>
 __device__ __forceinline__ void block_reduce_store(cx<R> (&v)[K], double2* out, int stride) {
+    using W = typename WarpSum<R>::T;
     __shared__ double2 sh[K][kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        R a = v[k].r, b = v[k].i;
+        W a, b;
+        if constexpr (sizeof(W) == 4) { a = v[k].r; b = v[k].i; }
+        else { a = todbl(v[k].r); b = todbl(v[k].i); }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_down_sync(0xffffffffu, a, o);
@@ -220,13 +307,22 @@ int launch_hop_f32(const Geom& g, const float4* links, const float4* in, float4*
                    bool g5in, bool g5out, const float4* dot_with, double2* partials,
                    const int* done, cudaStream_t st);
 
+int launch_hop_df(const Geom& g, const float4* links, const float4* in, float4* out,
+                  double diag, double ef, double eb, double t_bc, double scale,
+                  bool g5in, bool g5out, const float4* dot_with, double2* partials,
+                  const int* done, cudaStream_t st);
+
 // canonical (interleaved complex128 AoS) <-> internal layouts
 int launch_pack_spinor_f64(const Geom& g, const double* canon, double2* out, cudaStream_t st);
 int launch_unpack_spinor_f64(const Geom& g, const double2* in, double* canon, cudaStream_t st);
 int launch_pack_spinor_f32(const Geom& g, const double* canon, float4* out, cudaStream_t st);
 int launch_unpack_spinor_f32(const Geom& g, const float4* in, double* canon, cudaStream_t st);
-int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, cudaStream_t st);
+int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, float4* ldf, cudaStream_t st);
 int launch_convert_f64_to_f32(const Geom& g, const double2* in, float4* out, cudaStream_t st);
+// double-float spinors: [12][V] float4 = (re.hi, re.lo, im.hi, im.lo)
+int launch_pack_spinor_df(const Geom& g, const double* canon, float4* out, cudaStream_t st);
+int launch_unpack_spinor_df(const Geom& g, const float4* in, double* canon, cudaStream_t st);
+int launch_convert_df_to_f32(const Geom& g, const float4* in, float4* out, cudaStream_t st);
 
 // adjoint link force of <a1, D b1> + <a2, D b2> (a1 enters as gamma_5 a1), scaled by w,
 // added to the canonical gradient G; per-block partials of the mu-derivative.

@@ -8,6 +8,8 @@
 // boundary sign on hops across t = T-1 <-> 0, DeGrand-Rossi projectors).
 #pragma once
 
+#include <type_traits>
+
 #include "fa_internal.cuh"
 
 namespace fa {
@@ -154,6 +156,15 @@ __device__ __forceinline__ void hop_site(const Geom& g, const LinkView<R>& U, co
 #ifndef FA_HOP_MINB
 #define FA_HOP_MINB 3
 #endif
-template <typename R> constexpr int hop_min_blocks() { return sizeof(R) == 4 ? FA_HOP_MINB : 1; }
+// double-float: register budget for FA_HOP_MINB_DF resident blocks per SM.  The
+// kernel is bound by dependent FP32 instruction chains; measured on 16^3 x 32:
+// 1 block/SM (160 registers) 0.219 ms, 2 blocks/SM (128 registers, 40 B
+// spilled) 0.169 ms per sweep.
+#ifndef FA_HOP_MINB_DF
+#define FA_HOP_MINB_DF 2
+#endif
+template <typename R> constexpr int hop_min_blocks() {
+    return sizeof(R) == 4 ? FA_HOP_MINB : (std::is_same<R, df>::value ? FA_HOP_MINB_DF : 1);
+}
 
 }  // namespace fa

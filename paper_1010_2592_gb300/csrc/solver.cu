@@ -11,6 +11,7 @@
 #include <cstring>
 #include <algorithm>
 #include <vector>
+#include <type_traits>
 
 #include "fa_context.h"
 #include "solver_kernels.cuh"
@@ -82,6 +83,18 @@ int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, b
     hop_timing_end(c);
     c->launches++;
     if (rc == FA_ECUDA) return cuda_fail(cudaGetLastError(), "hop_f32");
+    return rc;
+}
+
+int hop_df(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, bool g5out, bool dagger_mu,
+           const float4* dot_with, double2* partials, const int* done) {
+    const double mu = dagger_mu ? -c->mu : c->mu;
+    hop_timing_begin(c, 2);
+    int rc = launch_hop_df(c->g, linksdf_of(c), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu), c->t_bc, scale,
+                           g5in, g5out, dot_with, partials, done, c->stream);
+    hop_timing_end(c);
+    c->launches++;
+    if (rc == FA_ECUDA) return cuda_fail(cudaGetLastError(), "hop_df");
     return rc;
 }
 
@@ -163,6 +176,7 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     d.g = c->g;
     d.links64 = links64_of(c);
     d.links32 = links32_of(c);
+    d.linksdf = linksdf_of(c);
     d.diag = 4.0 + c->mass;
     d.ef = std::exp(c->mu);
     d.eb = std::exp(-c->mu);
@@ -223,6 +237,12 @@ static int upload(Batch& B) {
     return FA_OK;
 }
 
+// working precision of a stretch of outer iterations
+enum Rp { RP64 = 0, RP32 = 1, RPDF = 2 };
+template <typename R> constexpr int rp_of() {
+    return std::is_same<R, double>::value ? RP64 : (std::is_same<R, float>::value ? RP32 : RPDF);
+}
+
 // ------------------------------------------------------------------ one outer iteration
 // Pass 1 (pass2 = false): seed recurrence with inner products and the scalar
 // kernels.  Pass 2 (pass2 = true): the same vector kernels with the recorded
@@ -237,7 +257,7 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     const dim3 gs(nb, n), gr(rg, n);
     const SolverDev* ds = B.dev;
     cudaStream_t st = c->stream;
-    constexpr int kind = sizeof(R) == 8 ? 0 : 1;
+    constexpr int kind = rp_of<R>() == RP64 ? 0 : (rp_of<R>() == RP32 ? 1 : 2);
     const bool timing = c->hop_timing && !B.use_graph;
     // One system: the stand-alone hop kernel with its pointers as kernel
     // parameters (no descriptor fields held in registers).  A batch: the
@@ -245,20 +265,24 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     using T = typename Ch<R>::T;
     const SolverDev& h0 = B.host[0];
     auto vsel = [&](int sel, int j) -> T* {
-        T* base = sizeof(R) == 8 ? (T*)(sel == 0 ? (void*)h0.u64 : sel == 1 ? (void*)h0.r64 : (void*)h0.tmp64)
-                                 : (T*)(sel == 0 ? (void*)h0.u32 : sel == 1 ? (void*)h0.r32 : (void*)h0.tmp32);
+        constexpr bool wide = rp_of<R>() != RP32;   // FP64 and double-float use the wide buffers
+        T* base = wide ? (T*)(sel == 0 ? (void*)h0.u64 : sel == 1 ? (void*)h0.r64 : (void*)h0.tmp64)
+                       : (T*)(sel == 0 ? (void*)h0.u32 : sel == 1 ? (void*)h0.r32 : (void*)h0.tmp32);
         return base + (size_t)j * (size_t)Ch<R>::N * h0.V;
     };
     auto hop = [&](int in_sel, int in_j, int out_sel, int out_j, int second, bool dot) -> int {
         if (timing) hop_timing_begin(c, kind);
         if (n == 1) {
-            const T* rt = sizeof(R) == 8 ? (const T*)(const void*)h0.rt64 : (const T*)(const void*)h0.rt32;
+            const T* rt = rp_of<R>() != RP32 ? (const T*)(const void*)h0.rt64 : (const T*)(const void*)h0.rt32;
             const int* done = pass2 ? nullptr : &h0.st->done;
             const double sc = second ? h0.scale : 1.0;
             int rc;
-            if constexpr (sizeof(R) == 8)
+            if constexpr (rp_of<R>() == RP64)
                 rc = launch_hop_f64(h0.g, h0.links64, vsel(in_sel, in_j), vsel(out_sel, out_j), h0.diag, h0.ef, h0.eb,
                                     h0.bc, sc, false, true, dot ? rt : nullptr, h0.part, done, st);
+            else if constexpr (rp_of<R>() == RPDF)
+                rc = launch_hop_df(h0.g, h0.linksdf, vsel(in_sel, in_j), vsel(out_sel, out_j), h0.diag, h0.ef, h0.eb,
+                                   h0.bc, sc, false, true, dot ? rt : nullptr, h0.part, done, st);
             else
                 rc = launch_hop_f32(h0.g, h0.links32, vsel(in_sel, in_j), vsel(out_sel, out_j), h0.diag, h0.ef, h0.eb,
                                     h0.bc, sc, false, true, dot ? rt : nullptr, h0.part, done, st);
@@ -289,7 +313,7 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
         if (pass2) {
             k_update_r<R, true, false><<<gs, kThreads, 0, st>>>(ds, j, p2);
         } else if (single) {
-            if constexpr (sizeof(R) == 8) k_update_r<R, false, true><<<gs, kThreads, 0, st>>>(ds, j, p2);
+            if constexpr (rp_of<R>() == RP64) k_update_r<R, false, true><<<gs, kThreads, 0, st>>>(ds, j, p2);
         } else {
             k_update_r<R, false, false><<<gs, kThreads, 0, st>>>(ds, j, p2);
         }
@@ -306,7 +330,7 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     if (pass2) {
         k_mr<R, L, true, false, false><<<gr, kThreads, 0, st>>>(ds, p2);
     } else if (single) {
-        if constexpr (sizeof(R) == 8) k_mr<R, L, false, true, true><<<gr, kThreads, 0, st>>>(ds, p2);
+        if constexpr (rp_of<R>() == RP64) k_mr<R, L, false, true, true><<<gr, kThreads, 0, st>>>(ds, p2);
     } else {
         k_mr<R, L, false, false, true><<<gr, kThreads, 0, st>>>(ds, p2);
     }
@@ -338,18 +362,19 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
 }
 
 template <int L>
-static int enqueue_outer_p(Batch& B, bool f64, bool pass2, bool single, bool head, bool rel) {
-    return f64 ? enqueue_outer<double, L>(B, pass2, single, head, rel)
-               : enqueue_outer<float, L>(B, pass2, single, head, rel);
+static int enqueue_outer_p(Batch& B, int rp, bool pass2, bool single, bool head, bool rel) {
+    if (rp == RP64) return enqueue_outer<double, L>(B, pass2, single, head, rel);
+    if (rp == RPDF) return enqueue_outer<df, L>(B, pass2, single, head, rel);
+    return enqueue_outer<float, L>(B, pass2, single, head, rel);
 }
 
-static int enqueue_outer_direct(Batch& B, bool f64, bool pass2, bool single, bool head, bool rel) {
+static int enqueue_outer_direct(Batch& B, int rp, bool pass2, bool single, bool head, bool rel) {
     switch (B.Lo.L) {
-        case 1: return enqueue_outer_p<1>(B, f64, pass2, single, head, rel);
-        case 2: return enqueue_outer_p<2>(B, f64, pass2, single, head, rel);
-        case 3: return enqueue_outer_p<3>(B, f64, pass2, single, head, rel);
-        case 4: return enqueue_outer_p<4>(B, f64, pass2, single, head, rel);
-        case 8: return enqueue_outer_p<8>(B, f64, pass2, single, head, rel);
+        case 1: return enqueue_outer_p<1>(B, rp, pass2, single, head, rel);
+        case 2: return enqueue_outer_p<2>(B, rp, pass2, single, head, rel);
+        case 3: return enqueue_outer_p<3>(B, rp, pass2, single, head, rel);
+        case 4: return enqueue_outer_p<4>(B, rp, pass2, single, head, rel);
+        case 8: return enqueue_outer_p<8>(B, rp, pass2, single, head, rel);
         default: return FA_EINVAL;
     }
 }
@@ -357,10 +382,10 @@ static int enqueue_outer_direct(Batch& B, bool f64, bool pass2, bool single, boo
 // One outer iteration, replayed from a captured CUDA graph when the batch
 // uses graphs (every argument of every launch is iteration-independent: the
 // kernels read m and their scalars from the device).
-static int enqueue_outer_any(Batch& B, bool f64, bool pass2, bool single, bool head, bool rel = false) {
-    if (!B.use_graph) return enqueue_outer_direct(B, f64, pass2, single, head, rel);
+static int enqueue_outer_any(Batch& B, int rp, bool pass2, bool single, bool head, bool rel = false) {
+    if (!B.use_graph) return enqueue_outer_direct(B, rp, pass2, single, head, rel);
     fa_ctx* c = B.c0;
-    const int key = (f64 ? 1 : 0) | (pass2 ? 2 : 0) | (single ? 4 : 0) | (head ? 8 : 0) | (rel ? 16 : 0);
+    const int key = rp | (pass2 ? 4 : 0) | (single ? 8 : 0) | (head ? 16 : 0) | (rel ? 32 : 0);
     GraphEntry* ge = nullptr;
     for (auto& e : c->graphs)
         if (e.key == key && e.L == B.Lo.L && e.dev == (void*)B.dev && e.n == B.n && e.V == B.Lo.V && e.exec)
@@ -369,7 +394,7 @@ static int enqueue_outer_any(Batch& B, bool f64, bool pass2, bool single, bool h
         const long long n0 = c->launches;
         cudaGraph_t g = nullptr;
         FA_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        const int rc = enqueue_outer_direct(B, f64, pass2, single, head, rel);
+        const int rc = enqueue_outer_direct(B, rp, pass2, single, head, rel);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (rc != FA_OK) { if (g) cudaGraphDestroy(g); return rc; }
         FA_CUDA(e, "end capture");
@@ -405,12 +430,13 @@ static int launch_sweep(Batch& B) {
 }
 
 // b (canonical) -> r_0 and rt of the requested precision, u_0 = 0, for system i
-static int load_source(Batch& B, int i, const double* b, bool f64) {
+static int load_source(Batch& B, int i, const double* b, int rp) {
     fa_ctx* c = B.sys[i];
     cudaStream_t st = B.c0->stream;
     const int V = B.Lo.V;
-    if (f64) {
-        FA_TRY(launch_pack_spinor_f64(c->g, b, c->r64.as<double2>(), st));
+    if (rp != RP32) {
+        if (rp == RP64) FA_TRY(launch_pack_spinor_f64(c->g, b, c->r64.as<double2>(), st));
+        else FA_TRY(launch_pack_spinor_df(c->g, b, c->r64.as<float4>(), st));
         FA_CUDA(cudaMemcpyAsync(c->rt64.p, c->r64.p, (size_t)12 * V * sizeof(double2), cudaMemcpyDeviceToDevice, st),
                 "copy rt");
         FA_CUDA(cudaMemsetAsync(c->u64.p, 0, (size_t)12 * V * sizeof(double2), st), "zero u");
@@ -424,13 +450,17 @@ static int load_source(Batch& B, int i, const double* b, bool f64) {
     return FA_OK;
 }
 
-// FP64 -> FP32 hand-over of the live seed vectors (r_0, u_0, rt) at an outer-iteration boundary
-static int switch_to_f32(Batch& B, int i) {
+// head (FP64 or double-float) -> FP32 hand-over of the live seed vectors
+// (r_0, u_0, rt) at an outer-iteration boundary
+static int switch_to_f32(Batch& B, int i, int from) {
     fa_ctx* c = B.sys[i];
     cudaStream_t st = B.c0->stream;
-    FA_TRY(launch_convert_f64_to_f32(c->g, c->r64.as<double2>(), c->r32.as<float4>(), st));
-    FA_TRY(launch_convert_f64_to_f32(c->g, c->u64.as<double2>(), c->u32.as<float4>(), st));
-    FA_TRY(launch_convert_f64_to_f32(c->g, c->rt64.as<double2>(), c->rt32.as<float4>(), st));
+    DevBuf* src[3] = {&c->r64, &c->u64, &c->rt64};
+    DevBuf* dst[3] = {&c->r32, &c->u32, &c->rt32};
+    for (int k = 0; k < 3; ++k) {
+        if (from == RPDF) FA_TRY(launch_convert_df_to_f32(c->g, src[k]->as<float4>(), dst[k]->as<float4>(), st));
+        else FA_TRY(launch_convert_f64_to_f32(c->g, src[k]->as<double2>(), dst[k]->as<float4>(), st));
+    }
     B.c0->launches += 3;
     return FA_OK;
 }
@@ -483,15 +513,17 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     const bool pseudo = p->mode == FA_PSEUDO;
     if (!single && !pseudo && p->mode != FA_DOUBLE) return FA_EINVAL;
     const int prec = p->precision;
-    if (prec != FA_F64 && prec != FA_F32 && prec != FA_MIXED) return FA_EINVAL;
+    if (prec != FA_F64 && prec != FA_F32 && prec != FA_MIXED && prec != FA_MIXED_DF) return FA_EINVAL;
     if (single && prec != FA_F64) return FA_EINVAL;
-    if (prec == FA_MIXED && n != 1) return FA_EINVAL;   // per-system switch points: one system at a time
+    const bool mixed = prec == FA_MIXED || prec == FA_MIXED_DF;
+    const int head_rp = prec == FA_MIXED_DF ? RPDF : RP64;   // working precision of the head
+    if (mixed && n != 1) return FA_EINVAL;   // per-system switch points: one system at a time
     const int rel_every = p->reliable_every;
     if (rel_every < 0 || (rel_every > 0 && n != 1)) return FA_EINVAL;
     // FA_MIXED: switch_resid <= 0 selects the default 0.04 / l^2 (the FP32
     // error of the power-basis recurrence grows with l)
     const double switch_resid = (p->switch_resid > 0.0) ? p->switch_resid : 0.04 / ((double)L * L);
-    if (prec == FA_MIXED && !(switch_resid < 1.0)) return FA_EINVAL;
+    if (mixed && !(switch_resid < 1.0)) return FA_EINVAL;
 
     Batch B;
     B.c0 = c0;
@@ -585,16 +617,18 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     FA_TRY(upload(B));
     int K = pseudo ? -1 : 0;                // first outer iteration not stored (-1: still storing)
     int m0_32 = prec == FA_F32 ? 0 : -1;    // first FP32 outer iteration (one value for the batch)
-    bool snap_f64 = true;
+    bool snap_wide = true;
     // called before outer iteration m is enqueued: at the first unstored one,
-    // snapshot the seed state so that a pass 2 can restart there
-    auto before_outer = [&](int m, bool f64now) -> int {
+    // snapshot the seed state so that a pass 2 can restart there (FP64 and
+    // double-float states use the wide buffers and stores)
+    auto before_outer = [&](int m, int rp) -> int {
         if (K >= 0) return FA_OK;
-        const bool stored = f64now ? (m < cap64) : (m0_32 >= 0 && m - m0_32 < cap32);
+        const bool wide = rp != RP32;
+        const bool stored = wide ? (m < cap64) : (m0_32 >= 0 && m - m0_32 < cap32);
         if (stored) return FA_OK;
         K = m;
-        snap_f64 = f64now;
-        for (int i = 0; i < n; ++i) FA_TRY(snapshot(B, i, f64now, false));
+        snap_wide = wide;
+        for (int i = 0; i < n; ++i) FA_TRY(snapshot(B, i, wide, false));
         return FA_OK;
     };
 
@@ -613,29 +647,30 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     if (timing) cudaEventRecord(ev[0], st);
 
     // ---- pass 1
-    bool f64 = prec != FA_F32;
-    bool head = prec == FA_MIXED;
-    for (int i = 0; i < n; ++i) FA_TRY(load_source(B, i, b[i], f64));
+    int rp = prec == FA_F32 ? RP32 : (prec == FA_F64 ? RP64 : head_rp);
+    bool head = mixed;
+    for (int i = 0; i < n; ++i) FA_TRY(load_source(B, i, b[i], rp));
     const dim3 gr(Lo.red_grid, n);
-    if (f64) k_dot2_sys<double><<<gr, kThreads, 0, st>>>(B.dev);
+    if (rp == RP64) k_dot2_sys<double><<<gr, kThreads, 0, st>>>(B.dev);
+    else if (rp == RPDF) k_dot2_sys<df><<<gr, kThreads, 0, st>>>(B.dev);
     else k_dot2_sys<float><<<gr, kThreads, 0, st>>>(B.dev);
     FA_LAUNCHED(c0, "k_dot2_sys");
-    k_sc_init<<<n, kScalarThreads, 0, st>>>(B.dev, Lo.red_grid, p->tol, prec == FA_MIXED ? switch_resid : 0.0);
+    k_sc_init<<<n, kScalarThreads, 0, st>>>(B.dev, Lo.red_grid, p->tol, mixed ? switch_resid : 0.0);
     FA_LAUNCHED(c0, "k_sc_init");
 
     std::vector<DevState> hs(n);
     int switch_outer = -1;
     int enq = 0;
     bool all_done = false;
-    // FP64 head of FA_MIXED (one system): one outer iteration at a time until the switch
+    // head of FA_MIXED / FA_MIXED_DF (one system): one outer iteration at a time until the switch
     while (head && enq < Lo.max_outer) {
-        FA_TRY(before_outer(enq, true));
-        FA_TRY(enqueue_outer_any(B, true, false, single, true, reliable_at(enq)));
+        FA_TRY(before_outer(enq, rp));
+        FA_TRY(enqueue_outer_any(B, rp, false, single, true, reliable_at(enq)));
         ++enq;
         FA_TRY(read_states(B, hs));
         if (hs[0].done) { all_done = true; break; }
         if (hs[0].switch_req) {
-            FA_TRY(switch_to_f32(B, 0));
+            FA_TRY(switch_to_f32(B, 0, rp));
             switch_outer = hs[0].m;
             m0_32 = switch_outer;
             // the stored prefix must stay contiguous: no FP32 slots if the head outran its slots
@@ -643,7 +678,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
             if (K >= 0) B.host[0].cap32 = 0, cap32 = 0;
             FA_TRY(upload(B));
             head = false;
-            f64 = false;
+            rp = RP32;
         }
     }
     if (!all_done) {
@@ -658,8 +693,8 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         int rc = FA_OK;
         while (!stop && enq < Lo.max_outer) {
             for (int i = 0; i < chunk && enq < Lo.max_outer; ++i, ++enq) {
-                rc = before_outer(enq, f64);
-                if (rc == FA_OK) rc = enqueue_outer_any(B, f64, false, single, false, reliable_at(enq));
+                rc = before_outer(enq, rp);
+                if (rc == FA_OK) rc = enqueue_outer_any(B, rp, false, single, false, reliable_at(enq));
                 if (rc != FA_OK) break;
             }
             if (rc != FA_OK) break;
@@ -702,8 +737,9 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         const dim3 gs(Lo.nblk, n);
         if (pseudo && Kst > 0) {
             if (cap64 > 0) {
-                k_gather<double><<<gs, kThreads, 0, st>>>(B.dev);
-                FA_LAUNCHED(c0, "k_gather<double>");
+                if (prec == FA_MIXED_DF) k_gather<df><<<gs, kThreads, 0, st>>>(B.dev);
+                else k_gather<double><<<gs, kThreads, 0, st>>>(B.dev);
+                FA_LAUNCHED(c0, "k_gather (head store)");
             }
             if (cap32 > 0 && m0_32 >= 0) {
                 k_gather<float><<<gs, kThreads, 0, st>>>(B.dev);
@@ -712,25 +748,26 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         }
         const int mstart = Kst;
         if (mstart < M) {
-            bool p2f64 = prec == FA_F64 || (prec == FA_MIXED && (switch_outer < 0 || mstart < switch_outer));
+            int p2 = prec == FA_F64 ? RP64
+                   : (prec == FA_F32 ? RP32 : ((switch_outer < 0 || mstart < switch_outer) ? head_rp : RP32));
             for (int i = 0; i < n; ++i) {
                 if (mstart == 0) {
-                    FA_TRY(load_source(B, i, b[i], p2f64));
+                    FA_TRY(load_source(B, i, b[i], p2));
                     if (B.host[i].x64)
                         FA_CUDA(cudaMemsetAsync(B.host[i].x64, 0, s64, st), "zero x");
                 } else {
-                    if (snap_f64 != p2f64) return FA_ESTATE;
-                    FA_TRY(snapshot(B, i, p2f64, true));
+                    if (snap_wide != (p2 != RP32)) return FA_ESTATE;
+                    FA_TRY(snapshot(B, i, p2 != RP32, true));
                 }
             }
             k_set_m<<<n, 1, 0, st>>>(B.dev, mstart);
             FA_LAUNCHED(c0, "k_set_m");
             for (int m = mstart; m < M; ++m) {
-                if (p2f64 && prec == FA_MIXED && m == switch_outer) {
-                    FA_TRY(switch_to_f32(B, 0));
-                    p2f64 = false;
+                if (p2 != RP32 && mixed && m == switch_outer) {
+                    FA_TRY(switch_to_f32(B, 0, p2));
+                    p2 = RP32;
                 }
-                FA_TRY(enqueue_outer_any(B, p2f64, true, false, false, reliable_at(m)));
+                FA_TRY(enqueue_outer_any(B, p2, true, false, false, reliable_at(m)));
             }
         }
         if (timing) cudaEventRecord(ev[3], st);

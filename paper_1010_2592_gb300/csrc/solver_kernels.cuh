@@ -62,6 +62,7 @@ struct SolverDev {
     Geom g;
     const double2* links64;
     const float4* links32;
+    const float4* linksdf;            // double-float links [4][9][V]
     double diag, ef, eb, bc, scale;   // 4+m, e^{+mu}, e^{-mu}, time-boundary sign, c
     const double* sigma;   // [ns]
     const double* omega;   // [ns]
@@ -103,6 +104,15 @@ template <> struct Vec<double> {
     __device__ static T* tmp(const SolverDev& d) { return d.tmp64; }
     __device__ static LinkView<double> links(const SolverDev& d) { return {d.links64, d.V}; }
 };
+// double-float vectors live in the FP64 buffers (same bytes: one float4 per complex)
+template <> struct Vec<df> {
+    using T = float4;
+    __device__ static T* r(const SolverDev& d) { return reinterpret_cast<T*>(d.r64); }
+    __device__ static T* u(const SolverDev& d) { return reinterpret_cast<T*>(d.u64); }
+    __device__ static T* rt(const SolverDev& d) { return reinterpret_cast<T*>(d.rt64); }
+    __device__ static T* tmp(const SolverDev& d) { return reinterpret_cast<T*>(d.tmp64); }
+    __device__ static LinkView<df> links(const SolverDev& d) { return {d.linksdf, d.V}; }
+};
 template <> struct Vec<float> {
     using T = float4;
     __device__ static T* r(const SolverDev& d) { return d.r32; }
@@ -132,6 +142,18 @@ template <> struct Ch<double> {
     }
     __device__ __forceinline__ void stv(T* b, int q, int V, int s) const {
         b[(size_t)q * V + s] = make_double2(c[0].r, c[0].i);
+    }
+};
+template <> struct Ch<df> {
+    static constexpr int W = 1, N = 12;
+    using T = float4;
+    cx<df> c[1];
+    __device__ __forceinline__ static Ch ld(const T* b, int q, int V, int s) {
+        float4 t = b[(size_t)q * V + s];
+        Ch r; r.c[0] = {df(t.x, t.y), df(t.z, t.w)}; return r;
+    }
+    __device__ __forceinline__ void stv(T* b, int q, int V, int s) const {
+        b[(size_t)q * V + s] = make_float4(c[0].r.hi, c[0].r.lo, c[0].i.hi, c[0].i.lo);
     }
 };
 template <> struct Ch<float> {
@@ -164,8 +186,10 @@ __device__ __forceinline__ typename Ch<R>::T* store_at(const SolverDev& d, int m
     return nullptr;
 }
 
-template <typename R> __device__ __forceinline__ cx<R> tocx(double2 v) { return {(R)v.x, (R)v.y}; }
-template <typename R> __device__ __forceinline__ cx<R> negcx(double2 v) { return {(R)(-v.x), (R)(-v.y)}; }
+template <typename R> __device__ __forceinline__ cx<R> tocx(double2 v) { return {fromdbl<R>(v.x), fromdbl<R>(v.y)}; }
+template <typename R> __device__ __forceinline__ cx<R> negcx(double2 v) {
+    return {fromdbl<R>(-v.x), fromdbl<R>(-v.y)};
+}
 
 // y (FP64, [12][V]) += t for the W complex components of chunk q
 template <typename R>
@@ -174,8 +198,8 @@ __device__ __forceinline__ void acc_y(double2* y, int q, int V, int s, const cx<
     for (int w = 0; w < Ch<R>::W; ++w) {
         double2* p = y + (size_t)(q * Ch<R>::W + w) * V + s;
         double2 a = *p;
-        a.x = __dadd_rn(a.x, (double)t[w].r);
-        a.y = __dadd_rn(a.y, (double)t[w].i);
+        a.x = __dadd_rn(a.x, todbl(t[w].r));
+        a.y = __dadd_rn(a.y, todbl(t[w].i));
         *p = a;
     }
 }
@@ -187,7 +211,7 @@ __device__ __forceinline__ void acc_x(double2* x, int q, int V, int s, double2 a
     for (int w = 0; w < Ch<R>::W; ++w) {
         double2* p = x + (size_t)(q * Ch<R>::W + w) * V + s;
         double2 t = *p;
-        const double vr = (double)v.c[w].r, vi = (double)v.c[w].i;
+        const double vr = todbl(v.c[w].r), vi = todbl(v.c[w].i);
         t.x = __fma_rn(a.x, vr, t.x);
         t.x = __fma_rn(-a.y, vi, t.x);
         t.y = __fma_rn(a.x, vi, t.y);
@@ -504,8 +528,8 @@ k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, i
         SpinorView<R> in{select_vec<R>(d, in_sel, in_j), d.V};
         SpinorView<R> out{select_vec<R>(d, out_sel, out_j), d.V};
         cx<R> p[12];
-        hop_site<R, false, true>(d.g, Vec<R>::links(d), in, s, (R)(sc * d.diag), (R)(-0.5 * sc), (R)d.ef, (R)d.eb,
-                                 (R)d.bc, p);
+        hop_site<R, false, true>(d.g, Vec<R>::links(d), in, s, fromdbl<R>(sc * d.diag), fromdbl<R>(-0.5 * sc),
+                                 fromdbl<R>(d.ef), fromdbl<R>(d.eb), fromdbl<R>(d.bc), p);
         out.store(s, p);
         if (DOT) {
             SpinorView<R> rt{Vec<R>::rt(d), d.V};
@@ -802,7 +826,7 @@ __global__ void __launch_bounds__(kThreads) k_reliable(const SolverDev* __restri
             for (int w = 0; w < Ch<R>::W; ++w) {
                 const size_t k = (size_t)(q * Ch<R>::W + w) * d.V + s;
                 const double2 bb = d.b64[k], aa = ax[k];
-                v.c[w] = {(R)__dsub_rn(bb.x, aa.x), (R)__dsub_rn(bb.y, aa.y)};
+                v.c[w] = {fromdbl<R>(__dsub_rn(bb.x, aa.x)), fromdbl<R>(__dsub_rn(bb.y, aa.y))};
             }
             v.stv(r0, q, d.V, s);
             Ch<R> tv = Ch<R>::ld(rt, q, d.V, s);
@@ -870,8 +894,8 @@ k_gather(const SolverDev* __restrict__ ds) {
         }
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            acc[2 * k] = __dadd_rn(acc[2 * k], (double)t[k].r);
-            acc[2 * k + 1] = __dadd_rn(acc[2 * k + 1], (double)t[k].i);
+            acc[2 * k] = __dadd_rn(acc[2 * k], todbl(t[k].r));
+            acc[2 * k + 1] = __dadd_rn(acc[2 * k + 1], todbl(t[k].i));
         }
     }
 #pragma unroll

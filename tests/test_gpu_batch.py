@@ -73,7 +73,8 @@ def test_batched_against_oracle():
     assert rel(to_host(ys[5]), y_o) < 1e-10
 
 
-@pytest.mark.parametrize("mode,precision", [("double", "f64"), ("pseudo", "mixed"), ("double", "f32")])
+@pytest.mark.parametrize("mode,precision", [("double", "f64"), ("pseudo", "mixed"), ("double", "f32"),
+                                            ("pseudo", "mixed_df")])
 def test_graph_replay_equals_direct_launches(mode, precision):
     import torch
     w = workload_case("wilson_4x4x4x8")
@@ -94,7 +95,7 @@ def test_graph_replay_equals_direct_launches(mode, precision):
     assert np.array_equal(to_host(r1.y), to_host(r2.y))
     assert r1.stats["outer_iters"] == r0.stats["outer_iters"]
     y_o, _ = oracle_double("wilson_4x4x4x8", None, 2, 1e-12)
-    tol = {"f64": 1e-9, "mixed": 1e-8, "f32": 1e-6}[precision]
+    tol = {"f64": 1e-9, "mixed": 1e-8, "f32": 1e-6, "mixed_df": 1e-8}[precision]
     assert rel(to_host(r1.y), y_o) < tol
 
 

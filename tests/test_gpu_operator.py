@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 # lattices spanning one partial block, several blocks with a ragged tail, and
 # the multi-block workload shapes
 SHAPES = [(3, 3, 3, 6), (6, 4, 6, 10), (4, 4, 4, 8), (8, 8, 8, 16)]
-TOL = {"f64": 1e-13, "f32": 5e-6}
+TOL = {"f64": 1e-13, "f32": 5e-6, "df": 1e-11}
 
 
 @pytest.fixture(scope="module", params=SHAPES, ids=lambda d: "x".join(map(str, d)))
@@ -24,7 +24,7 @@ def case(request):
     return dims, U, psi
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "df"])
 @pytest.mark.parametrize("mu,t_bc", [(0.05, -1), (0.0, 1), (0.3, -1)])
 def test_dw_matches_oracle(case, precision, mu, t_bc):
     dims, U, psi = case
@@ -37,7 +37,7 @@ def test_dw_matches_oracle(case, precision, mu, t_bc):
     assert rel(gotd, wantd) < TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "df"])
 def test_A_matches_oracle(case, precision):
     dims, U, psi = case
     ctx = make_context(dims, U, -1.8, 0.1, 0.037)
