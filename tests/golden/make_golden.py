@@ -5,7 +5,11 @@ the power-iteration scale c, then the double-pass multi-shift BiCGstab(2)
 with Neuberger's 20 poles at tol 1e-12, and stores c, the outer-iteration
 counts and y* = f(A) b at 512 seeded sample positions, plus |y*|.
 
-    python tests/golden/make_golden.py [workload]     (about 30 min of numpy)
+    python tests/golden/make_golden.py [workload] [tol]     (about 15 min of numpy)
+
+With a tolerance other than 1e-12 the file is named <workload>_tol<tol>.json; the
+benchmark reads the outer-iteration count of the tol-1e-9 run to scale its oracle
+(CPU) baseline to a whole solve at the headline's tolerance.
 """
 import json
 import os
@@ -42,11 +46,13 @@ def main(name="wilson_16x16x16x32", tol=1e-12, n_samples=512):
         oracle_seconds=time.time() - t0,
         source="oracle.msbicgstab.multishift_double (FP64 numpy), written by tests/golden/make_golden.py",
     )
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}.json")
+    suffix = "" if tol == 1e-12 else f"_tol{tol:g}"
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}{suffix}.json")
     with open(path, "w") as f:
         json.dump(out, f)
     print(path, st.n_outer, time.time() - t0)
 
 
 if __name__ == "__main__":
-    main(*sys.argv[1:2])
+    args = sys.argv[1:]
+    main(args[0] if args else "wilson_16x16x16x32", float(args[1]) if len(args) > 1 else 1e-12)
