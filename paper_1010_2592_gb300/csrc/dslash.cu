@@ -18,12 +18,12 @@
 
 namespace fa {
 
-template <typename R, bool G5IN, bool G5OUT, bool DOT>
-__global__ void __launch_bounds__(kThreads, hop_min_blocks<R>())
+template <typename R, bool G5IN, bool G5OUT, bool DOT, int NT = kThreads, int MB = hop_min_blocks<R>()>
+__global__ void __launch_bounds__(NT, MB)
 hop_kernel(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb,
            R bc, SpinorView<R> dotv, double2* partials, const int* done) {
     if (done != nullptr && *done) return;
-    const int s = blockIdx.x * kThreads + threadIdx.x;
+    const int s = blockIdx.x * NT + threadIdx.x;
     cx<R> dres[1] = {czero<R>()};
     if (s < g.V) {
         cx<R> p[12];
@@ -38,12 +38,35 @@ hop_kernel(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, 
             dres[0] = a;
         }
     }
-    if (DOT) block_reduce_store<1, R>(dres, partials, 0);
+    if (DOT) block_reduce_store<1, R, NT>(dres, partials, 0, blockIdx.x);
 }
 
-static df fromdbl_host(double x) {
-    const float h = (float)x;
-    return df(h, (float)(x - (double)h));
+// Number of SMs of the current device (cached per device).
+int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+bool hop_narrow(int V) {
+    const int n = sm_count();
+    return n > 0 && kHopNarrowBlocks > 0 && (V + kHopNarrowThreads - 1) / kHopNarrowThreads <= kHopNarrowBlocks * n;
+}
+
+// the same sweep split by colour row (double-float)
+template <typename R, bool G5IN, bool G5OUT, bool DOT>
+__global__ void __launch_bounds__(kRowThreads, rows_min_blocks<DOT>())
+hop_rows_kernel(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb,
+                R bc, SpinorView<R> dotv, double2* partials, const int* done) {
+    if (done != nullptr && *done) return;
+    cx<R> dres[1] = {hop_rows_body<R, G5IN, G5OUT, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv)};
+    if (DOT) block_reduce_store<1, R, kRowThreads>(dres, partials, 0, blockIdx.x);
 }
 
 template <typename R, typename LP, typename SP>
@@ -56,8 +79,23 @@ static int launch_hop_t(const Geom& g, const LP* links, const SP* in, SP* out, d
     SpinorView<R> vd{const_cast<SP*>(dot_with), g.V};
     const R cdiag = (R)(scale * diag), chop = (R)(-0.5 * scale);
     const R ref = (R)ef, reb = (R)eb, rbc = (R)t_bc;
-    const int nb = nblocks(g.V);
     const bool dot = dot_with != nullptr;
+    if constexpr (std::is_same<R, float>::value) {
+      if (hop_narrow(g.V)) {
+        constexpr int NT = kHopNarrowThreads, MB = kHopNarrowBlocks;
+        const int nb = (g.V + NT - 1) / NT;
+#define FA_HOPN(A, B, C) hop_kernel<R, A, B, C, NT, MB><<<nb, NT, 0, st>>>(g, U, vin, vout, cdiag, chop, ref, reb, rbc, vd, partials, done)
+        if (!g5in && !g5out && !dot) FA_HOPN(false, false, false);
+        else if (!g5in && g5out && !dot) FA_HOPN(false, true, false);
+        else if (!g5in && g5out && dot) FA_HOPN(false, true, true);
+        else if (g5in && g5out && !dot) FA_HOPN(true, true, false);
+        else if (!g5in && !g5out && dot) FA_HOPN(false, false, true);
+        else return FA_EINVAL;
+#undef FA_HOPN
+        return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA;
+      }
+    }
+    const int nb = nblocks(g.V);
 #define FA_HOP(A, B, C) hop_kernel<R, A, B, C><<<nb, kThreads, 0, st>>>(g, U, vin, vout, cdiag, chop, ref, reb, rbc, vd, partials, done)
     if (!g5in && !g5out && !dot) FA_HOP(false, false, false);
     else if (!g5in && g5out && !dot) FA_HOP(false, true, false);
@@ -83,11 +121,11 @@ int launch_hop_df(const Geom& g, const float4* links, const float4* in, float4* 
     SpinorView<df> vin{const_cast<float4*>(in), g.V};
     SpinorView<df> vout{out, g.V};
     SpinorView<df> vd{const_cast<float4*>(dot_with), g.V};
-    const df cdiag = fromdbl_host(scale * diag), chop = fromdbl_host(-0.5 * scale);
-    const df ref = fromdbl_host(ef), reb = fromdbl_host(eb), rbc = fromdbl_host(t_bc);
-    const int nb = nblocks(g.V);
+    const df cdiag = host_cvt<df>(scale * diag), chop = host_cvt<df>(-0.5 * scale);
+    const df ref = host_cvt<df>(ef), reb = host_cvt<df>(eb), rbc = host_cvt<df>(t_bc);
+    const int nb = row_blocks(g.V);
     const bool dot = dot_with != nullptr;
-#define FA_HOPD(A, B, C) hop_kernel<df, A, B, C><<<nb, kThreads, 0, st>>>(g, U, vin, vout, cdiag, chop, ref, reb, rbc, vd, partials, done)
+#define FA_HOPD(A, B, C) hop_rows_kernel<df, A, B, C><<<nb, kRowThreads, 0, st>>>(g, U, vin, vout, cdiag, chop, ref, reb, rbc, vd, partials, done)
     if (!g5in && !g5out && !dot) FA_HOPD(false, false, false);
     else if (!g5in && g5out && !dot) FA_HOPD(false, true, false);
     else if (!g5in && g5out && dot) FA_HOPD(false, true, true);

@@ -74,6 +74,7 @@ struct fa_ctx {
     fa::DevBuf shiftbuf;                 // sigma, omega, zeta, zeta_p, active, iters
     fa::DevBuf rec;                      // alpha, beta, gamma records
     fa::DevBuf prec, coef, cs;           // per-shift record, pass-2 weights, sweep output
+    fa::DevBuf coef4;                    // pass-2 weights as FP32 pairs (gathers of FP32 / double-float stores)
     fa::DevBuf r64, u64, rt64, r32, u32, rt32;   // seed vectors (l+1 each, contiguous)
     fa::DevBuf y64;                      // accumulated result (FP64 internal)
     fa::DevBuf xs64, us64;               // single-pass shift vectors

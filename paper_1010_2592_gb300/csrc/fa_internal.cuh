@@ -8,6 +8,8 @@
 // Site index s = x + X*(y + Y*(z + Z*t)), as in the canonical layout.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
@@ -19,7 +21,7 @@ namespace fa {
 constexpr int kMaxEll = 8;
 constexpr int kMaxShifts = 64;
 constexpr int kThreads = 256;          // block size of all site kernels
-constexpr int kScalarThreads = 256;    // block size of the single-block scalar kernels
+constexpr int kScalarThreads = 256;    // block size of the single-block kernels (power-iteration norm)
 
 struct Geom {
     int X, Y, Z, T;
@@ -89,6 +91,12 @@ template <> __device__ __forceinline__ df fromdbl<df>(double x) {
     const float h = __double2float_rn(x);
     return {h, __double2float_rn(__dsub_rn(x, (double)h))};
 }
+// the same conversions on the host (kernel arguments)
+template <typename R> inline R host_cvt(double x) { return (R)x; }
+template <> inline df host_cvt<df>(double x) {
+    const float h = (float)x;
+    return df(h, (float)(x - (double)h));
+}
 
 template <typename R> __device__ __forceinline__ cx<R> czero() { return {R(0), R(0)}; }
 template <typename R> __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return {addR(a.r, b.r), addR(a.i, b.i)}; }
@@ -157,6 +165,13 @@ template <> struct SpinorView<double> {
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[(size_t)k * V + s] = make_double2(v[k].r, v[k].i);
     }
+    __device__ __forceinline__ cx<double> ld1(int s, int k) const {
+        const double2 t = __ldg(p + (size_t)k * V + s);
+        return {t.x, t.y};
+    }
+    __device__ __forceinline__ void st1(int s, int k, cx<double> v) const {
+        p[(size_t)k * V + s] = make_double2(v.r, v.i);
+    }
 };
 
 template <> struct SpinorView<float> {
@@ -191,6 +206,13 @@ template <> struct SpinorView<df> {
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[(size_t)k * V + s] = make_float4(v[k].r.hi, v[k].r.lo, v[k].i.hi, v[k].i.lo);
     }
+    __device__ __forceinline__ cx<df> ld1(int s, int k) const {
+        const float4 t = __ldg(p + (size_t)k * V + s);
+        return {df(t.x, t.y), df(t.z, t.w)};
+    }
+    __device__ __forceinline__ void st1(int s, int k, cx<df> v) const {
+        p[(size_t)k * V + s] = make_float4(v.r.hi, v.r.lo, v.i.hi, v.i.lo);
+    }
 };
 
 // bytes of one internal spinor
@@ -209,6 +231,11 @@ template <> struct LinkView<double> {
             double2 t = __ldg(b + (size_t)e * V);
             U[e / 3][e % 3] = {t.x, t.y};
         }
+    }
+    // element (row, col) = e / 3, e % 3
+    __device__ __forceinline__ cx<double> ld1(int mu, int s, int e) const {
+        const double2 t = __ldg(p + ((size_t)mu * 9 + e) * V + s);
+        return {t.x, t.y};
     }
 };
 
@@ -242,47 +269,99 @@ template <> struct LinkView<df> {
             U[e / 3][e % 3] = {df(t.x, t.y), df(t.z, t.w)};
         }
     }
+    __device__ __forceinline__ cx<df> ld1(int mu, int s, int e) const {
+        const float4 t = __ldg(p + ((size_t)mu * 9 + e) * V + s);
+        return {df(t.x, t.y), df(t.z, t.w)};
+    }
 };
 
 // ------------------------------------------------------------------ block reduction
-// Sum K complex values over the block (FP32 values are summed in FP32 within a
-// warp, FP64 and double-float values in FP64; FP64 across warps); thread 0
-// writes them to out[k*stride] as double2.  Deterministic for a fixed launch shape.
-template <typename R> struct WarpSum { using T = double; };
-template <> struct WarpSum<float> { using T = float; };
+// Sum K complex values over the block; thread 0 writes them to
+// out[k*stride + bidx] as double2.  FP64 values are summed in FP64.  FP32
+// values are summed in FP32 within a warp, double-float values in
+// double-float; both then in double-float across warps (FP32 pipe: FP64
+// instructions are scarce on this part), converted to FP64 once.
+// Deterministic for a fixed launch shape.
+__device__ __forceinline__ df shfl_down_df(df a, int o) {
+    return df(__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o));
+}
 
-template <int K, typename R>
-__device__ __forceinline__ void block_reduce_store(cx<R> (&v)[K], double2* out, int stride) {
-    using W = typename WarpSum<R>::T;
-    __shared__ double2 sh[K][kThreads / 32];
+template <int K, typename R, int NT = kThreads>
+__device__ __forceinline__ void block_reduce_store(cx<R> (&v)[K], double2* out, int stride, int bidx) {
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        W a, b;
-        if constexpr (sizeof(W) == 4) { a = v[k].r; b = v[k].i; }
-        else { a = todbl(v[k].r); b = todbl(v[k].i); }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) sh[k][warp] = make_double2((double)a, (double)b);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        constexpr int NW = kThreads / 32;
+    if constexpr (sizeof(R) == 8 && !std::is_same<R, df>::value) {
+        __shared__ double2 sh[K][NW];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double a = 0.0, b = 0.0;
-            if (lane < NW) { a = sh[k][lane].x; b = sh[k][lane].y; }
+            double a = v[k].r, b = v[k].i;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 a += __shfl_down_sync(0xffffffffu, a, o);
                 b += __shfl_down_sync(0xffffffffu, b, o);
             }
-            if (lane == 0) out[(size_t)k * stride + blockIdx.x] = make_double2(a, b);
+            if (lane == 0) sh[k][warp] = make_double2(a, b);
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                double a = 0.0, b = 0.0;
+                if (lane < NW) { a = sh[k][lane].x; b = sh[k][lane].y; }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_down_sync(0xffffffffu, a, o);
+                    b += __shfl_down_sync(0xffffffffu, b, o);
+                }
+                if (lane == 0) out[(size_t)k * stride + bidx] = make_double2(a, b);
+            }
+        }
+    } else {
+        __shared__ float4 sh[K][NW];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if constexpr (std::is_same<R, float>::value) {
+                float a = v[k].r, b = v[k].i;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_down_sync(0xffffffffu, a, o);
+                    b += __shfl_down_sync(0xffffffffu, b, o);
+                }
+                if (lane == 0) sh[k][warp] = make_float4(a, 0.0f, b, 0.0f);
+            } else {
+                df a = v[k].r, b = v[k].i;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a = addR(a, shfl_down_df(a, o));
+                    b = addR(b, shfl_down_df(b, o));
+                }
+                if (lane == 0) sh[k][warp] = make_float4(a.hi, a.lo, b.hi, b.lo);
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            constexpr int TOP = NW > 16 ? 16 : NW > 8 ? 8 : NW > 4 ? 4 : NW > 2 ? 2 : 1;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                df a(0.0f), b(0.0f);
+                if (lane < NW) {
+                    const float4 t = sh[k][lane];
+                    a = df(t.x, t.y);
+                    b = df(t.z, t.w);
+                }
+#pragma unroll
+                for (int o = TOP; o > 0; o >>= 1) {
+                    a = addR(a, shfl_down_df(a, o));
+                    b = addR(b, shfl_down_df(b, o));
+                }
+                if (lane == 0) out[(size_t)k * stride + bidx] = make_double2(todbl(a), todbl(b));
+            }
         }
     }
+}
+template <int K, typename R>
+__device__ __forceinline__ void block_reduce_store(cx<R> (&v)[K], double2* out, int stride) {
+    block_reduce_store<K, R>(v, out, stride, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ operator params
@@ -318,6 +397,10 @@ int launch_unpack_spinor_f64(const Geom& g, const double2* in, double* canon, cu
 int launch_pack_spinor_f32(const Geom& g, const double* canon, float4* out, cudaStream_t st);
 int launch_unpack_spinor_f32(const Geom& g, const float4* in, double* canon, cudaStream_t st);
 int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, float4* ldf, cudaStream_t st);
+// SMs of the current device; whether an FP32 sweep of V sites uses the narrow
+// launch shape (kHopNarrowThreads x kHopNarrowBlocks per SM, one wave)
+int sm_count();
+bool hop_narrow(int V);
 int launch_convert_f64_to_f32(const Geom& g, const double2* in, float4* out, cudaStream_t st);
 // double-float spinors: [12][V] float4 = (re.hi, re.lo, im.hi, im.lo)
 int launch_pack_spinor_df(const Geom& g, const double* canon, float4* out, cudaStream_t st);

@@ -15,51 +15,57 @@
 namespace fa {
 
 // projector P = 1 - S g_MU (S = +1 forward hop, -1 backward hop) applied to
-// the 4 spin x 3 colour spinor p, as the two independent spin rows h0, h1.
-// i*a = (-a.i, a.r).
+// one colour of the spinor (spins a0..a3), as the two independent spin rows
+// h0, h1.  i*a = (-a.i, a.r).
 template <int MU, int S, typename R>
-__device__ __forceinline__ void project(const cx<R> p[12], cx<R> h[6]) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const cx<R> a0 = p[c], a1 = p[3 + c], a2 = p[6 + c], a3 = p[9 + c];
-        if (MU == 0) {        // h0 = a0 - S i a3, h1 = a1 - S i a2
-            h[c] = {a0.r + S * a3.i, a0.i - S * a3.r};
-            h[3 + c] = {a1.r + S * a2.i, a1.i - S * a2.r};
-        } else if (MU == 1) { // h0 = a0 + S a3, h1 = a1 - S a2
-            h[c] = {a0.r + S * a3.r, a0.i + S * a3.i};
-            h[3 + c] = {a1.r - S * a2.r, a1.i - S * a2.i};
-        } else if (MU == 2) { // h0 = a0 - S i a2, h1 = a1 + S i a3
-            h[c] = {a0.r + S * a2.i, a0.i - S * a2.r};
-            h[3 + c] = {a1.r - S * a3.i, a1.i + S * a3.r};
-        } else {              // h0 = a0 - S a2, h1 = a1 - S a3
-            h[c] = {a0.r - S * a2.r, a0.i - S * a2.i};
-            h[3 + c] = {a1.r - S * a3.r, a1.i - S * a3.i};
-        }
+__device__ __forceinline__ void project1(cx<R> a0, cx<R> a1, cx<R> a2, cx<R> a3, cx<R>& h0, cx<R>& h1) {
+    if (MU == 0) {        // h0 = a0 - S i a3, h1 = a1 - S i a2
+        h0 = {a0.r + S * a3.i, a0.i - S * a3.r};
+        h1 = {a1.r + S * a2.i, a1.i - S * a2.r};
+    } else if (MU == 1) { // h0 = a0 + S a3, h1 = a1 - S a2
+        h0 = {a0.r + S * a3.r, a0.i + S * a3.i};
+        h1 = {a1.r - S * a2.r, a1.i - S * a2.i};
+    } else if (MU == 2) { // h0 = a0 - S i a2, h1 = a1 + S i a3
+        h0 = {a0.r + S * a2.i, a0.i - S * a2.r};
+        h1 = {a1.r - S * a3.i, a1.i + S * a3.r};
+    } else {              // h0 = a0 - S a2, h1 = a1 - S a3
+        h0 = {a0.r - S * a2.r, a0.i - S * a2.i};
+        h1 = {a1.r - S * a3.r, a1.i - S * a3.i};
     }
 }
 
-// acc += P psi given the projected, link-multiplied half spinor h.
+// the 4 spin x 3 colour spinor p -> h[c] = h0, h[3 + c] = h1 for every colour
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const cx<R> p[12], cx<R> h[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) project1<MU, S>(p[c], p[3 + c], p[6 + c], p[9 + c], h[c], h[3 + c]);
+}
+
+// one colour of acc += P psi given the link-multiplied spin rows h0, h1
+template <int MU, int S, typename R>
+__device__ __forceinline__ void recon1(cx<R>& c0, cx<R>& c1, cx<R>& c2, cx<R>& c3, cx<R> h0, cx<R> h1) {
+    c0 = cadd(c0, h0);
+    c1 = cadd(c1, h1);
+    if (MU == 0) {        // rows 2,3: S i h1, S i h0
+        c2 = {c2.r - S * h1.i, c2.i + S * h1.r};
+        c3 = {c3.r - S * h0.i, c3.i + S * h0.r};
+    } else if (MU == 1) { // rows 2,3: -S h1, S h0
+        c2 = {c2.r - S * h1.r, c2.i - S * h1.i};
+        c3 = {c3.r + S * h0.r, c3.i + S * h0.i};
+    } else if (MU == 2) { // rows 2,3: S i h0, -S i h1
+        c2 = {c2.r - S * h0.i, c2.i + S * h0.r};
+        c3 = {c3.r + S * h1.i, c3.i - S * h1.r};
+    } else {              // rows 2,3: -S h0, -S h1
+        c2 = {c2.r - S * h0.r, c2.i - S * h0.i};
+        c3 = {c3.r - S * h1.r, c3.i - S * h1.i};
+    }
+}
+
+// acc += P psi given the projected, link-multiplied half spinor h
 template <int MU, int S, typename R>
 __device__ __forceinline__ void recon_add(cx<R> acc[12], const cx<R> h[6]) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const cx<R> h0 = h[c], h1 = h[3 + c];
-        acc[c] = cadd(acc[c], h0);
-        acc[3 + c] = cadd(acc[3 + c], h1);
-        if (MU == 0) {        // rows 2,3: S i h1, S i h0
-            acc[6 + c] = {acc[6 + c].r - S * h1.i, acc[6 + c].i + S * h1.r};
-            acc[9 + c] = {acc[9 + c].r - S * h0.i, acc[9 + c].i + S * h0.r};
-        } else if (MU == 1) { // rows 2,3: -S h1, S h0
-            acc[6 + c] = {acc[6 + c].r - S * h1.r, acc[6 + c].i - S * h1.i};
-            acc[9 + c] = {acc[9 + c].r + S * h0.r, acc[9 + c].i + S * h0.i};
-        } else if (MU == 2) { // rows 2,3: S i h0, -S i h1
-            acc[6 + c] = {acc[6 + c].r - S * h0.i, acc[6 + c].i + S * h0.r};
-            acc[9 + c] = {acc[9 + c].r + S * h1.i, acc[9 + c].i - S * h1.r};
-        } else {              // rows 2,3: -S h0, -S h1
-            acc[6 + c] = {acc[6 + c].r - S * h0.r, acc[6 + c].i - S * h0.i};
-            acc[9 + c] = {acc[9 + c].r - S * h1.r, acc[9 + c].i - S * h1.i};
-        }
-    }
+    for (int c = 0; c < 3; ++c) recon1<MU, S>(acc[c], acc[3 + c], acc[6 + c], acc[9 + c], h[c], h[3 + c]);
 }
 
 template <typename R, bool G5IN>
@@ -149,6 +155,214 @@ __device__ __forceinline__ void hop_site(const Geom& g, const LinkView<R>& U, co
     }
 }
 
+// ------------------------------------------------------------------ colour-row split (double-float)
+// The double-float sweep with one thread per site and output colour row a: a
+// thread projects the neighbour colour by colour and multiplies by row a of U
+// (column a of U^H) as it goes, so it holds two partial products and four
+// accumulators instead of whole spinors.
+//
+// Its arithmetic is compensated rather than renormalised after every
+// operation: each row of U h is one compensated dot product (the Dot2 scheme of
+// Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26 (2005), with FP32-pair
+// inputs).  A value is carried as an FP32 sum s and an FP32 term e; a product
+// adds its rounded value to s by TwoSum and its exact error (FMA), the two
+// hi*lo cross terms and the TwoSum error to e.  Projections and the sum over
+// the eight directions carry (s, e) the same way, and each output component is
+// renormalised once (TwoSum of s and e).  The result has the accuracy of a
+// product in twice the working precision, rounded to an FP32 pair (relative
+// error a few times 2^-44 at most here), at about 70% of the instructions.
+struct dsum {
+    float s, e;
+};
+__device__ __forceinline__ dsum dsum_of(df a) { return {a.hi, a.lo}; }
+__device__ __forceinline__ dsum dneg(dsum a) { return {-a.s, -a.e}; }
+// a + b: TwoSum of the leading parts, the lower parts added to the error term
+__device__ __forceinline__ dsum dadd(dsum a, dsum b) {
+    const float s = __fadd_rn(a.s, b.s);
+    const float bb = __fsub_rn(s, a.s);
+    const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(b.s, bb));
+    return {s, __fadd_rn(t, __fadd_rn(a.e, b.e))};
+}
+// a * b: the rounded product and its exact error plus the cross terms
+__device__ __forceinline__ dsum dmul(dsum a, dsum b) {
+    const float p = __fmul_rn(a.s, b.s);
+    float err = __fmaf_rn(a.s, b.s, -p);
+    err = __fmaf_rn(a.s, b.e, err);
+    err = __fmaf_rn(a.e, b.s, err);
+    return {p, err};
+}
+// A + a * b
+__device__ __forceinline__ dsum dfma(dsum a, dsum b, dsum A) {
+    const float p = __fmul_rn(a.s, b.s);
+    float err = __fmaf_rn(a.s, b.s, -p);
+    err = __fmaf_rn(a.s, b.e, err);
+    err = __fmaf_rn(a.e, b.s, err);
+    const float s = __fadd_rn(A.s, p);
+    const float bb = __fsub_rn(s, A.s);
+    const float t = __fadd_rn(__fsub_rn(A.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    return {s, __fadd_rn(A.e, __fadd_rn(err, t))};
+}
+// renormalised FP32 pair (TwoSum: |e| may exceed |s| after cancellation)
+__device__ __forceinline__ df dnorm(dsum a) { return two_sum(a.s, a.e); }
+
+struct dcs {     // complex (s, e) pairs
+    dsum r, i;
+};
+__device__ __forceinline__ dcs dcs_of(cx<df> a) { return {dsum_of(a.r), dsum_of(a.i)}; }
+
+// projector rows of one colour in (s, e) form (project1 with compensated sums)
+template <int MU, int S>
+__device__ __forceinline__ void project1_c(dcs a0, dcs a1, dcs a2, dcs a3, dcs& h0, dcs& h1) {
+    auto sg = [](dsum x) { return S > 0 ? x : dneg(x); };
+    if (MU == 0) {        // h0 = a0 - S i a3, h1 = a1 - S i a2
+        h0 = {dadd(a0.r, sg(a3.i)), dadd(a0.i, dneg(sg(a3.r)))};
+        h1 = {dadd(a1.r, sg(a2.i)), dadd(a1.i, dneg(sg(a2.r)))};
+    } else if (MU == 1) { // h0 = a0 + S a3, h1 = a1 - S a2
+        h0 = {dadd(a0.r, sg(a3.r)), dadd(a0.i, sg(a3.i))};
+        h1 = {dadd(a1.r, dneg(sg(a2.r))), dadd(a1.i, dneg(sg(a2.i)))};
+    } else if (MU == 2) { // h0 = a0 - S i a2, h1 = a1 + S i a3
+        h0 = {dadd(a0.r, sg(a2.i)), dadd(a0.i, dneg(sg(a2.r)))};
+        h1 = {dadd(a1.r, dneg(sg(a3.i))), dadd(a1.i, sg(a3.r))};
+    } else {              // h0 = a0 - S a2, h1 = a1 - S a3
+        h0 = {dadd(a0.r, dneg(sg(a2.r))), dadd(a0.i, dneg(sg(a2.i)))};
+        h1 = {dadd(a1.r, dneg(sg(a3.r))), dadd(a1.i, dneg(sg(a3.i)))};
+    }
+}
+
+// acc (4 spins of one colour) += P psi given the link-multiplied rows h0, h1
+template <int MU, int S>
+__device__ __forceinline__ void recon1_c(dcs acc[4], dcs h0, dcs h1) {
+    auto sg = [](dsum x) { return S > 0 ? x : dneg(x); };
+    acc[0] = {dadd(acc[0].r, h0.r), dadd(acc[0].i, h0.i)};
+    acc[1] = {dadd(acc[1].r, h1.r), dadd(acc[1].i, h1.i)};
+    if (MU == 0) {        // rows 2,3: S i h1, S i h0
+        acc[2] = {dadd(acc[2].r, dneg(sg(h1.i))), dadd(acc[2].i, sg(h1.r))};
+        acc[3] = {dadd(acc[3].r, dneg(sg(h0.i))), dadd(acc[3].i, sg(h0.r))};
+    } else if (MU == 1) { // rows 2,3: -S h1, S h0
+        acc[2] = {dadd(acc[2].r, dneg(sg(h1.r))), dadd(acc[2].i, dneg(sg(h1.i)))};
+        acc[3] = {dadd(acc[3].r, sg(h0.r)), dadd(acc[3].i, sg(h0.i))};
+    } else if (MU == 2) { // rows 2,3: S i h0, -S i h1
+        acc[2] = {dadd(acc[2].r, dneg(sg(h0.i))), dadd(acc[2].i, sg(h0.r))};
+        acc[3] = {dadd(acc[3].r, sg(h1.i)), dadd(acc[3].i, dneg(sg(h1.r)))};
+    } else {              // rows 2,3: -S h0, -S h1
+        acc[2] = {dadd(acc[2].r, dneg(sg(h0.r))), dadd(acc[2].i, dneg(sg(h0.i)))};
+        acc[3] = {dadd(acc[3].r, dneg(sg(h1.r))), dadd(acc[3].i, dneg(sg(h1.i)))};
+    }
+}
+
+// one hop of row a: acc += w P (U or U^H) psi(nb), link at site ls
+template <int MU, int S, bool WEIGHT, bool G5IN>
+__device__ __forceinline__ void hop_row(dcs acc[4], const SpinorView<df>& in, const LinkView<df>& U, int ls, int nb,
+                                        int a, df w) {
+    dcs t0, t1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dcs p0 = dcs_of(in.ld1(nb, c)), p1 = dcs_of(in.ld1(nb, 3 + c));
+        dcs p2 = dcs_of(in.ld1(nb, 6 + c)), p3 = dcs_of(in.ld1(nb, 9 + c));
+        if (G5IN) {
+            p2 = {dneg(p2.r), dneg(p2.i)};
+            p3 = {dneg(p3.r), dneg(p3.i)};
+        }
+        dcs h0, h1;
+        project1_c<MU, S>(p0, p1, p2, p3, h0, h1);
+        // forward: row a of U_MU(s), L h; backward: column a of U_MU(nb)^H, conj(L) h
+        const dcs L = dcs_of(U.ld1(MU, ls, S > 0 ? a * 3 + c : c * 3 + a));
+        const dsum li = S > 0 ? L.i : dneg(L.i);     // imaginary part of L or conj(L)
+        if (c == 0) {
+            t0 = {dfma(dneg(li), h0.i, dmul(L.r, h0.r)), dfma(li, h0.r, dmul(L.r, h0.i))};
+            t1 = {dfma(dneg(li), h1.i, dmul(L.r, h1.r)), dfma(li, h1.r, dmul(L.r, h1.i))};
+        } else {
+            t0 = {dfma(dneg(li), h0.i, dfma(L.r, h0.r, t0.r)), dfma(li, h0.r, dfma(L.r, h0.i, t0.i))};
+            t1 = {dfma(dneg(li), h1.i, dfma(L.r, h1.r, t1.r)), dfma(li, h1.r, dfma(L.r, h1.i, t1.i))};
+        }
+    }
+    if (WEIGHT) {
+        const dsum ws = dsum_of(w);
+        t0 = {dmul(dsum_of(dnorm(t0.r)), ws), dmul(dsum_of(dnorm(t0.i)), ws)};
+        t1 = {dmul(dsum_of(dnorm(t1.r)), ws), dmul(dsum_of(dnorm(t1.i)), ws)};
+    }
+    recon1_c<MU, S>(acc, t0, t1);
+}
+
+// o[sp] = output component (spin sp, colour a) of the sweep
+template <bool G5IN, bool G5OUT>
+__device__ __forceinline__ void hop_site_row(const Geom& g, const LinkView<df>& U, const SpinorView<df>& in, int s,
+                                             int a, df cdiag, df chop, df ef, df eb, df bc, cx<df> o[4]) {
+    const int X = g.X, Y = g.Y, Z = g.Z, T = g.T;
+    const int x = s % X;
+    const int r1 = s / X;
+    const int y = r1 % Y;
+    const int r2 = r1 / Y;
+    const int z = r2 % Z;
+    const int t = r2 / Z;
+    const int sY = X, sZ = X * Y, sT = X * Y * Z;
+    dcs acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    const df one(1.0f);
+    int nb = (x == X - 1) ? s - (X - 1) : s + 1;
+    hop_row<0, +1, false, G5IN>(acc, in, U, s, nb, a, one);
+    nb = (x == 0) ? s + (X - 1) : s - 1;
+    hop_row<0, -1, false, G5IN>(acc, in, U, nb, nb, a, one);
+    nb = (y == Y - 1) ? s - (Y - 1) * sY : s + sY;
+    hop_row<1, +1, false, G5IN>(acc, in, U, s, nb, a, one);
+    nb = (y == 0) ? s + (Y - 1) * sY : s - sY;
+    hop_row<1, -1, false, G5IN>(acc, in, U, nb, nb, a, one);
+    nb = (z == Z - 1) ? s - (Z - 1) * sZ : s + sZ;
+    hop_row<2, +1, false, G5IN>(acc, in, U, s, nb, a, one);
+    nb = (z == 0) ? s + (Z - 1) * sZ : s - sZ;
+    hop_row<2, -1, false, G5IN>(acc, in, U, nb, nb, a, one);
+    const df wf = (t == T - 1) ? mulR(ef, bc) : ef;
+    const df wb = (t == 0) ? mulR(eb, bc) : eb;
+    nb = (t == T - 1) ? s - (T - 1) * sT : s + sT;
+    hop_row<3, +1, true, G5IN>(acc, in, U, s, nb, a, wf);
+    nb = (t == 0) ? s + (T - 1) * sT : s - sT;
+    hop_row<3, -1, true, G5IN>(acc, in, U, nb, nb, a, wb);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        cx<df> p = in.ld1(s, sp * 3 + a);
+        if (G5IN && sp >= 2) p = {-p.r, -p.i};
+        const bool neg = G5OUT && sp >= 2;
+        const df ca = neg ? -cdiag : cdiag;
+        const df cb = neg ? -chop : chop;
+        const cx<df> h{dnorm(acc[sp].r), dnorm(acc[sp].i)};
+        cx<df> v = cscale(ca, p);
+        v = crfma(cb, h, v);
+        o[sp] = v;
+    }
+}
+
+// Thread layout of the row-split sweep: blocks of kRowThreads = 3 colour rows x
+// 64 sites; warps 2a and 2a+1 take row a of 32 consecutive sites each, so the
+// three rows of a site run on one SM and share its neighbour loads in L1.
+constexpr int kRowSites = 64;
+constexpr int kRowThreads = 3 * kRowSites;
+__device__ __forceinline__ int row_of_thread() { return (int)(threadIdx.x >> 6); }
+__device__ __forceinline__ int site_of_thread() {
+    return (int)blockIdx.x * kRowSites + (int)(threadIdx.x & (kRowSites - 1));
+}
+inline int row_blocks(int V) { return (V + kRowSites - 1) / kRowSites; }
+
+// out(s, row) = hop_site(s) row; DOT: returns <dotv, out> over the thread's 4 components
+template <typename R, bool G5IN, bool G5OUT, bool DOT>
+__device__ __forceinline__ cx<R> hop_rows_body(const Geom& g, const LinkView<R>& U, const SpinorView<R>& in,
+                                               const SpinorView<R>& out, R cdiag, R chop, R ef, R eb, R bc,
+                                               const SpinorView<R>& dotv) {
+    const int a = row_of_thread(), s = site_of_thread();
+    cx<R> dres = czero<R>();
+    if (s < g.V) {
+        cx<R> o[4];
+        hop_site_row<G5IN, G5OUT>(g, U, in, s, a, cdiag, chop, ef, eb, bc, o);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) out.st1(s, sp * 3 + a, o[sp]);
+        if (DOT) {
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp) dres = cjfma(dotv.ld1(s, sp * 3 + a), o[sp], dres);
+        }
+    }
+    return dres;
+}
+
 // FP32: the kernel is bound by load latency (long-scoreboard stalls); the
 // register budget is set for FA_HOP_MINB resident blocks per SM.  Measured on
 // 32^3 x 64: 3 blocks/SM (79 registers) 5.02 TB/s, 4 blocks/SM (64 registers,
@@ -163,6 +377,25 @@ __device__ __forceinline__ void hop_site(const Geom& g, const LinkView<R>& U, co
 #ifndef FA_HOP_MINB_DF
 #define FA_HOP_MINB_DF 2
 #endif
+// row-split double-float sweep: resident blocks of kRowThreads per SM.  Measured
+// per sweep (16^3 x 32 / 32^3 x 64): 3 blocks/SM 0.099 / 1.416 ms, 4 (80
+// registers) 0.099 / 1.409 ms, 5 (64 registers, 16 B spilled) 0.098 / 1.377 ms;
+// the whole-site double-float sweep took 0.169 / 2.65 ms.
+// The variants that also form <dotv, out> and run a scalar step keep one block
+// less (80 registers, no spill).
+#ifndef FA_HOP_ROWS_MINB
+#define FA_HOP_ROWS_MINB 5
+#endif
+template <bool DOT> constexpr int rows_min_blocks() { return DOT ? FA_HOP_ROWS_MINB - 1 : FA_HOP_ROWS_MINB; }
+// FP32 narrow launch shape: 128-thread blocks, 7 per SM (72 registers), used
+// when the whole lattice then fits in one wave (7 x 128 x SMs sites); a lattice
+// a little larger than one wave of the 3 x 256 shape otherwise runs a second,
+// nearly empty wave.
+#ifndef FA_HOP_NARROW_BLOCKS
+#define FA_HOP_NARROW_BLOCKS 7
+#endif
+constexpr int kHopNarrowThreads = 128;
+constexpr int kHopNarrowBlocks = FA_HOP_NARROW_BLOCKS;   // 0: never narrow
 template <typename R> constexpr int hop_min_blocks() {
     return sizeof(R) == 4 ? FA_HOP_MINB : (std::is_same<R, df>::value ? FA_HOP_MINB_DF : 1);
 }

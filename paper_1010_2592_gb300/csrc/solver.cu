@@ -106,7 +106,9 @@ static int apply_A_64(fa_ctx* c, const double2* in, double2* out, double2* tmp, 
 }
 // ------------------------------------------------------------------ small FP64 kernels
 __global__ void k_sc_invnorm(const double2* part, int nblk, double* out) {
-    const dcx v = reduce_partials(part, 1, nblk);
+    __shared__ dcx red[2];
+    reduce_slots<2>(part, nblk, 2, red);
+    const dcx v = red[1];
     if (threadIdx.x == 0) {
         out[0] = 1.0 / sqrt(v.r);
         out[1] = sqrt(v.r);
@@ -133,7 +135,8 @@ static int red_grid_for(int V) { return std::min(nblocks(V), 8 * 152); }
 static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
     const int V = Lo.V, L = Lo.L, ns = c->ns, MO = Lo.max_outer;
     const size_t s64 = (size_t)12 * V * sizeof(double2), s32 = (size_t)6 * V * sizeof(float4);
-    FA_CUDA(c->partials.ensure((size_t)std::max(Lo.nblk, Lo.red_grid) * Lo.part_slots * sizeof(double2)),
+    FA_CUDA(c->partials.ensure(std::max((size_t)std::max(Lo.nblk, Lo.red_grid) * Lo.part_slots,
+                                        (size_t)row_blocks(V)) * sizeof(double2)),
             "alloc partials");
     FA_CUDA(c->state.ensure(sizeof(DevState)), "alloc state");
     FA_CUDA(c->shiftbuf.ensure((size_t)kMaxShifts * (2 * sizeof(double) + 2 * sizeof(double2) + 2 * sizeof(int))),
@@ -141,6 +144,7 @@ static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
     FA_CUDA(c->rec.ensure((size_t)MO * (3 * L + 1) * sizeof(double2)), "alloc record");
     FA_CUDA(c->prec.ensure((size_t)ns * MO * ps_stride(L) * sizeof(double2)), "alloc shift record");
     FA_CUDA(c->coef.ensure((size_t)MO * nc_slots(L) * sizeof(double2)), "alloc weights");
+    FA_CUDA(c->coef4.ensure((size_t)MO * nc_slots(L) * sizeof(float4)), "alloc weights");
     if (!Lo.single) FA_CUDA(c->cs.ensure((size_t)ns * MO * nc_slots(L) * sizeof(double2)), "alloc sweep");
     FA_CUDA(c->y64.ensure(s64), "alloc y");
     if (Lo.need64) {
@@ -195,6 +199,7 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     d.rec_gamma = rb + (size_t)2 * Lo.max_outer * Lo.L;
     d.prec = c->prec.as<double2>();
     d.coef = c->coef.as<double2>();
+    d.coef4 = c->coef4.as<float4>();
     d.cs = Lo.single ? nullptr : c->cs.as<double2>();
     d.r64 = c->r64.as<double2>();
     d.u64 = c->u64.as<double2>();
@@ -247,8 +252,7 @@ template <typename R> constexpr int rp_of() {
 // Pass 1 (pass2 = false): seed recurrence with inner products and the scalar
 // kernels.  Pass 2 (pass2 = true): the same vector kernels with the recorded
 // scalars, no inner products, and y accumulation.  single: shift vectors too.
-// Each launch covers the whole batch (grid.y = systems, or one block per
-// system for the scalar kernels).
+// Each launch covers the whole batch (grid.y = systems).
 template <typename R, int L>
 static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reliable) {
     fa_ctx* c = B.c0;
@@ -270,74 +274,113 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
                        : (T*)(sel == 0 ? (void*)h0.u32 : sel == 1 ? (void*)h0.r32 : (void*)h0.tmp32);
         return base + (size_t)j * (size_t)Ch<R>::N * h0.V;
     };
-    auto hop = [&](int in_sel, int in_j, int out_sel, int out_j, int second, bool dot) -> int {
+    const ScalarStep none{STEP_NONE, 0};
+    auto hop = [&](int in_sel, int in_j, int out_sel, int out_j, int second, bool dot, ScalarStep step) -> int {
         if (timing) hop_timing_begin(c, kind);
         if (n == 1) {
             const T* rt = rp_of<R>() != RP32 ? (const T*)(const void*)h0.rt64 : (const T*)(const void*)h0.rt32;
             const int* done = pass2 ? nullptr : &h0.st->done;
             const double sc = second ? h0.scale : 1.0;
-            int rc;
-            if constexpr (rp_of<R>() == RP64)
-                rc = launch_hop_f64(h0.g, h0.links64, vsel(in_sel, in_j), vsel(out_sel, out_j), h0.diag, h0.ef, h0.eb,
-                                    h0.bc, sc, false, true, dot ? rt : nullptr, h0.part, done, st);
-            else if constexpr (rp_of<R>() == RPDF)
-                rc = launch_hop_df(h0.g, h0.linksdf, vsel(in_sel, in_j), vsel(out_sel, out_j), h0.diag, h0.ef, h0.eb,
-                                   h0.bc, sc, false, true, dot ? rt : nullptr, h0.part, done, st);
-            else
-                rc = launch_hop_f32(h0.g, h0.links32, vsel(in_sel, in_j), vsel(out_sel, out_j), h0.diag, h0.ef, h0.eb,
-                                    h0.bc, sc, false, true, dot ? rt : nullptr, h0.part, done, st);
+            const int V = h0.V;
+            LinkView<R> U;
+            if constexpr (rp_of<R>() == RP64) U = LinkView<R>{h0.links64, V};
+            else if constexpr (rp_of<R>() == RPDF) U = LinkView<R>{h0.linksdf, V};
+            else U = LinkView<R>{h0.links32, V};
+            const SpinorView<R> vin{vsel(in_sel, in_j), V}, vout{vsel(out_sel, out_j), V};
+            const SpinorView<R> vdot{const_cast<T*>(rt), V};
+            const R cdiag = host_cvt<R>(sc * h0.diag), chop = host_cvt<R>(-0.5 * sc);
+            const R ef = host_cvt<R>(h0.ef), eb = host_cvt<R>(h0.eb), bc = host_cvt<R>(h0.bc);
+            if constexpr (rp_of<R>() == RPDF) {
+                const int nbh = row_blocks(V);
+                if (dot)
+                    k_hop1_rows<R, true><<<nbh, kRowThreads, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
+                                                                       vdot, h0.part, done, ds, step);
+                else
+                    k_hop1_rows<R, false><<<nbh, kRowThreads, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
+                                                                        vdot, nullptr, done, ds, none);
+            } else {
+                bool narrow = false;
+                if constexpr (rp_of<R>() == RP32) {
+                    if (hop_narrow(V)) {
+                        narrow = true;
+                        constexpr int NT = kHopNarrowThreads, MB = kHopNarrowBlocks;
+                        const int nbh = (V + NT - 1) / NT;
+                        if (dot)
+                            k_hop1<R, true, NT, MB><<<nbh, NT, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
+                                                                        vdot, h0.part, done, ds, step);
+                        else
+                            k_hop1<R, false, NT, MB><<<nbh, NT, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
+                                                                         vdot, nullptr, done, ds, none);
+                    }
+                }
+                if (!narrow) {
+                    const int nbh = nblocks(V);
+                    if (dot)
+                        k_hop1<R, true><<<nbh, kThreads, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc, vdot,
+                                                                  h0.part, done, ds, step);
+                    else
+                        k_hop1<R, false><<<nbh, kThreads, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc, vdot,
+                                                                   nullptr, done, ds, none);
+                }
+            }
             if (timing) hop_timing_end(c);
-            c->launches++;
-            if (rc != FA_OK) return cuda_fail(cudaGetLastError(), "hop_kernel");
+            FA_LAUNCHED(c, "k_hop1");
             return FA_OK;
         }
-        if (dot) k_hop_sys<R, true><<<gs, kThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2);
-        else k_hop_sys<R, false><<<gs, kThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2);
+        if constexpr (rp_of<R>() == RPDF) {
+            const dim3 gw(row_blocks(h0.V), n);
+            if (dot) k_hop_sys_rows<R, true><<<gw, kRowThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2, step);
+            else k_hop_sys_rows<R, false><<<gw, kRowThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2, none);
+        } else {
+            if (dot) k_hop_sys<R, true><<<gs, kThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2, step);
+            else k_hop_sys<R, false><<<gs, kThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2, none);
+        }
         if (timing) hop_timing_end(c);
         FA_LAUNCHED(c, "k_hop_sys");
         return FA_OK;
     };
+    // Pass 1: the seed parts of the scalar steps run in the last block of the
+    // reduction that precedes them (alpha after <rt, u_{j+1}>, the next beta
+    // after <rt, r_{j+1}>, the MR coefficients after the Gram matrix,
+    // convergence after |r_0|^2); the shift parts in block 0 of the next
+    // vector kernel (double-pass forms) or with the seed part (single pass).
     for (int j = 0; j < L; ++j) {
-        if (!pass2 && j > 0) {
-            k_sc_beta<<<n, kScalarThreads, 0, st>>>(ds, j, nb);
-            FA_LAUNCHED(c, "k_sc_beta");
-        }
         k_update_u<R><<<gs, kThreads, 0, st>>>(ds, j, p2);
         FA_LAUNCHED(c, "k_update_u");
-        FA_TRY(hop(0, j, 2, 0, 0, false));          // tmp = g5 D u_j
-        FA_TRY(hop(2, 0, 0, j + 1, 1, !pass2));     // u_{j+1} = c g5 D tmp, <rt, u_{j+1}>
-        if (!pass2) {
-            k_sc_alpha<<<n, kScalarThreads, 0, st>>>(ds, j, nb);
-            FA_LAUNCHED(c, "k_sc_alpha");
-        }
+        FA_TRY(hop(0, j, 2, 0, 0, false, none));                                   // tmp = g5 D u_j
+        const ScalarStep alpha{single ? STEP_ALPHA_ALL : STEP_ALPHA, j};
+        FA_TRY(hop(2, 0, 0, j + 1, 1, !pass2, pass2 ? none : alpha));              // u_{j+1}
         if (pass2) {
             k_update_r<R, true, false><<<gs, kThreads, 0, st>>>(ds, j, p2);
         } else if (single) {
             if constexpr (rp_of<R>() == RP64) k_update_r<R, false, true><<<gs, kThreads, 0, st>>>(ds, j, p2);
         } else {
-            k_update_r<R, false, false><<<gs, kThreads, 0, st>>>(ds, j, p2);
+            // block 0: shift part of sub-step j beside the vector blocks
+            k_update_r<R, false, false, true><<<dim3(nb + 1, n), kThreads, 0, st>>>(ds, j, p2);
         }
         FA_LAUNCHED(c, "k_update_r");
-        FA_TRY(hop(1, j, 2, 0, 0, false));                      // tmp = g5 D r_j
-        FA_TRY(hop(2, 0, 1, j + 1, 1, !pass2 && j < L - 1));    // r_{j+1} = c g5 D tmp
+        FA_TRY(hop(1, j, 2, 0, 0, false, none));                                   // tmp = g5 D r_j
+        const bool next_beta = !pass2 && j < L - 1;
+        FA_TRY(hop(2, 0, 1, j + 1, 1, next_beta, next_beta ? ScalarStep{STEP_BETA, j + 1} : none));   // r_{j+1}
     }
     if (!pass2) {
-        k_gram<R, L><<<gr, kThreads, 0, st>>>(ds);
+        k_gram<R, L><<<gr, kThreads, 0, st>>>(ds, single ? 1 : 0);
         FA_LAUNCHED(c, "k_gram");
-        k_sc_mr<L><<<n, kScalarThreads, 0, st>>>(ds, rg);
-        FA_LAUNCHED(c, "k_sc_mr");
     }
+    const ScalarStep conv = pass2 ? none : ScalarStep{STEP_CONV, head ? 1 : 0};
     if (pass2) {
-        k_mr<R, L, true, false, false><<<gr, kThreads, 0, st>>>(ds, p2);
+        k_mr<R, L, true, false, false><<<gr, kThreads, 0, st>>>(ds, p2, none);
     } else if (single) {
-        if constexpr (rp_of<R>() == RP64) k_mr<R, L, false, true, true><<<gr, kThreads, 0, st>>>(ds, p2);
+        if constexpr (rp_of<R>() == RP64)
+            k_mr<R, L, false, true, true><<<gr, kThreads, 0, st>>>(ds, p2, reliable ? none : conv);
     } else {
-        k_mr<R, L, false, false, true><<<gr, kThreads, 0, st>>>(ds, p2);
+        // block 0: shift part of the MR step beside the vector blocks
+        k_mr<R, L, false, false, true, true><<<dim3(rg + 1, n), kThreads, 0, st>>>(ds, p2, reliable ? none : conv);
     }
     FA_LAUNCHED(c, "k_mr");
     if (reliable) {
         // r_0 <- b - A x in FP64 (one system): A x through two FP64 hops, then the
-        // replacement and fresh <rt, r_0>, |r_0|^2 for the convergence kernel
+        // replacement and fresh <rt, r_0>, |r_0|^2 for the convergence step
         double2* t1 = c->io64a.as<double2>();
         double2* t2 = c->io64b.as<double2>();
         const int* done = pass2 ? nullptr : &h0.st->done;
@@ -348,13 +391,10 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
                                 nullptr, nullptr, done, st);
         c->launches += 2;
         if (rc != FA_OK) return cuda_fail(cudaGetLastError(), "reliable update");
-        k_reliable<R><<<gr, kThreads, 0, st>>>(ds, t2, p2);
+        k_reliable<R><<<gr, kThreads, 0, st>>>(ds, t2, p2, conv);
         FA_LAUNCHED(c, "k_reliable");
     }
-    if (!pass2) {
-        k_sc_conv<<<n, kScalarThreads, 0, st>>>(ds, rg, head ? 1 : 0);
-        FA_LAUNCHED(c, "k_sc_conv");
-    } else {
+    if (pass2) {
         k_advance<<<n, 1, 0, st>>>(ds);
         FA_LAUNCHED(c, "k_advance");
     }
@@ -651,12 +691,13 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     bool head = mixed;
     for (int i = 0; i < n; ++i) FA_TRY(load_source(B, i, b[i], rp));
     const dim3 gr(Lo.red_grid, n);
-    if (rp == RP64) k_dot2_sys<double><<<gr, kThreads, 0, st>>>(B.dev);
-    else if (rp == RPDF) k_dot2_sys<df><<<gr, kThreads, 0, st>>>(B.dev);
-    else k_dot2_sys<float><<<gr, kThreads, 0, st>>>(B.dev);
+    for (int i = 0; i < n; ++i)
+        FA_CUDA(cudaMemsetAsync(B.host[i].st, 0, sizeof(DevState), st), "clear state");
+    const double theta = mixed ? switch_resid : 0.0;
+    if (rp == RP64) k_dot2_sys<double><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta);
+    else if (rp == RPDF) k_dot2_sys<df><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta);
+    else k_dot2_sys<float><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta);
     FA_LAUNCHED(c0, "k_dot2_sys");
-    k_sc_init<<<n, kScalarThreads, 0, st>>>(B.dev, Lo.red_grid, p->tol, mixed ? switch_resid : 0.0);
-    FA_LAUNCHED(c0, "k_sc_init");
 
     std::vector<DevState> hs(n);
     int switch_outer = -1;
@@ -734,15 +775,16 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         k_coef_reduce<<<dim3((M * NC + 255) / 256, n), 256, 0, st>>>(B.dev);
         FA_LAUNCHED(c0, "k_coef_reduce");
         if (timing) cudaEventRecord(ev[2], st);
-        const dim3 gs(Lo.nblk, n);
         if (pseudo && Kst > 0) {
+            // one thread per site and chunk: 12 chunks per site (FP64, double-float), 6 (FP32)
             if (cap64 > 0) {
-                if (prec == FA_MIXED_DF) k_gather<df><<<gs, kThreads, 0, st>>>(B.dev);
-                else k_gather<double><<<gs, kThreads, 0, st>>>(B.dev);
+                const dim3 gw(Lo.nblk * 12, n);
+                if (prec == FA_MIXED_DF) k_gather<df><<<gw, kThreads, 0, st>>>(B.dev);
+                else k_gather<double><<<gw, kThreads, 0, st>>>(B.dev);
                 FA_LAUNCHED(c0, "k_gather (head store)");
             }
             if (cap32 > 0 && m0_32 >= 0) {
-                k_gather<float><<<gs, kThreads, 0, st>>>(B.dev);
+                k_gather<float><<<dim3(Lo.nblk * 6, n), kThreads, 0, st>>>(B.dev);
                 FA_LAUNCHED(c0, "k_gather<float>");
             }
         }

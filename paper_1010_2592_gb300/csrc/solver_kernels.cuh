@@ -37,7 +37,7 @@ struct DevState {
     int n_outer;     // M, set when pass 1 ends
     int switch_req;  // FA_MIXED: head residuals below the switch threshold
     int max_outer;
-    int pad;
+    unsigned ticket; // blocks of the current reduction that have stored their partials
 };
 
 // Per-shift record of pass 1 at outer iteration m (complex FP64):
@@ -54,7 +54,7 @@ __host__ __device__ constexpr int n_gram(int L) { return (L + 1) * (L + 2) / 2; 
 
 // Everything one system needs on the device.  Kernels read their system's
 // descriptor from an array (ds[blockIdx.y] for site kernels, ds[blockIdx.x]
-// for the single-block scalar kernels), so one launch serves a batch of
+// for the kernels with one block per system), so one launch serves a batch of
 // systems of the same lattice shape; a single solve is a batch of one.
 struct SolverDev {
     DevState* st;
@@ -75,6 +75,7 @@ struct SolverDev {
     double2* rec_gamma;    // [max_outer][L+1]
     double2* prec;         // [ns][max_outer][ps_stride]
     double2* coef;         // [max_outer][nc_slots]
+    float4* coef4;         // the same weights as FP32 pairs (hi, lo) per part
     double2* cs;           // [ns][max_outer][nc_slots]   per-shift sweep output
     // seed vectors: r_0..r_l and u_0..u_l contiguous, the shadow vector, scratch
     double2 *r64, *u64, *rt64, *tmp64;
@@ -190,6 +191,17 @@ template <typename R> __device__ __forceinline__ cx<R> tocx(double2 v) { return 
 template <typename R> __device__ __forceinline__ cx<R> negcx(double2 v) {
     return {fromdbl<R>(-v.x), fromdbl<R>(-v.y)};
 }
+// pass-2 weight k in R from its FP64 and FP32-pair copies (the same value as
+// tocx<R>(cf[k]); the pair form needs no FP64 conversion per thread)
+template <typename R> __device__ __forceinline__ cx<R> weight(const double2* cf, const float4* cf4, size_t k) {
+    if constexpr (std::is_same<R, double>::value) {
+        return tocx<double>(cf[k]);
+    } else {
+        const float4 t = cf4[k];
+        if constexpr (std::is_same<R, float>::value) return {t.x, t.z};
+        else return {df(t.x, t.y), df(t.z, t.w)};
+    }
+}
 
 // y (FP64, [12][V]) += t for the W complex components of chunk q
 template <typename R>
@@ -217,6 +229,409 @@ __device__ __forceinline__ void acc_x(double2* x, int q, int V, int s, double2 a
         t.y = __fma_rn(a.x, vi, t.y);
         t.y = __fma_rn(a.y, vr, t.y);
         *p = t;
+    }
+}
+
+// ------------------------------------------------------------------ scalar steps
+// The scalar steps of the recurrence run inside the vector kernels, in two
+// parts.  The seed part (beta, alpha, the MR coefficients gamma, convergence)
+// runs in the last block of the reduction kernel whose partials it reads: each
+// block stores its partials, fences and takes a ticket, and the block holding
+// the last ticket sums all partials in a fixed order (so the result does not
+// depend on which block finished last) and runs the step.  The shift part (the
+// zeta recurrences and the per-shift scalars of every BiCG sub-step and MR
+// step) is not needed by the next seed-vector kernel: in the double-pass forms
+// it runs in an extra block 0 of that next kernel, beside its vector blocks.
+// Single-pass solves consume the shift scalars at once and run both parts in
+// the last block.
+//
+// FP64 instructions are scarce on this part (one warp instruction occupies a
+// sub-partition's FP64 pipe for tens of cycles, a division for hundreds), so
+// the steps use fused multiply-adds, one real division per complex inverse,
+// and reuse inverses between the per-shift scalars.
+__device__ __forceinline__ bool last_block(DevState* S) {
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // thread 0 stored the block's partials; the fence is cumulative over
+        // what the barrier ordered before it
+        __threadfence();
+        const unsigned t = atomicAdd(&S->ticket, 1u);
+        is_last = t == gridDim.x - 1u;
+        if (is_last) S->ticket = 0u;   // every block of this launch has taken its ticket
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
+__device__ __forceinline__ dcx zmul(dcx a, dcx b) {
+    return {__fma_rn(a.r, b.r, -__dmul_rn(a.i, b.i)), __fma_rn(a.r, b.i, __dmul_rn(a.i, b.r))};
+}
+__device__ __forceinline__ dcx zfma(dcx a, dcx b, dcx c) {   // a b + c
+    return {__fma_rn(a.r, b.r, __fma_rn(-a.i, b.i, c.r)), __fma_rn(a.r, b.i, __fma_rn(a.i, b.r, c.i))};
+}
+__device__ __forceinline__ dcx zrfma(double a, dcx b, dcx c) { return {__fma_rn(a, b.r, c.r), __fma_rn(a, b.i, c.i)}; }
+__device__ __forceinline__ dcx zscale(double a, dcx b) { return {__dmul_rn(a, b.r), __dmul_rn(a, b.i)}; }
+__device__ __forceinline__ dcx zsub(dcx a, dcx b) { return {__dsub_rn(a.r, b.r), __dsub_rn(a.i, b.i)}; }
+__device__ __forceinline__ double zabs2(dcx a) { return __fma_rn(a.r, a.r, __dmul_rn(a.i, a.i)); }
+__device__ __forceinline__ dcx zconj_scale(double a, dcx b) { return {__dmul_rn(a, b.r), -__dmul_rn(a, b.i)}; }
+__device__ __forceinline__ dcx zinv(dcx a) { return zconj_scale(1.0 / zabs2(a), a); }
+__device__ __forceinline__ bool zfinite(dcx a) { return isfinite(a.r) && isfinite(a.i); }
+// 1/p and 1/q (p, q > 0) from one division while p q stays well inside the
+// FP64 range, else from two
+__device__ __forceinline__ void recip2(double p, double q, double& ip, double& iq) {
+    const double pq = __dmul_rn(p, q);
+    if (pq > 1e-280 && pq < 1e280) {
+        const double r = 1.0 / pq;
+        ip = __dmul_rn(q, r);
+        iq = __dmul_rn(p, r);
+    } else {
+        ip = 1.0 / p;
+        iq = 1.0 / q;
+    }
+}
+
+// Sums of the nblk partials of slots 0..ns-1 into out[0..ns-1], fixed order:
+// each slot is split into four quarters, one warp each (consecutive warps sit
+// on different sub-partitions), summed by the lanes in strided order and a
+// shuffle tree; the quarters are then added in order.  Partials are read from
+// L2 (other blocks of the same launch stored them).
+template <int NSMAX>
+__device__ __forceinline__ void reduce_slots(const double2* part, int nblk, int ns, dcx* out) {
+    __shared__ double2 qs[4 * NSMAX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (nblk + 3) >> 2;
+    for (int u = warp; u < 4 * ns; u += nw) {
+        const int k = u >> 2;
+        const int i0 = (u & 3) * per, i1 = min(nblk, i0 + per);
+        double a = 0.0, b = 0.0;
+        // eight loads in flight per lane before the adds (adding the zero
+        // padding leaves the sums unchanged)
+        for (int ib = i0 + lane; ib < i1; ib += 32 * 8) {
+            double2 v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int i = ib + 32 * t;
+                v[t] = i < i1 ? __ldcg(part + (size_t)k * nblk + i) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                a = __dadd_rn(a, v[t].x);
+                b = __dadd_rn(b, v[t].y);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
+            b = __dadd_rn(b, __shfl_down_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) qs[u] = make_double2(a, b);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+        const double2 q0 = qs[4 * k], q1 = qs[4 * k + 1], q2 = qs[4 * k + 2], q3 = qs[4 * k + 3];
+        out[k] = {__dadd_rn(__dadd_rn(q0.x, q1.x), __dadd_rn(q2.x, q3.x)),
+                  __dadd_rn(__dadd_rn(q0.y, q1.y), __dadd_rn(q2.y, q3.y))};
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void fail(DevState* S, int code) {
+    if (S->status == FA_OK) S->status = code;
+    S->done = 1;
+}
+
+// start of pass 1: partials hold <rt, r0> and |r0|^2 with r0 = rt = b
+__device__ __noinline__ void sc_init(const SolverDev& d, int nblk, double tol, double theta) {
+    DevState* S = d.st;
+    __shared__ dcx red[2];
+    reduce_slots<2>(d.part, nblk, 2, red);
+    const dcx rtr = red[0];
+    const double bb = red[1].r;
+    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
+        d.zeta[sh] = pk(mk(1.0));
+        d.zeta_p[sh] = pk(mk(1.0));
+        d.active[sh] = 1;
+        d.iters[sh] = 0;
+    }
+    if (threadIdx.x == 0) {
+        S->bnorm2 = bb;
+        S->tol2b = tol * tol * bb;
+        S->theta2b = theta * theta * bb;
+        S->rnorm2 = bb;
+        S->m = 0;
+        S->done = 0;
+        S->status = FA_OK;
+        S->n_active = d.ns;
+        S->n_outer = 0;
+        S->switch_req = 0;
+        S->max_outer = d.max_outer;
+        S->omega = pk(mk(1.0));
+        S->alpha = pk(mk(0.0));
+        S->alpha_prev = pk(mk(1.0));
+        // first BiCG sub-step: rho0 <- -omega rho0 with rho0 = 1; beta = alpha rho1/rho0 = 0
+        S->rho0 = pk(rtr);
+        d.rec_beta[0] = pk(mk(0.0));
+        if (!(bb > 0.0) || !isfinite(bb)) fail(S, FA_EINVAL);
+    }
+}
+
+// beta of BiCG sub-step j >= 1 from partials of <rt, r_j>
+__device__ __noinline__ void sc_beta(const SolverDev& d, int j, int nblk) {
+    DevState* S = d.st;
+    if (S->done) return;
+    __shared__ dcx red[1];
+    reduce_slots<1>(d.part, nblk, 1, red);
+    if (threadIdx.x == 0) {
+        const dcx rho1 = red[0];
+        const dcx rho0 = ld(S->rho0);
+        if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
+        const dcx beta = zmul(zmul(ld(S->alpha), rho1), zinv(rho0));
+        if (!zfinite(beta)) { fail(S, FA_ENONFINITE); return; }
+        S->rho0 = pk(rho1);
+        d.rec_beta[S->m * d.L + j] = pk(beta);
+    }
+}
+
+// alpha of BiCG sub-step j from partials of <rt, u_{j+1}> (seed part)
+__device__ __noinline__ void sc_alpha_seed(const SolverDev& d, int j, int nblk) {
+    DevState* S = d.st;
+    if (S->done) return;
+    __shared__ dcx red[1];
+    reduce_slots<1>(d.part, nblk, 1, red);
+    if (threadIdx.x == 0) {
+        const dcx den = red[0];
+        if (zabs2(den) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
+        const dcx alpha = zmul(ld(S->rho0), zinv(den));
+        if (!zfinite(alpha)) { fail(S, FA_ENONFINITE); return; }
+        d.rec_alpha[S->m * d.L + j] = pk(alpha);
+        S->alpha = pk(alpha);
+        S->alpha_prev = pk(alpha);
+    }
+}
+
+// Shift part of BiCG sub-step j of the current outer iteration, from the
+// recorded alpha, beta and the previous sub-step's alpha:
+//   zeta_new = (1 + sigma alpha) zeta + (alpha beta / alpha_prev)(zeta' - zeta)
+//   alpha_s = alpha zeta / zeta_new,  beta_s = beta (zeta' / zeta)^2
+// and the weights 1/zeta, 1/(alpha_s zeta) = zeta_new / (alpha zeta^2),
+// 1/(alpha_s zeta_new) = 1/(alpha zeta) that the sweep and the single-pass
+// shift updates use.  One division per shift (recip2).
+__device__ __noinline__ void sc_alpha_shifts(const SolverDev& d, int j) {
+    DevState* S = d.st;
+    if (S->done) return;
+    const int m = S->m;
+    const int t = m * d.L + j;
+    const dcx alpha = ld(d.rec_alpha[t]);
+    const dcx beta = ld(d.rec_beta[t]);
+    const dcx aprev = t > 0 ? ld(d.rec_alpha[t - 1]) : mk(1.0);
+    // 1/alpha and 1/alpha_prev from one division
+    double ina, inp;
+    recip2(zabs2(alpha), zabs2(aprev), ina, inp);
+    const dcx inv_a = zconj_scale(ina, alpha);
+    const dcx inv_p = zconj_scale(inp, aprev);
+    const dcx c1 = zmul(zmul(alpha, beta), inv_p);
+    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
+        if (!d.active[sh]) continue;
+        const double sg = d.sigma[sh];
+        const dcx z = ld(d.zeta[sh]), zp = ld(d.zeta_p[sh]);
+        const dcx zs = zrfma(sg, zmul(alpha, z), z);            // (1 + sigma alpha) zeta
+        const dcx zn = zfma(c1, zsub(zp, z), zs);
+        const double nzn = zabs2(zn);
+        double izn, iz;
+        recip2(nzn, zabs2(z), izn, iz);
+        const dcx inv_zn = zconj_scale(izn, zn);
+        const dcx inv_z = zconj_scale(iz, z);
+        const dcx as = zmul(zmul(alpha, z), inv_zn);
+        const dcx r = zmul(zp, inv_z);
+        const dcx bs = zmul(beta, zmul(r, r));
+        const dcx iaz = zmul(inv_a, inv_z);                       // 1/(alpha zeta)
+        double2* P = d.prec + ((size_t)sh * d.max_outer + m) * ps_stride(d.L) + 5 * j;
+        P[0] = pk(as);
+        P[1] = pk(bs);
+        P[2] = pk(inv_z);
+        P[3] = pk(zmul(zn, zmul(iaz, inv_z)));
+        P[4] = pk(iaz);
+        if (!(nzn > 0.0) || !isfinite(izn) || !zfinite(as) || !zfinite(zn)) fail(S, FA_ENONFINITE);
+        d.zeta_p[sh] = pk(z);
+        d.zeta[sh] = pk(zn);
+    }
+}
+
+// MR coefficients gamma (seed part) from the Gram partials: diagonally scaled
+// normal equations, Gaussian elimination with partial pivoting.
+template <int L>
+__device__ __noinline__ void sc_mr_seed(const SolverDev& d, int nblk) {
+    DevState* S = d.st;
+    if (S->done) return;
+    constexpr int NG = n_gram(L);
+    __shared__ dcx G[NG];
+    reduce_slots<NG>(d.part, nblk, NG, G);
+    if (threadIdx.x != 0) return;
+    int bad = 0;
+    // slot of (i, k), i <= k, in the row-major upper triangle
+    auto slot = [](int i, int k) { return i * (L + 1) - i * (i - 1) / 2 + (k - i); };
+    dcx Ab[L][L + 1];
+    double dsc[L];
+    for (int i = 1; i <= L; ++i) {
+        const double gii = G[slot(i, i)].r;
+        if (!(gii > 0.0) || !isfinite(gii)) bad = FA_EBREAKDOWN;
+        dsc[i - 1] = (gii > 0.0) ? 1.0 / sqrt(gii) : 1.0;
+    }
+    for (int i = 1; i <= L; ++i) {
+        for (int k = 1; k <= L; ++k) {
+            const dcx gik = (i <= k) ? G[slot(i, k)] : conjd(G[slot(k, i)]);
+            Ab[i - 1][k - 1] = zscale(__dmul_rn(dsc[i - 1], dsc[k - 1]), gik);
+        }
+        Ab[i - 1][L] = zscale(dsc[i - 1], conjd(G[slot(0, i)]));   // <r_i, r_0>
+    }
+    // elimination with partial pivoting (the power basis r_1..r_l can make
+    // the normal equations numerically indefinite for large l; any solution
+    // is a valid MR polynomial); one inverse per pivot
+    dcx ipiv[L];
+    for (int k = 0; k < L && !bad; ++k) {
+        int pr = k;
+        double best = zabs2(Ab[k][k]);
+        for (int i = k + 1; i < L; ++i)
+            if (zabs2(Ab[i][k]) > best) { best = zabs2(Ab[i][k]); pr = i; }
+        if (!(best > 0.0)) { bad = FA_EBREAKDOWN; break; }
+        if (pr != k)
+            for (int q = k; q <= L; ++q) { dcx tq = Ab[k][q]; Ab[k][q] = Ab[pr][q]; Ab[pr][q] = tq; }
+        ipiv[k] = zinv(Ab[k][k]);
+        for (int i = k + 1; i < L; ++i) {
+            const dcx f = zmul(Ab[i][k], ipiv[k]);
+            for (int q = k + 1; q <= L; ++q) Ab[i][q] = zsub(Ab[i][q], zmul(f, Ab[k][q]));
+        }
+    }
+    dcx gam[L + 1];
+    if (!bad) {
+        dcx z[L];
+        for (int i = L - 1; i >= 0; --i) {
+            dcx v = Ab[i][L];
+            for (int q = i + 1; q < L; ++q) v = zsub(v, zmul(Ab[i][q], z[q]));
+            z[i] = zmul(v, ipiv[i]);
+        }
+        gam[0] = mk(-1.0);
+        for (int j = 1; j <= L; ++j) {
+            gam[j] = zscale(dsc[j - 1], z[j - 1]);
+            if (!zfinite(gam[j])) bad = FA_ENONFINITE;
+        }
+    }
+    if (bad) { fail(S, bad); return; }
+    const int m = S->m;
+    for (int j = 0; j <= L; ++j) d.rec_gamma[m * (L + 1) + j] = pk(gam[j]);
+    S->omega = pk(gam[L]);
+}
+
+// Shift part of the MR step: p_s = 1 - sum_j gamma_j (-sigma)^j, the weights
+// 1/p_s and c_k/(zeta p_s) with c_k = sum_{j>k} gamma_j (-sigma)^{j-1-k}, and
+// zeta <- zeta p_s, zeta' <- zeta' p_s.  The powers of -sigma are real.
+template <int L>
+__device__ __noinline__ void sc_mr_shifts(const SolverDev& d) {
+    DevState* S = d.st;
+    if (S->done) return;
+    const int m = S->m;
+    dcx gam[L + 1];
+#pragma unroll
+    for (int j = 0; j <= L; ++j) gam[j] = ld(d.rec_gamma[m * (L + 1) + j]);
+    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
+        if (!d.active[sh]) continue;
+        const double ms = -d.sigma[sh];
+        double pw[L + 1];
+        pw[0] = 1.0;
+#pragma unroll
+        for (int j = 1; j <= L; ++j) pw[j] = __dmul_rn(pw[j - 1], ms);
+        dcx ps = mk(1.0);
+#pragma unroll
+        for (int j = 1; j <= L; ++j) ps = zrfma(-pw[j], gam[j], ps);
+        const dcx z = ld(d.zeta[sh]);
+        const dcx zps = zmul(z, ps);
+        const double nps = zabs2(ps);
+        double ips, izps;
+        recip2(nps, zabs2(zps), ips, izps);
+        const dcx inv_ps = zconj_scale(ips, ps);
+        const dcx inv_zps = zconj_scale(izps, zps);
+        double2* P = d.prec + ((size_t)sh * d.max_outer + m) * ps_stride(L) + 5 * L;
+        P[0] = pk(inv_ps);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            dcx c = mk(0.0);
+#pragma unroll
+            for (int j = k + 1; j <= L; ++j) c = zrfma(pw[j - 1 - k], gam[j], c);
+            P[1 + k] = pk(zmul(c, inv_zps));
+        }
+        if (!(nps > 0.0) || !isfinite(ips) || !isfinite(izps) || !zfinite(ps)) fail(S, FA_ENONFINITE);
+        d.zeta[sh] = pk(zps);
+        d.zeta_p[sh] = pk(zmul(ld(d.zeta_p[sh]), ps));
+    }
+}
+
+// end of an outer iteration: convergence and freezing of shifts, next beta
+__device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
+    DevState* S = d.st;
+    if (S->done) return;
+    __shared__ dcx red[2];
+    reduce_slots<2>(d.part, nblk, 2, red);
+    const dcx rtr = red[0];
+    const double rn2 = red[1].r;
+    const int m = S->m;
+    __shared__ int n_act, all_small;
+    if (threadIdx.x == 0) { n_act = 0; all_small = 1; }
+    __syncthreads();
+    const double tol2b = S->tol2b, theta2b = S->theta2b;
+    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
+        if (!d.active[sh]) continue;
+        const double z2 = zabs2(ld(d.zeta[sh]));
+        if (rn2 <= tol2b * z2) {
+            d.active[sh] = 0;
+            d.iters[sh] = m + 1;
+        } else {
+            atomicAdd(&n_act, 1);
+            if (rn2 > theta2b * z2) atomicAnd(&all_small, 0);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    S->rnorm2 = rn2;
+    S->m = m + 1;
+    S->n_active = n_act;
+    if (!isfinite(rn2) || !zfinite(rtr)) { fail(S, FA_ENONFINITE); S->n_outer = m + 1; return; }
+    if (head && all_small) S->switch_req = 1;
+    if (n_act == 0) { S->done = 1; S->n_outer = m + 1; return; }
+    if (m + 1 >= d.max_outer) { fail(S, FA_ENOCONV); S->n_outer = m + 1; return; }
+    const dcx rho0 = zscale(-1.0, zmul(ld(S->omega), ld(S->rho0)));
+    if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); S->n_outer = m + 1; return; }
+    const dcx beta = zmul(zmul(ld(S->alpha), rtr), zinv(rho0));
+    S->rho0 = pk(rtr);
+    d.rec_beta[(m + 1) * d.L] = pk(beta);
+}
+
+// Step run by the last block of a reduction over the pass-1 seed vectors.
+enum StepKind : int {
+    STEP_NONE = 0,
+    STEP_BETA = 1,          // beta of sub-step arg
+    STEP_ALPHA = 2,         // alpha of sub-step arg (seed part)
+    STEP_ALPHA_ALL = 3,     // alpha of sub-step arg, seed and shift parts (single pass)
+    STEP_CONV = 4           // convergence; arg = head flag
+};
+struct ScalarStep {
+    int kind;
+    int arg;
+};
+
+__device__ __forceinline__ void run_step(const SolverDev& d, ScalarStep e, int nblk) {
+    if (e.kind == STEP_NONE || !last_block(d.st)) return;
+    if (e.kind == STEP_BETA) {
+        sc_beta(d, e.arg, nblk);
+    } else if (e.kind == STEP_ALPHA || e.kind == STEP_ALPHA_ALL) {
+        sc_alpha_seed(d, e.arg, nblk);
+        if (e.kind == STEP_ALPHA_ALL) {
+            __syncthreads();
+            sc_alpha_shifts(d, e.arg);
+        }
+    } else {
+        sc_conv(d, nblk, e.arg);
     }
 }
 
@@ -251,12 +666,18 @@ k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
 // ACC (pass 2): y += sum_i coef[m][slot_old(j,i)] r_i(before the update).
 // SHIFTS (single-pass, FP64): the shift-vector updates of the BiCG sub-step,
 // reading each seed vector once for all active shifts.
-template <typename R, bool ACC, bool SHIFTS>
+// XS (pass 1 of the double-pass forms): block 0 runs the shift part of sub-step
+// j (sc_alpha_shifts) beside the vector blocks 1..nblk.
+template <typename R, bool ACC, bool SHIFTS, bool XS = false>
 __global__ void __launch_bounds__(kThreads)
 k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
-    const int s = blockIdx.x * kThreads + threadIdx.x;
+    if (XS && blockIdx.x == 0) {
+        sc_alpha_shifts(d, j);
+        return;
+    }
+    const int s = (blockIdx.x - (XS ? 1 : 0)) * kThreads + threadIdx.x;
     if (s >= d.V) return;
     const int m = d.st->m;
     typename Ch<R>::T* r = Vec<R>::r(d);
@@ -269,7 +690,7 @@ k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
     typename Ch<R>::T* store = pass2 ? nullptr : store_at<R>(d, m);
     const int L = d.L;
     const cx<R> na = negcx<R>(d.rec_alpha[m * L + j]);
-    const double2* cf = d.coef + (size_t)m * nc_slots(L);
+    const size_t cf0 = (size_t)m * nc_slots(L);
 #pragma unroll
     for (int q = 0; q < Ch<R>::N; ++q) {
         cx<R> t[Ch<R>::W];
@@ -280,7 +701,7 @@ k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
             Ch<R> a = Ch<R>::ld(ri, q, d.V, s), b = Ch<R>::ld(u + (i + 1) * vs, q, d.V, s);
             if (store != nullptr) a.stv(store + slot_old(j, i) * vs, q, d.V, s);
             if (ACC) {
-                const cx<R> c = tocx<R>(cf[slot_old(j, i)]);
+                const cx<R> c = weight<R>(d.coef, d.coef4, cf0 + slot_old(j, i));
 #pragma unroll
                 for (int w = 0; w < Ch<R>::W; ++w) t[w] = cfma(c, a.c[w], t[w]);
             }
@@ -336,9 +757,11 @@ k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
 
 // ------------------------------------------------------------------ MR part
 // Gram matrix <r_i, r_k>, 0 <= i <= k <= L, grid-stride, per-block partials.
+// Last block: the MR coefficients (sc_mr_seed) and, for single-pass solves
+// (shifts != 0), their shift part.
 template <typename R, int L>
 __global__ void __launch_bounds__(kThreads)
-k_gram(const SolverDev* __restrict__ ds) {
+k_gram(const SolverDev* __restrict__ ds, int shifts) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, 0)) return;
     const typename Ch<R>::T* r = Vec<R>::r(d);
@@ -366,17 +789,35 @@ k_gram(const SolverDev* __restrict__ ds) {
         }
     }
     block_reduce_store<NG, R>(acc, partials, gridDim.x);
+    if (last_block(d.st)) {
+        sc_mr_seed<L>(d, gridDim.x);
+        if (shifts) {
+            __syncthreads();
+            sc_mr_shifts<L>(d);
+        }
+    }
 }
 
 // MR update: r_0 -= sum gamma_j r_j, u_0 -= sum gamma_j u_j.
 // ACC: y += sum_k coef[m][slot_mr(k)] r_k (before the update).
 // SHIFTS: x_s += sum_k c_k/(zeta p_s) r_k, u^s_0 <- (u^s_0 - sum gamma_j u^s_j)/p_s.
-// DOT: per-block partials of <rt, r_0> (slot 0) and |r_0|^2 (slot 1), grid-stride.
-template <typename R, int L, bool ACC, bool SHIFTS, bool DOT>
+// DOT: per-block partials of <rt, r_0> (slot 0) and |r_0|^2 (slot 1), grid-stride,
+// then `step` (convergence) in the last block.
+// XS (pass 1 of the double-pass forms): block 0 runs the shift part of the MR
+// step (sc_mr_shifts) and takes a ticket too, so that the convergence step sees
+// the new zeta; blocks 1.. are the vector blocks.
+template <typename R, int L, bool ACC, bool SHIFTS, bool DOT, bool XS = false>
 __global__ void __launch_bounds__(kThreads)
-k_mr(const SolverDev* __restrict__ ds, int pass2) {
+k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
+    const unsigned bx = blockIdx.x - (XS ? 1u : 0u), nbx = gridDim.x - (XS ? 1u : 0u);
+    if (XS && blockIdx.x == 0) {
+        sc_mr_shifts<L>(d);
+        __threadfence();   // the new zeta of every thread before the ticket
+        run_step(d, step, nbx);
+        return;
+    }
     const int m = d.st->m;
     typename Ch<R>::T* r = Vec<R>::r(d);
     typename Ch<R>::T* u = Vec<R>::u(d);
@@ -392,9 +833,9 @@ k_mr(const SolverDev* __restrict__ ds, int pass2) {
     ng[0] = czero<R>();
 #pragma unroll
     for (int j = 1; j <= L; ++j) ng[j] = negcx<R>(d.rec_gamma[m * (L + 1) + j]);
-    const double2* cf = d.coef + (size_t)m * nc_slots(L);
+    const size_t cf0 = (size_t)m * nc_slots(L);
     cx<R> dots[2] = {czero<R>(), czero<R>()};
-    for (int s = blockIdx.x * kThreads + threadIdx.x; s < d.V; s += gridDim.x * kThreads) {
+    for (int s = bx * kThreads + threadIdx.x; s < d.V; s += nbx * kThreads) {
 #pragma unroll
         for (int q = 0; q < Ch<R>::N; ++q) {
             Ch<R> rv[L + 1];
@@ -410,7 +851,7 @@ k_mr(const SolverDev* __restrict__ ds, int pass2) {
                 for (int w = 0; w < Ch<R>::W; ++w) t[w] = czero<R>();
 #pragma unroll
                 for (int k = 0; k < L; ++k) {
-                    const cx<R> c = tocx<R>(cf[slot_mr(L, k)]);
+                    const cx<R> c = weight<R>(d.coef, d.coef4, cf0 + slot_mr(L, k));
 #pragma unroll
                     for (int w = 0; w < Ch<R>::W; ++w) t[w] = cfma(c, rv[k].c[w], t[w]);
                 }
@@ -471,7 +912,10 @@ k_mr(const SolverDev* __restrict__ ds, int pass2) {
             }
         }
     }
-    if (DOT) block_reduce_store<2, R>(dots, partials, gridDim.x);
+    if (DOT) {
+        block_reduce_store<2, R>(dots, partials, nbx, bx);
+        run_step(d, step, nbx);
+    }
 }
 
 // <rt, r0> (slot 0) and |r0|^2 (slot 1), grid-stride (start of a solve)
@@ -500,10 +944,12 @@ k_dot2(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0, double2*
     k_dot2_body<R>(V, rt, r0, partials);
 }
 
+// start of pass 1: <rt, r0>, |r0|^2 and, in the last block, the initial state
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_dot2_sys(const SolverDev* __restrict__ ds) {
+__global__ void __launch_bounds__(kThreads) k_dot2_sys(const SolverDev* __restrict__ ds, double tol, double theta) {
     const SolverDev& d = ds[blockIdx.y];
     k_dot2_body<R>(d.V, Vec<R>::rt(d), Vec<R>::r(d), d.part);
+    if (last_block(d.st)) sc_init(d, gridDim.x, tol, theta);
 }
 
 // A application inside the solver: out = scale * g5 D in on the system's own
@@ -518,7 +964,8 @@ __device__ __forceinline__ typename Ch<R>::T* select_vec(const SolverDev& d, int
 
 template <typename R, bool DOT>
 __global__ void __launch_bounds__(kThreads, hop_min_blocks<R>())
-k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2) {
+k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
+          ScalarStep step) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
     const int s = blockIdx.x * kThreads + threadIdx.x;
@@ -541,278 +988,82 @@ k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, i
             dres[0] = a;
         }
     }
-    if (DOT) block_reduce_store<1, R>(dres, d.part, 0);
-}
-
-// ------------------------------------------------------------------ single-block scalar kernels
-// Deterministic reduction of nblk partials of slot `slot` by the whole block.
-__device__ __forceinline__ dcx reduce_partials(const double2* part, int slot, int nblk) {
-    __shared__ double2 red[kScalarThreads];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-        double2 v = part[(size_t)slot * nblk + i];
-        a += v.x;
-        b += v.y;
-    }
-    red[threadIdx.x] = make_double2(a, b);
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            red[threadIdx.x].x += red[threadIdx.x + o].x;
-            red[threadIdx.x].y += red[threadIdx.x + o].y;
-        }
-        __syncthreads();
-    }
-    dcx r = ld(red[0]);
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ void fail(DevState* S, int code) {
-    if (S->status == FA_OK) S->status = code;
-    S->done = 1;
-}
-
-// start of pass 1: partials hold <rt, r0> and |r0|^2 with r0 = rt = b
-__global__ void k_sc_init(const SolverDev* __restrict__ ds, int nblk, double tol, double theta) {
-    const SolverDev& d = ds[blockIdx.x];
-    const double2* part = d.part;
-    DevState* S = d.st;
-    const dcx rtr = reduce_partials(part, 0, nblk);
-    const dcx bb = reduce_partials(part, 1, nblk);
-    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
-        d.zeta[sh] = pk(mk(1.0));
-        d.zeta_p[sh] = pk(mk(1.0));
-        d.active[sh] = 1;
-        d.iters[sh] = 0;
-    }
-    if (threadIdx.x == 0) {
-        S->bnorm2 = bb.r;
-        S->tol2b = tol * tol * bb.r;
-        S->theta2b = theta * theta * bb.r;
-        S->rnorm2 = bb.r;
-        S->m = 0;
-        S->done = 0;
-        S->status = FA_OK;
-        S->n_active = d.ns;
-        S->n_outer = 0;
-        S->switch_req = 0;
-        S->max_outer = d.max_outer;
-        S->omega = pk(mk(1.0));
-        S->alpha = pk(mk(0.0));
-        S->alpha_prev = pk(mk(1.0));
-        // first BiCG sub-step: rho0 <- -omega rho0 with rho0 = 1; beta = alpha rho1/rho0 = 0
-        S->rho0 = pk(rtr);
-        d.rec_beta[0] = pk(mk(0.0));
-        if (!(bb.r > 0.0) || !isfinite(bb.r)) fail(S, FA_EINVAL);
+    if (DOT) {
+        block_reduce_store<1, R>(dres, d.part, 0);
+        run_step(d, step, gridDim.x);
     }
 }
 
-// beta of BiCG sub-step j >= 1 from partials of <rt, r_j>
-__global__ void k_sc_beta(const SolverDev* __restrict__ ds, int j, int nblk) {
-    const SolverDev& d = ds[blockIdx.x];
-    const double2* part = d.part;
-    DevState* S = d.st;
-    if (S->done) return;
-    const dcx rho1 = reduce_partials(part, 0, nblk);
-    if (threadIdx.x == 0) {
-        const dcx rho0 = ld(S->rho0);
-        if (abs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
-        const dcx beta = ld(S->alpha) * rho1 / rho0;
-        if (!finite(beta)) { fail(S, FA_ENONFINITE); return; }
-        S->rho0 = pk(rho1);
-        d.rec_beta[S->m * d.L + j] = pk(beta);
+// double-float batches: the row-split sweep (kRowThreads per block)
+template <typename R, bool DOT>
+__global__ void __launch_bounds__(kRowThreads, rows_min_blocks<DOT>())
+k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
+               ScalarStep step) {
+    const SolverDev& d = ds[blockIdx.y];
+    if (sys_idle(d, pass2)) return;
+    const double sc = second ? d.scale : 1.0;
+    const Geom g = d.g;
+    const SpinorView<R> in{select_vec<R>(d, in_sel, in_j), d.V}, out{select_vec<R>(d, out_sel, out_j), d.V};
+    const SpinorView<R> rt{Vec<R>::rt(d), d.V};
+    cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, Vec<R>::links(d), in, out,
+                                                        fromdbl<R>(sc * d.diag), fromdbl<R>(-0.5 * sc),
+                                                        fromdbl<R>(d.ef), fromdbl<R>(d.eb), fromdbl<R>(d.bc), rt)};
+    if (DOT) {
+        block_reduce_store<1, R, kRowThreads>(dres, d.part, 0, blockIdx.x);
+        run_step(d, step, gridDim.x);
     }
 }
 
-// alpha of BiCG sub-step j from partials of <rt, u_{j+1}>, and the shift scalars
-__global__ void k_sc_alpha(const SolverDev* __restrict__ ds, int j, int nblk) {
-    const SolverDev& d = ds[blockIdx.x];
-    const double2* part = d.part;
-    DevState* S = d.st;
-    if (S->done) return;
-    const dcx den = reduce_partials(part, 0, nblk);
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = (abs2(den) == 0.0) ? FA_EBREAKDOWN : 0;
-    __syncthreads();
-    if (bad) { if (threadIdx.x == 0) fail(S, bad); return; }
-    const int m = S->m;
-    const dcx alpha = ld(S->rho0) / den;
-    const dcx beta = ld(d.rec_beta[m * d.L + j]);
-    const dcx aprev = ld(S->alpha_prev);
-    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
-        if (!d.active[sh]) continue;
-        const double sg = d.sigma[sh];
-        const dcx z = ld(d.zeta[sh]), zp = ld(d.zeta_p[sh]);
-        const dcx zn = (mk(1.0) + sg * alpha) * z + (alpha * beta / aprev) * (zp - z);
-        const dcx as = alpha * z / zn;
-        const dcx r = zp / z;
-        const dcx bs = beta * r * r;
-        double2* P = d.prec + ((size_t)sh * d.max_outer + m) * ps_stride(d.L) + 5 * j;
-        P[0] = pk(as);
-        P[1] = pk(bs);
-        P[2] = pk(mk(1.0) / z);
-        P[3] = pk(mk(1.0) / (as * z));
-        P[4] = pk(mk(1.0) / (as * zn));
-        if (!finite(zn) || abs2(zn) == 0.0 || !finite(as)) fail(S, FA_ENONFINITE);
-        d.zeta_p[sh] = pk(z);
-        d.zeta[sh] = pk(zn);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (!finite(alpha)) { fail(S, FA_ENONFINITE); return; }
-        d.rec_alpha[m * d.L + j] = pk(alpha);
-        S->alpha = pk(alpha);
-        S->alpha_prev = pk(alpha);
+// The hop of a single solve with its pointers as kernel parameters (the
+// descriptor is read only by the scalar step of the last block).  DOT:
+// partials of <dotv, out>, then `step`.  Double-float uses the row-split
+// sweep (kRowThreads per block, one partial per block).
+template <typename R, bool DOT>
+__global__ void __launch_bounds__(kRowThreads, rows_min_blocks<DOT>())
+k_hop1_rows(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb, R bc,
+            SpinorView<R> dotv, double2* partials, const int* done, const SolverDev* __restrict__ ds,
+            ScalarStep step) {
+    if (done != nullptr && *done) return;
+    cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv)};
+    if (DOT) {
+        block_reduce_store<1, R, kRowThreads>(dres, partials, 0, blockIdx.x);
+        run_step(ds[0], step, gridDim.x);
     }
 }
 
-// MR coefficients: gamma from the Gram partials (diagonally scaled normal
-// equations, pivoted elimination), then the shift polynomials p_s(-sigma), c_k.
-template <int L>
-__global__ void k_sc_mr(const SolverDev* __restrict__ ds, int nblk) {
-    const SolverDev& d = ds[blockIdx.x];
-    const double2* part = d.part;
-    DevState* S = d.st;
-    if (S->done) return;
-    constexpr int NG = n_gram(L);
-    __shared__ dcx G[NG];
-    __shared__ dcx gam[L + 1];
-    __shared__ int bad;
-    for (int k = 0; k < NG; ++k) {
-        dcx v = reduce_partials(part, k, nblk);
-        if (threadIdx.x == 0) G[k] = v;
-    }
-    if (threadIdx.x == 0) {
-        bad = 0;
-        // slot of (i, k), i <= k, in the row-major upper triangle
-        auto slot = [](int i, int k) { return i * (L + 1) - i * (i - 1) / 2 + (k - i); };
-        dcx M[L][L], rhs[L];
-        double dsc[L];
-        for (int i = 1; i <= L; ++i) {
-            const double gii = G[slot(i, i)].r;
-            if (!(gii > 0.0) || !isfinite(gii)) bad = FA_EBREAKDOWN;
-            dsc[i - 1] = (gii > 0.0) ? 1.0 / sqrt(gii) : 1.0;
-        }
-        for (int i = 1; i <= L; ++i) {
-            for (int k = 1; k <= L; ++k) {
-                const dcx gik = (i <= k) ? G[slot(i, k)] : conjd(G[slot(k, i)]);
-                M[i - 1][k - 1] = (dsc[i - 1] * dsc[k - 1]) * gik;
-            }
-            rhs[i - 1] = dsc[i - 1] * conjd(G[slot(0, i)]);   // <r_i, r_0>
-        }
-        // Gaussian elimination with partial pivoting on the scaled normal
-        // equations (the power basis r_1..r_l can make them numerically
-        // indefinite for large l; any solution is a valid MR polynomial)
-        dcx Ab[L][L + 1];
-        for (int i = 0; i < L; ++i) {
-            for (int k = 0; k < L; ++k) Ab[i][k] = M[i][k];
-            Ab[i][L] = rhs[i];
-        }
-        for (int k = 0; k < L && !bad; ++k) {
-            int pr = k;
-            double best = abs2(Ab[k][k]);
-            for (int i = k + 1; i < L; ++i)
-                if (abs2(Ab[i][k]) > best) { best = abs2(Ab[i][k]); pr = i; }
-            if (!(best > 0.0)) { bad = FA_EBREAKDOWN; break; }
-            if (pr != k)
-                for (int q = k; q <= L; ++q) { dcx t = Ab[k][q]; Ab[k][q] = Ab[pr][q]; Ab[pr][q] = t; }
-            for (int i = k + 1; i < L; ++i) {
-                const dcx f = Ab[i][k] / Ab[k][k];
-                for (int q = k; q <= L; ++q) Ab[i][q] = Ab[i][q] - f * Ab[k][q];
-            }
-        }
-        if (!bad) {
-            dcx z[L];
-            for (int i = L - 1; i >= 0; --i) {
-                dcx v = Ab[i][L];
-                for (int q = i + 1; q < L; ++q) v = v - Ab[i][q] * z[q];
-                z[i] = v / Ab[i][i];
-            }
-            gam[0] = mk(-1.0);
-            for (int j = 1; j <= L; ++j) {
-                gam[j] = dsc[j - 1] * z[j - 1];
-                if (!finite(gam[j])) bad = FA_ENONFINITE;
-            }
-        }
-        if (bad) fail(S, bad);
-    }
-    __syncthreads();
-    if (bad) return;
-    const int m = S->m;
-    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
-        if (!d.active[sh]) continue;
-        const dcx ms = mk(-d.sigma[sh]);
-        dcx pw[L + 1];
-        pw[0] = mk(1.0);
-        for (int j = 1; j <= L; ++j) pw[j] = pw[j - 1] * ms;
-        dcx ps = mk(1.0);
-        for (int j = 1; j <= L; ++j) ps = ps - gam[j] * pw[j];
-        const dcx z = ld(d.zeta[sh]);
-        double2* P = d.prec + ((size_t)sh * d.max_outer + m) * ps_stride(L) + 5 * L;
-        const dcx zps = z * ps;
-        P[0] = pk(mk(1.0) / ps);
-        for (int k = 0; k < L; ++k) {
-            dcx c = mk(0.0);
-            for (int j = k + 1; j <= L; ++j) c = c + gam[j] * pw[j - 1 - k];
-            P[1 + k] = pk(c / zps);
-        }
-        if (abs2(ps) == 0.0 || !finite(ps)) fail(S, FA_ENONFINITE);
-        d.zeta[sh] = pk(zps);
-        d.zeta_p[sh] = pk(ld(d.zeta_p[sh]) * ps);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int j = 0; j <= L; ++j) d.rec_gamma[m * (L + 1) + j] = pk(gam[j]);
-        S->omega = pk(gam[L]);
-    }
-}
-
-// end of an outer iteration: convergence and freezing of shifts, next beta
-__global__ void k_sc_conv(const SolverDev* __restrict__ ds, int nblk, int head) {
-    const SolverDev& d = ds[blockIdx.x];
-    const double2* part = d.part;
-    DevState* S = d.st;
-    if (S->done) return;
-    const dcx rtr = reduce_partials(part, 0, nblk);
-    const double rn2 = reduce_partials(part, 1, nblk).r;
-    const int m = S->m;
-    __shared__ int n_act, all_small;
-    if (threadIdx.x == 0) { n_act = 0; all_small = 1; }
-    __syncthreads();
-    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
-        if (!d.active[sh]) continue;
-        const double z2 = abs2(ld(d.zeta[sh]));
-        if (rn2 <= S->tol2b * z2) {
-            d.active[sh] = 0;
-            d.iters[sh] = m + 1;
-        } else {
-            atomicAdd(&n_act, 1);
-            if (rn2 > S->theta2b * z2) atomicAnd(&all_small, 0);
+template <typename R, bool DOT, int NT = kThreads, int MB = hop_min_blocks<R>()>
+__global__ void __launch_bounds__(NT, MB)
+k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb, R bc,
+       SpinorView<R> dotv, double2* partials, const int* done, const SolverDev* __restrict__ ds, ScalarStep step) {
+    if (done != nullptr && *done) return;
+    const int s = blockIdx.x * NT + threadIdx.x;
+    cx<R> dres[1] = {czero<R>()};
+    if (s < g.V) {
+        cx<R> p[12];
+        hop_site<R, false, true>(g, U, in, s, cdiag, chop, ef, eb, bc, p);
+        out.store(s, p);
+        if (DOT) {
+            cx<R> q[12];
+            dotv.load(s, q);
+            cx<R> a = czero<R>();
+#pragma unroll
+            for (int k = 0; k < 12; ++k) a = cjfma(q[k], p[k], a);
+            dres[0] = a;
         }
     }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    S->rnorm2 = rn2;
-    S->m = m + 1;
-    S->n_active = n_act;
-    if (!isfinite(rn2) || !finite(rtr)) { fail(S, FA_ENONFINITE); S->n_outer = m + 1; return; }
-    if (head && all_small) S->switch_req = 1;
-    if (n_act == 0) { S->done = 1; S->n_outer = m + 1; return; }
-    if (m + 1 >= d.max_outer) { fail(S, FA_ENOCONV); S->n_outer = m + 1; return; }
-    const dcx rho0 = -1.0 * (ld(S->omega) * ld(S->rho0));
-    if (abs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); S->n_outer = m + 1; return; }
-    const dcx beta = ld(S->alpha) * rtr / rho0;
-    S->rho0 = pk(rtr);
-    d.rec_beta[(m + 1) * d.L] = pk(beta);
+    if (DOT) {
+        block_reduce_store<1, R, NT>(dres, partials, 0, blockIdx.x);
+        run_step(ds[0], step, gridDim.x);
+    }
 }
 
 // ------------------------------------------------------------------ reliable update
 // r_0 <- b - A x with A x (FP64) already in ax; the new r_0 is rounded to R.
 // Rewrites the partials of <rt, r_0> (slot 0) and |r_0|^2 (slot 1) that the
-// convergence kernel reads, grid-stride like k_mr.
+// convergence step reads, grid-stride like k_mr.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_reliable(const SolverDev* __restrict__ ds, const double2* ax, int pass2) {
+__global__ void __launch_bounds__(kThreads)
+k_reliable(const SolverDev* __restrict__ ds, const double2* ax, int pass2, ScalarStep step) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
     typename Ch<R>::T* r0 = Vec<R>::r(d);
@@ -839,18 +1090,51 @@ __global__ void __launch_bounds__(kThreads) k_reliable(const SolverDev* __restri
         }
     }
     block_reduce_store<2, R>(dots, d.part, gridDim.x);
+    run_step(d, step, gridDim.x);
 }
 
 // ------------------------------------------------------------------ pseudo-double-pass gather
 // y += sum_{m in [m_begin, m_end)} sum_k coef[m][k] v(m, k), the stored seed-vector
-// occurrences of pass 1 (store slot (m - m0) * NC + k).  Terms are summed in R
-// in groups of four, each group added to y in FP64.
+// occurrences of pass 1 (store slot (m - m0) * NC + k).  One thread per site and
+// chunk (grid.x = chunks x site blocks), so a thread holds a few accumulators and
+// many loads stay in flight.  Terms are summed in R in groups of four; each group
+// enters a compensated FP32-pair accumulator (FP64 for an FP64 store), which is
+// added to y in FP64 once.
+template <typename R> struct GatherAcc {        // FP32 and double-float stores
+    df a[2 * Ch<R>::W];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < 2 * Ch<R>::W; ++k) a[k] = df(0.0f);
+    }
+    __device__ __forceinline__ static df widen(float x) { return df(x); }
+    __device__ __forceinline__ static df widen(df x) { return x; }
+    __device__ __forceinline__ void add(const cx<R> (&t)[Ch<R>::W]) {
+#pragma unroll
+        for (int w = 0; w < Ch<R>::W; ++w) {
+            a[2 * w] = addR(a[2 * w], widen(t[w].r));
+            a[2 * w + 1] = addR(a[2 * w + 1], widen(t[w].i));
+        }
+    }
+    __device__ __forceinline__ double get(int k) const { return todbl(a[k]); }
+};
+template <> struct GatherAcc<double> {
+    double a[2];
+    __device__ __forceinline__ void zero() { a[0] = a[1] = 0.0; }
+    __device__ __forceinline__ void add(const cx<double> (&t)[1]) {
+        a[0] = __dadd_rn(a[0], t[0].r);
+        a[1] = __dadd_rn(a[1], t[0].i);
+    }
+    __device__ __forceinline__ double get(int k) const { return a[k]; }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_gather(const SolverDev* __restrict__ ds) {
     const SolverDev& d = ds[blockIdx.y];
-    const int s = blockIdx.x * kThreads + threadIdx.x;
-    if (s >= d.V) return;
+    const int nsb = (d.V + kThreads - 1) / kThreads;
+    const int q = blockIdx.x / nsb;
+    const int s = (blockIdx.x - q * nsb) * kThreads + threadIdx.x;
+    if (q >= Ch<R>::N || s >= d.V) return;
     const int M = d.st->n_outer;
     int m_begin, m_end, m0;
     const typename Ch<R>::T* store;
@@ -869,41 +1153,47 @@ k_gather(const SolverDev* __restrict__ ds) {
     }
     if (m_end <= m_begin) return;
     const size_t vs = vstride<R>(d);
-    double2* y = d.y;
     const int NC = nc_slots(d.L);
     const int n = (m_end - m_begin) * NC;
-    const double2* cf = d.coef + (size_t)m_begin * NC;
+    const size_t cf0 = (size_t)m_begin * NC;
     const typename Ch<R>::T* base = store + (size_t)(m_begin - m0) * NC * vs;
-    double acc[24];
+    constexpr int W = Ch<R>::W;
+    GatherAcc<R> acc;
+    acc.zero();
+    int k0 = 0;
+    for (; k0 + 4 <= n; k0 += 4) {
+        Ch<R> v[4];
 #pragma unroll
-    for (int k = 0; k < 24; ++k) acc[k] = 0.0;
-    for (int k0 = 0; k0 < n; k0 += 4) {
-        cx<R> t[12];
+        for (int g = 0; g < 4; ++g) v[g] = Ch<R>::ld(base + (size_t)(k0 + g) * vs, q, d.V, s);
+        cx<R> t[W];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) t[k] = czero<R>();
-        const int k1 = min(n, k0 + 4);
-        for (int k = k0; k < k1; ++k) {
-            const cx<R> c = tocx<R>(cf[k]);
-            const typename Ch<R>::T* v = base + (size_t)k * vs;
+        for (int w = 0; w < W; ++w) t[w] = czero<R>();
 #pragma unroll
-            for (int q = 0; q < Ch<R>::N; ++q) {
-                Ch<R> a = Ch<R>::ld(v, q, d.V, s);
+        for (int g = 0; g < 4; ++g) {
+            const cx<R> c = weight<R>(d.coef, d.coef4, cf0 + k0 + g);
 #pragma unroll
-                for (int w = 0; w < Ch<R>::W; ++w) t[q * Ch<R>::W + w] = cfma(c, a.c[w], t[q * Ch<R>::W + w]);
-            }
+            for (int w = 0; w < W; ++w) t[w] = cfma(c, v[g].c[w], t[w]);
         }
+        acc.add(t);
+    }
+    if (k0 < n) {
+        cx<R> t[W];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            acc[2 * k] = __dadd_rn(acc[2 * k], todbl(t[k].r));
-            acc[2 * k + 1] = __dadd_rn(acc[2 * k + 1], todbl(t[k].i));
+        for (int w = 0; w < W; ++w) t[w] = czero<R>();
+        for (int k = k0; k < n; ++k) {
+            const Ch<R> v = Ch<R>::ld(base + (size_t)k * vs, q, d.V, s);
+            const cx<R> c = weight<R>(d.coef, d.coef4, cf0 + k);
+#pragma unroll
+            for (int w = 0; w < W; ++w) t[w] = cfma(c, v.c[w], t[w]);
         }
+        acc.add(t);
     }
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        double2* p = y + (size_t)k * d.V + s;
+    for (int w = 0; w < W; ++w) {
+        double2* p = d.y + (size_t)(q * W + w) * d.V + s;
         double2 a = *p;
-        a.x = __dadd_rn(a.x, acc[2 * k]);
-        a.y = __dadd_rn(a.y, acc[2 * k + 1]);
+        a.x = __dadd_rn(a.x, acc.get(2 * w));
+        a.y = __dadd_rn(a.y, acc.get(2 * w + 1));
         *p = a;
     }
 }
@@ -998,6 +1288,10 @@ __global__ void k_coef_reduce(const SolverDev* __restrict__ ds) {
         a = a + d.omega[sh] * ld(d.cs[((size_t)sh * d.max_outer + m) * NC + k]);
     }
     d.coef[(size_t)m * NC + k] = pk(a);
+    // the same weight as an FP32 pair per part (hi = FP32 rounding, lo = rest)
+    const float hr = __double2float_rn(a.r), hi = __double2float_rn(a.i);
+    d.coef4[(size_t)m * NC + k] = make_float4(hr, __double2float_rn(__dsub_rn(a.r, (double)hr)),
+                                              hi, __double2float_rn(__dsub_rn(a.i, (double)hi)));
 }
 
 // single-pass result y = sum_s omega_s x_s (FP64 [12][V]) of each system

@@ -43,7 +43,7 @@ def workload_case(name, dims=None):
     return w
 
 
-@functools.lru_cache(maxsize=16)
+@functools.lru_cache(maxsize=64)
 def oracle_double(name, dims, ell, tol):
     w = workload_case(name, dims)
     op = dirac.Operator(w["U"], w["mass"], w["mu"], w["c"], w["t_bc"])
@@ -52,7 +52,7 @@ def oracle_double(name, dims, ell, tol):
     return y, st
 
 
-@functools.lru_cache(maxsize=16)
+@functools.lru_cache(maxsize=64)
 def oracle_single(name, dims, ell, tol):
     w = workload_case(name, dims)
     op = dirac.Operator(w["U"], w["mass"], w["mu"], w["c"], w["t_bc"])

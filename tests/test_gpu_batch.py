@@ -62,14 +62,16 @@ def test_batched_equals_one_at_a_time(mode, precision):
 
 def test_batched_against_oracle():
     ctxs, srcs, (a, _, _) = build_batch()
-    ys, _ = fa.apply_f_batched(ctxs, srcs, ell=2, tol=1e-10, mode="pseudo", precision="f64")
+    # both solves at tol 1e-12, so that the comparison at 1e-10 is not limited by
+    # where each stops
+    ys, _ = fa.apply_f_batched(ctxs, srcs, ell=2, tol=1e-12, mode="pseudo", precision="f64")
     d1 = (4, 4, 4, 8)
     U = inputs.su3_exp_gauge(d1, 0.5, 301)
     c = scale.power_scale(dirac.Operator(U, -1.8, 0.05).A, inputs.gaussian_spinor(d1, 304), 100)
     om, sg = fa.neuberger_poles(10)
     from oracle import msbicgstab as ms
     op = dirac.Operator(U, -1.8, 0.05, c)
-    y_o = ms.multishift_double(op.A, inputs.gaussian_spinor(d1, 9), sg, om, 2, 1e-10)
+    y_o = ms.multishift_double(op.A, inputs.gaussian_spinor(d1, 9), sg, om, 2, 1e-12)
     assert rel(to_host(ys[5]), y_o) < 1e-10
 
 

