@@ -277,10 +277,11 @@ template <> struct LinkView<df> {
 
 // ------------------------------------------------------------------ block reduction
 // Sum K complex values over the block; thread 0 writes them to
-// out[k*stride + bidx] as double2.  FP64 values are summed in FP64.  FP32
-// values are summed in FP32 within a warp, double-float values in
-// double-float; both then in double-float across warps (FP32 pipe: FP64
-// instructions are scarce on this part), converted to FP64 once.
+// out[k*stride + bidx].  FP64 values are summed in FP64 and stored as double2.
+// FP32 values are summed in FP32 within a warp, double-float values in
+// double-float; both then in double-float across warps and stored as an FP32
+// pair per part (float4: re.hi, re.lo, im.hi, im.lo) in the same 16 bytes, so
+// that no FP64 instruction is spent (they are scarce on this part).
 // Deterministic for a fixed launch shape.
 __device__ __forceinline__ df shfl_down_df(df a, int o) {
     return df(__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o));
@@ -354,7 +355,8 @@ __device__ __forceinline__ void block_reduce_store(cx<R> (&v)[K], double2* out, 
                     a = addR(a, shfl_down_df(a, o));
                     b = addR(b, shfl_down_df(b, o));
                 }
-                if (lane == 0) out[(size_t)k * stride + bidx] = make_double2(todbl(a), todbl(b));
+                if (lane == 0)
+                    reinterpret_cast<float4*>(out)[(size_t)k * stride + bidx] = make_float4(a.hi, a.lo, b.hi, b.lo);
             }
         }
     }

@@ -254,14 +254,18 @@ __device__ __forceinline__ bool last_block(DevState* S) {
     __syncthreads();
     if (threadIdx.x == 0) {
         // thread 0 stored the block's partials; the fence is cumulative over
-        // what the barrier ordered before it
+        // what the barrier ordered before it (release), and the one after the
+        // last ticket orders the reads that follow (acquire; the other threads
+        // read the partials after the barrier, from L2)
         __threadfence();
         const unsigned t = atomicAdd(&S->ticket, 1u);
         is_last = t == gridDim.x - 1u;
-        if (is_last) S->ticket = 0u;   // every block of this launch has taken its ticket
+        if (is_last) {
+            S->ticket = 0u;   // every block of this launch has taken its ticket
+            __threadfence();
+        }
     }
     __syncthreads();
-    if (is_last) __threadfence();
     return is_last != 0;
 }
 
@@ -278,6 +282,14 @@ __device__ __forceinline__ double zabs2(dcx a) { return __fma_rn(a.r, a.r, __dmu
 __device__ __forceinline__ dcx zconj_scale(double a, dcx b) { return {__dmul_rn(a, b.r), -__dmul_rn(a, b.i)}; }
 __device__ __forceinline__ dcx zinv(dcx a) { return zconj_scale(1.0 / zabs2(a), a); }
 __device__ __forceinline__ bool zfinite(dcx a) { return isfinite(a.r) && isfinite(a.i); }
+// 2^-floor(e/2) for x = f 2^e (x > 0, normal): x * result^2 lies in [1, 4).
+// Integer work on the exponent bits only.
+__device__ __forceinline__ double pow2_rsqrt(double x) {
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    const int h = e >= 0 ? e / 2 : -((1 - e) / 2);     // floor(e / 2)
+    return __longlong_as_double((long long)(1023 - h) << 52);
+}
 // 1/p and 1/q (p, q > 0) from one division while p q stays well inside the
 // FP64 range, else from two
 __device__ __forceinline__ void recip2(double p, double q, double& ip, double& iq) {
@@ -296,43 +308,88 @@ __device__ __forceinline__ void recip2(double p, double q, double& ip, double& i
 // each slot is split into four quarters, one warp each (consecutive warps sit
 // on different sub-partitions), summed by the lanes in strided order and a
 // shuffle tree; the quarters are then added in order.  Partials are read from
-// L2 (other blocks of the same launch stored them).
-template <int NSMAX>
+// L2 (other blocks of the same launch stored them).  DFP: the partials are
+// FP32 pairs (float4: re.hi, re.lo, im.hi, im.lo; the FP32 and double-float
+// kernels store them so) and are summed in double-float on the FP32 pipe;
+// otherwise FP64 values summed in FP64.
+template <typename R> constexpr bool dfp_of() { return !std::is_same<R, double>::value; }
+
+template <int NSMAX, bool DFP>
 __device__ __forceinline__ void reduce_slots(const double2* part, int nblk, int ns, dcx* out) {
     __shared__ double2 qs[4 * NSMAX];
+    __shared__ float4 qf[4 * NSMAX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int per = (nblk + 3) >> 2;
     for (int u = warp; u < 4 * ns; u += nw) {
         const int k = u >> 2;
         const int i0 = (u & 3) * per, i1 = min(nblk, i0 + per);
-        double a = 0.0, b = 0.0;
-        // eight loads in flight per lane before the adds (adding the zero
-        // padding leaves the sums unchanged)
-        for (int ib = i0 + lane; ib < i1; ib += 32 * 8) {
-            double2 v[8];
+        if constexpr (DFP) {
+            const float4* pf = reinterpret_cast<const float4*>(part) + (size_t)k * nblk;
+            df a(0.0f), b(0.0f);
+            // eight loads in flight per lane before the adds (zero padding
+            // leaves the sums unchanged)
+            for (int ib = i0 + lane; ib < i1; ib += 32 * 8) {
+                float4 v[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int i = ib + 32 * t;
-                v[t] = i < i1 ? __ldcg(part + (size_t)k * nblk + i) : make_double2(0.0, 0.0);
+                for (int t = 0; t < 8; ++t) {
+                    const int i = ib + 32 * t;
+                    v[t] = i < i1 ? __ldcg(pf + i) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    a = addR(a, df(v[t].x, v[t].y));
+                    b = addR(b, df(v[t].z, v[t].w));
+                }
             }
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                a = __dadd_rn(a, v[t].x);
-                b = __dadd_rn(b, v[t].y);
+            for (int o = 16; o > 0; o >>= 1) {
+                a = addR(a, shfl_down_df(a, o));
+                b = addR(b, shfl_down_df(b, o));
             }
-        }
+            if (lane == 0) qf[u] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        } else {
+            const double2* pd = part + (size_t)k * nblk;
+            double a = 0.0, b = 0.0;
+            for (int ib = i0 + lane; ib < i1; ib += 32 * 8) {
+                double2 v[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
-            b = __dadd_rn(b, __shfl_down_sync(0xffffffffu, b, o));
+                for (int t = 0; t < 8; ++t) {
+                    const int i = ib + 32 * t;
+                    v[t] = i < i1 ? __ldcg(pd + i) : make_double2(0.0, 0.0);
+                }
+                const int nt = min(8, (i1 - ib + 31) >> 5);   // loads that hit (FP64 adds are scarce)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    if (t < nt) {
+                        a = __dadd_rn(a, v[t].x);
+                        b = __dadd_rn(b, v[t].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a = __dadd_rn(a, __shfl_down_sync(0xffffffffu, a, o));
+                b = __dadd_rn(b, __shfl_down_sync(0xffffffffu, b, o));
+            }
+            if (lane == 0) qs[u] = make_double2(a, b);
         }
-        if (lane == 0) qs[u] = make_double2(a, b);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-        const double2 q0 = qs[4 * k], q1 = qs[4 * k + 1], q2 = qs[4 * k + 2], q3 = qs[4 * k + 3];
-        out[k] = {__dadd_rn(__dadd_rn(q0.x, q1.x), __dadd_rn(q2.x, q3.x)),
-                  __dadd_rn(__dadd_rn(q0.y, q1.y), __dadd_rn(q2.y, q3.y))};
+        if constexpr (DFP) {
+            df a(0.0f), b(0.0f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 t = qf[4 * k + q];
+                a = addR(a, df(t.x, t.y));
+                b = addR(b, df(t.z, t.w));
+            }
+            out[k] = {todbl(a), todbl(b)};
+        } else {
+            const double2 q0 = qs[4 * k], q1 = qs[4 * k + 1], q2 = qs[4 * k + 2], q3 = qs[4 * k + 3];
+            out[k] = {__dadd_rn(__dadd_rn(q0.x, q1.x), __dadd_rn(q2.x, q3.x)),
+                      __dadd_rn(__dadd_rn(q0.y, q1.y), __dadd_rn(q2.y, q3.y))};
+        }
     }
     __syncthreads();
 }
@@ -343,10 +400,11 @@ __device__ __forceinline__ void fail(DevState* S, int code) {
 }
 
 // start of pass 1: partials hold <rt, r0> and |r0|^2 with r0 = rt = b
+template <bool DFP>
 __device__ __noinline__ void sc_init(const SolverDev& d, int nblk, double tol, double theta) {
     DevState* S = d.st;
     __shared__ dcx red[2];
-    reduce_slots<2>(d.part, nblk, 2, red);
+    reduce_slots<2, DFP>(d.part, nblk, 2, red);
     const dcx rtr = red[0];
     const double bb = red[1].r;
     for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
@@ -378,34 +436,42 @@ __device__ __noinline__ void sc_init(const SolverDev& d, int nblk, double tol, d
 }
 
 // beta of BiCG sub-step j >= 1 from partials of <rt, r_j>
+template <bool DFP>
 __device__ __noinline__ void sc_beta(const SolverDev& d, int j, int nblk) {
     DevState* S = d.st;
-    if (S->done) return;
+    // state loads and the inverse of rho0 before the reduction
+    const int done = S->done, m = S->m;
+    const dcx rho0 = ld(S->rho0), alpha = ld(S->alpha);
+    if (done) return;
+    dcx a_rho = mk(0.0);
+    if (threadIdx.x == 0 && zabs2(rho0) != 0.0) a_rho = zmul(alpha, zinv(rho0));
     __shared__ dcx red[1];
-    reduce_slots<1>(d.part, nblk, 1, red);
+    reduce_slots<1, DFP>(d.part, nblk, 1, red);
     if (threadIdx.x == 0) {
         const dcx rho1 = red[0];
-        const dcx rho0 = ld(S->rho0);
         if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
-        const dcx beta = zmul(zmul(ld(S->alpha), rho1), zinv(rho0));
+        const dcx beta = zmul(a_rho, rho1);
         if (!zfinite(beta)) { fail(S, FA_ENONFINITE); return; }
         S->rho0 = pk(rho1);
-        d.rec_beta[S->m * d.L + j] = pk(beta);
+        d.rec_beta[m * d.L + j] = pk(beta);
     }
 }
 
 // alpha of BiCG sub-step j from partials of <rt, u_{j+1}> (seed part)
+template <bool DFP>
 __device__ __noinline__ void sc_alpha_seed(const SolverDev& d, int j, int nblk) {
     DevState* S = d.st;
-    if (S->done) return;
+    const int done = S->done, m = S->m;
+    const dcx rho0 = ld(S->rho0);
+    if (done) return;
     __shared__ dcx red[1];
-    reduce_slots<1>(d.part, nblk, 1, red);
+    reduce_slots<1, DFP>(d.part, nblk, 1, red);
     if (threadIdx.x == 0) {
         const dcx den = red[0];
         if (zabs2(den) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
-        const dcx alpha = zmul(ld(S->rho0), zinv(den));
+        const dcx alpha = zmul(rho0, zinv(den));
         if (!zfinite(alpha)) { fail(S, FA_ENONFINITE); return; }
-        d.rec_alpha[S->m * d.L + j] = pk(alpha);
+        d.rec_alpha[m * d.L + j] = pk(alpha);
         S->alpha = pk(alpha);
         S->alpha_prev = pk(alpha);
     }
@@ -461,65 +527,87 @@ __device__ __noinline__ void sc_alpha_shifts(const SolverDev& d, int j) {
 
 // MR coefficients gamma (seed part) from the Gram partials: diagonally scaled
 // normal equations, Gaussian elimination with partial pivoting.
-template <int L>
+template <int L, bool DFP>
 __device__ __noinline__ void sc_mr_seed(const SolverDev& d, int nblk) {
     DevState* S = d.st;
     if (S->done) return;
+    const int m = S->m;
     constexpr int NG = n_gram(L);
     __shared__ dcx G[NG];
-    reduce_slots<NG>(d.part, nblk, NG, G);
+    reduce_slots<NG, DFP>(d.part, nblk, NG, G);
     if (threadIdx.x != 0) return;
     int bad = 0;
     // slot of (i, k), i <= k, in the row-major upper triangle
     auto slot = [](int i, int k) { return i * (L + 1) - i * (i - 1) / 2 + (k - i); };
-    dcx Ab[L][L + 1];
-    double dsc[L];
+    dcx gam[L + 1];
+    gam[0] = mk(-1.0);
     for (int i = 1; i <= L; ++i) {
         const double gii = G[slot(i, i)].r;
         if (!(gii > 0.0) || !isfinite(gii)) bad = FA_EBREAKDOWN;
-        dsc[i - 1] = (gii > 0.0) ? 1.0 / sqrt(gii) : 1.0;
     }
-    for (int i = 1; i <= L; ++i) {
-        for (int k = 1; k <= L; ++k) {
-            const dcx gik = (i <= k) ? G[slot(i, k)] : conjd(G[slot(k, i)]);
-            Ab[i - 1][k - 1] = zscale(__dmul_rn(dsc[i - 1], dsc[k - 1]), gik);
+    if (L == 1 && !bad) {
+        // gamma_1 = <r_1, r_0> / <r_1, r_1>
+        gam[1] = zscale(1.0 / G[slot(1, 1)].r, conjd(G[slot(0, 1)]));
+    } else if (!bad) {
+        // Diagonal scaling by powers of two (exact; integer work only), so that
+        // the scaled diagonal lies in [1, 4).
+        double dsc[L];
+        for (int i = 1; i <= L; ++i) dsc[i - 1] = pow2_rsqrt(G[slot(i, i)].r);
+        dcx Ab[L][L + 1];
+        for (int i = 1; i <= L; ++i) {
+            for (int k = 1; k <= L; ++k) {
+                const dcx gik = (i <= k) ? G[slot(i, k)] : conjd(G[slot(k, i)]);
+                Ab[i - 1][k - 1] = zscale(__dmul_rn(dsc[i - 1], dsc[k - 1]), gik);
+            }
+            Ab[i - 1][L] = zscale(dsc[i - 1], conjd(G[slot(0, i)]));   // <r_i, r_0>
         }
-        Ab[i - 1][L] = zscale(dsc[i - 1], conjd(G[slot(0, i)]));   // <r_i, r_0>
-    }
-    // elimination with partial pivoting (the power basis r_1..r_l can make
-    // the normal equations numerically indefinite for large l; any solution
-    // is a valid MR polynomial); one inverse per pivot
-    dcx ipiv[L];
-    for (int k = 0; k < L && !bad; ++k) {
-        int pr = k;
-        double best = zabs2(Ab[k][k]);
-        for (int i = k + 1; i < L; ++i)
-            if (zabs2(Ab[i][k]) > best) { best = zabs2(Ab[i][k]); pr = i; }
-        if (!(best > 0.0)) { bad = FA_EBREAKDOWN; break; }
-        if (pr != k)
-            for (int q = k; q <= L; ++q) { dcx tq = Ab[k][q]; Ab[k][q] = Ab[pr][q]; Ab[pr][q] = tq; }
-        ipiv[k] = zinv(Ab[k][k]);
-        for (int i = k + 1; i < L; ++i) {
-            const dcx f = zmul(Ab[i][k], ipiv[k]);
-            for (int q = k + 1; q <= L; ++q) Ab[i][q] = zsub(Ab[i][q], zmul(f, Ab[k][q]));
-        }
-    }
-    dcx gam[L + 1];
-    if (!bad) {
         dcx z[L];
-        for (int i = L - 1; i >= 0; --i) {
-            dcx v = Ab[i][L];
-            for (int q = i + 1; q < L; ++q) v = zsub(v, zmul(Ab[i][q], z[q]));
-            z[i] = zmul(v, ipiv[i]);
+        if constexpr (L == 2) {
+            // Cramer's rule on the Hermitian 2 x 2 system
+            const double a11 = Ab[0][0].r, a22 = Ab[1][1].r;
+            const dcx a12 = Ab[0][1];
+            const double det = __fma_rn(a11, a22, -zabs2(a12));
+            if (!(det != 0.0) || !isfinite(det)) {
+                bad = FA_EBREAKDOWN;
+            } else {
+                const double idet = 1.0 / det;
+                z[0] = zscale(idet, zsub(zscale(a22, Ab[0][L]), zmul(a12, Ab[1][L])));
+                z[1] = zscale(idet, zsub(zscale(a11, Ab[1][L]), zmul(conjd(a12), Ab[0][L])));
+            }
+        } else {
+            // elimination with partial pivoting (the power basis r_1..r_l can
+            // make the normal equations numerically indefinite for large l; any
+            // solution is a valid MR polynomial); one inverse per pivot
+            dcx ipiv[L];
+            for (int k = 0; k < L && !bad; ++k) {
+                int pr = k;
+                double best = zabs2(Ab[k][k]);
+                for (int i = k + 1; i < L; ++i)
+                    if (zabs2(Ab[i][k]) > best) { best = zabs2(Ab[i][k]); pr = i; }
+                if (!(best > 0.0)) { bad = FA_EBREAKDOWN; break; }
+                if (pr != k)
+                    for (int q = k; q <= L; ++q) { dcx tq = Ab[k][q]; Ab[k][q] = Ab[pr][q]; Ab[pr][q] = tq; }
+                ipiv[k] = zinv(Ab[k][k]);
+                for (int i = k + 1; i < L; ++i) {
+                    const dcx f = zmul(Ab[i][k], ipiv[k]);
+                    for (int q = k + 1; q <= L; ++q) Ab[i][q] = zsub(Ab[i][q], zmul(f, Ab[k][q]));
+                }
+            }
+            if (!bad) {
+                for (int i = L - 1; i >= 0; --i) {
+                    dcx v = Ab[i][L];
+                    for (int q = i + 1; q < L; ++q) v = zsub(v, zmul(Ab[i][q], z[q]));
+                    z[i] = zmul(v, ipiv[i]);
+                }
+            }
         }
-        gam[0] = mk(-1.0);
-        for (int j = 1; j <= L; ++j) {
-            gam[j] = zscale(dsc[j - 1], z[j - 1]);
-            if (!zfinite(gam[j])) bad = FA_ENONFINITE;
-        }
+        if (!bad)
+            for (int j = 1; j <= L; ++j) gam[j] = zscale(dsc[j - 1], z[j - 1]);
     }
+    if (!bad)
+        for (int j = 1; j <= L; ++j)
+            if (!zfinite(gam[j])) bad = FA_ENONFINITE;
     if (bad) { fail(S, bad); return; }
-    const int m = S->m;
     for (int j = 0; j <= L; ++j) d.rec_gamma[m * (L + 1) + j] = pk(gam[j]);
     S->omega = pk(gam[L]);
 }
@@ -568,21 +656,32 @@ __device__ __noinline__ void sc_mr_shifts(const SolverDev& d) {
 }
 
 // end of an outer iteration: convergence and freezing of shifts, next beta
+template <bool DFP>
 __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     DevState* S = d.st;
-    if (S->done) return;
+    // every load the step needs is issued before the reduction, and the next
+    // beta's denominator is inverted while the partials arrive
+    const int done = S->done, m = S->m;
+    const double tol2b = S->tol2b, theta2b = S->theta2b;
+    const dcx omega = ld(S->omega), rho_old = ld(S->rho0), alpha = ld(S->alpha);
+    const int sh = threadIdx.x;
+    const bool mine = sh < d.ns && d.active[sh];
+    const double z2 = mine ? zabs2(ld(d.zeta[sh])) : 0.0;
+    if (done) return;
+    dcx rho0 = mk(0.0), a_rho = mk(0.0);
+    if (threadIdx.x == 0) {
+        rho0 = zscale(-1.0, zmul(omega, rho_old));
+        if (zabs2(rho0) != 0.0) a_rho = zmul(alpha, zinv(rho0));
+    }
     __shared__ dcx red[2];
-    reduce_slots<2>(d.part, nblk, 2, red);
+    reduce_slots<2, DFP>(d.part, nblk, 2, red);
     const dcx rtr = red[0];
     const double rn2 = red[1].r;
-    const int m = S->m;
     __shared__ int n_act, all_small;
     if (threadIdx.x == 0) { n_act = 0; all_small = 1; }
     __syncthreads();
-    const double tol2b = S->tol2b, theta2b = S->theta2b;
-    for (int sh = threadIdx.x; sh < d.ns; sh += blockDim.x) {
-        if (!d.active[sh]) continue;
-        const double z2 = zabs2(ld(d.zeta[sh]));
+    // one thread per shift (kMaxShifts <= blockDim.x)
+    if (mine) {
         if (rn2 <= tol2b * z2) {
             d.active[sh] = 0;
             d.iters[sh] = m + 1;
@@ -600,9 +699,8 @@ __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     if (head && all_small) S->switch_req = 1;
     if (n_act == 0) { S->done = 1; S->n_outer = m + 1; return; }
     if (m + 1 >= d.max_outer) { fail(S, FA_ENOCONV); S->n_outer = m + 1; return; }
-    const dcx rho0 = zscale(-1.0, zmul(ld(S->omega), ld(S->rho0)));
     if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); S->n_outer = m + 1; return; }
-    const dcx beta = zmul(zmul(ld(S->alpha), rtr), zinv(rho0));
+    const dcx beta = zmul(a_rho, rtr);
     S->rho0 = pk(rtr);
     d.rec_beta[(m + 1) * d.L] = pk(beta);
 }
@@ -620,35 +718,48 @@ struct ScalarStep {
     int arg;
 };
 
+template <bool DFP>
 __device__ __forceinline__ void run_step(const SolverDev& d, ScalarStep e, int nblk) {
     if (e.kind == STEP_NONE || !last_block(d.st)) return;
     if (e.kind == STEP_BETA) {
-        sc_beta(d, e.arg, nblk);
+        sc_beta<DFP>(d, e.arg, nblk);
     } else if (e.kind == STEP_ALPHA || e.kind == STEP_ALPHA_ALL) {
-        sc_alpha_seed(d, e.arg, nblk);
+        sc_alpha_seed<DFP>(d, e.arg, nblk);
         if (e.kind == STEP_ALPHA_ALL) {
             __syncthreads();
             sc_alpha_shifts(d, e.arg);
         }
     } else {
-        sc_conv(d, nblk, e.arg);
+        sc_conv<DFP>(d, nblk, e.arg);
     }
+}
+
+// Resident blocks per SM of the balanced vector kernels (register budget <= 64).
+constexpr int kVecBlocks = 4;
+
+// Contiguous site range [s0, s1) of block bx of nbx (V/nbx sites, +-1).  The
+// vector kernels run at most one wave (kVecBlocks per SM, which their register
+// budget guarantees); larger lattices loop over their range.
+__device__ __forceinline__ void site_range(int V, unsigned bx, unsigned nbx, int& s0, int& s1) {
+    s0 = (int)(((long long)V * bx) / nbx);
+    s1 = (int)(((long long)V * (bx + 1)) / nbx);
 }
 
 // ------------------------------------------------------------------ BiCG sub-step kernels
 // u_i <- r_i - beta u_i, i = 0..j (r, u: l+1 spinors each, contiguous, stride vs)
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
-    const int s = blockIdx.x * kThreads + threadIdx.x;
-    if (s >= d.V) return;
+    int s0, s1;
+    site_range(d.V, blockIdx.x, gridDim.x, s0, s1);
     const typename Ch<R>::T* r = Vec<R>::r(d);
     typename Ch<R>::T* u = Vec<R>::u(d);
     const size_t vs = vstride<R>(d);
     const int m = d.st->m;
     const cx<R> nb = negcx<R>(d.rec_beta[m * d.L + j]);
+    for (int s = s0 + threadIdx.x; s < s1; s += kThreads) {
     for (int i = 0; i <= j; ++i) {
         const typename Ch<R>::T* ri = r + i * vs;
         typename Ch<R>::T* ui = u + i * vs;
@@ -660,6 +771,7 @@ k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
             b.stv(ui, q, d.V, s);
         }
     }
+    }
 }
 
 // r_i <- r_i - alpha u_{i+1}, i = 0..j.
@@ -669,7 +781,7 @@ k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
 // XS (pass 1 of the double-pass forms): block 0 runs the shift part of sub-step
 // j (sc_alpha_shifts) beside the vector blocks 1..nblk.
 template <typename R, bool ACC, bool SHIFTS, bool XS = false>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
@@ -677,8 +789,8 @@ k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
         sc_alpha_shifts(d, j);
         return;
     }
-    const int s = (blockIdx.x - (XS ? 1 : 0)) * kThreads + threadIdx.x;
-    if (s >= d.V) return;
+    int s0, s1;
+    site_range(d.V, blockIdx.x - (XS ? 1u : 0u), gridDim.x - (XS ? 1u : 0u), s0, s1);
     const int m = d.st->m;
     typename Ch<R>::T* r = Vec<R>::r(d);
     const typename Ch<R>::T* u = Vec<R>::u(d);
@@ -691,6 +803,7 @@ k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
     const int L = d.L;
     const cx<R> na = negcx<R>(d.rec_alpha[m * L + j]);
     const size_t cf0 = (size_t)m * nc_slots(L);
+    for (int s = s0 + threadIdx.x; s < s1; s += kThreads) {
 #pragma unroll
     for (int q = 0; q < Ch<R>::N; ++q) {
         cx<R> t[Ch<R>::W];
@@ -753,14 +866,17 @@ k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
         if (ACC) acc_y<R>(y, q, d.V, s, t);
         if (d.x64 != nullptr) acc_x<R>(d.x64, q, d.V, s, d.rec_alpha[m * L + j], Ch<R>::ld(u, q, d.V, s));
     }
+    }
 }
 
 // ------------------------------------------------------------------ MR part
 // Gram matrix <r_i, r_k>, 0 <= i <= k <= L, grid-stride, per-block partials.
 // Last block: the MR coefficients (sc_mr_seed) and, for single-pass solves
 // (shifts != 0), their shift part.
+// l <= 2: registers capped for 4 blocks/SM (one wave of 512 blocks)
+template <typename R, int L> constexpr int gram_min_blocks() { return L <= 2 ? 4 : 1; }
 template <typename R, int L>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, gram_min_blocks<R, L>())
 k_gram(const SolverDev* __restrict__ ds, int shifts) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, 0)) return;
@@ -771,7 +887,9 @@ k_gram(const SolverDev* __restrict__ ds, int shifts) {
     cx<R> acc[NG];
 #pragma unroll
     for (int k = 0; k < NG; ++k) acc[k] = czero<R>();
-    for (int s = blockIdx.x * kThreads + threadIdx.x; s < d.V; s += gridDim.x * kThreads) {
+    int s0, s1;
+    site_range(d.V, blockIdx.x, gridDim.x, s0, s1);
+    for (int s = s0 + threadIdx.x; s < s1; s += kThreads) {
 #pragma unroll
         for (int q = 0; q < Ch<R>::N; ++q) {
             Ch<R> v[L + 1];
@@ -790,7 +908,7 @@ k_gram(const SolverDev* __restrict__ ds, int shifts) {
     }
     block_reduce_store<NG, R>(acc, partials, gridDim.x);
     if (last_block(d.st)) {
-        sc_mr_seed<L>(d, gridDim.x);
+        sc_mr_seed<L, dfp_of<R>()>(d, gridDim.x);
         if (shifts) {
             __syncthreads();
             sc_mr_shifts<L>(d);
@@ -806,8 +924,14 @@ k_gram(const SolverDev* __restrict__ ds, int shifts) {
 // XS (pass 1 of the double-pass forms): block 0 runs the shift part of the MR
 // step (sc_mr_shifts) and takes a ticket too, so that the convergence step sees
 // the new zeta; blocks 1.. are the vector blocks.
+// FP32 and double-float, l <= 3: registers capped for 4 blocks/SM (64; some
+// bytes spilled), so that a 16^3 x 32 lattice (512 blocks) runs in one wave
+// instead of 1.12 (left alone, the compiler takes up to 167 registers here)
+template <typename R, int L> constexpr int mr_min_blocks() {
+    return (!std::is_same<R, double>::value && L <= 3) ? 4 : 1;
+}
 template <typename R, int L, bool ACC, bool SHIFTS, bool DOT, bool XS = false>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, mr_min_blocks<R, L>())
 k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
@@ -815,7 +939,7 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
     if (XS && blockIdx.x == 0) {
         sc_mr_shifts<L>(d);
         __threadfence();   // the new zeta of every thread before the ticket
-        run_step(d, step, nbx);
+        run_step<dfp_of<R>()>(d, step, nbx);
         return;
     }
     const int m = d.st->m;
@@ -835,7 +959,9 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
     for (int j = 1; j <= L; ++j) ng[j] = negcx<R>(d.rec_gamma[m * (L + 1) + j]);
     const size_t cf0 = (size_t)m * nc_slots(L);
     cx<R> dots[2] = {czero<R>(), czero<R>()};
-    for (int s = bx * kThreads + threadIdx.x; s < d.V; s += nbx * kThreads) {
+    int s0, s1;
+    site_range(d.V, bx, nbx, s0, s1);
+    for (int s = s0 + threadIdx.x; s < s1; s += kThreads) {
 #pragma unroll
         for (int q = 0; q < Ch<R>::N; ++q) {
             Ch<R> rv[L + 1];
@@ -914,7 +1040,7 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
     }
     if (DOT) {
         block_reduce_store<2, R>(dots, partials, nbx, bx);
-        run_step(d, step, nbx);
+        run_step<dfp_of<R>()>(d, step, nbx);
     }
 }
 
@@ -923,7 +1049,9 @@ template <typename R>
 __device__ __forceinline__ void k_dot2_body(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0,
                                             double2* partials) {
     cx<R> dots[2] = {czero<R>(), czero<R>()};
-    for (int s = blockIdx.x * kThreads + threadIdx.x; s < V; s += gridDim.x * kThreads) {
+    int s0, s1;
+    site_range(V, blockIdx.x, gridDim.x, s0, s1);
+    for (int s = s0 + threadIdx.x; s < s1; s += kThreads) {
 #pragma unroll
         for (int q = 0; q < Ch<R>::N; ++q) {
             Ch<R> a = Ch<R>::ld(rt, q, V, s), b = Ch<R>::ld(r0, q, V, s);
@@ -946,10 +1074,10 @@ k_dot2(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0, double2*
 
 // start of pass 1: <rt, r0>, |r0|^2 and, in the last block, the initial state
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_dot2_sys(const SolverDev* __restrict__ ds, double tol, double theta) {
+__global__ void __launch_bounds__(kThreads, kVecBlocks) k_dot2_sys(const SolverDev* __restrict__ ds, double tol, double theta) {
     const SolverDev& d = ds[blockIdx.y];
     k_dot2_body<R>(d.V, Vec<R>::rt(d), Vec<R>::r(d), d.part);
-    if (last_block(d.st)) sc_init(d, gridDim.x, tol, theta);
+    if (last_block(d.st)) sc_init<dfp_of<R>()>(d, gridDim.x, tol, theta);
 }
 
 // A application inside the solver: out = scale * g5 D in on the system's own
@@ -990,7 +1118,7 @@ k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, i
     }
     if (DOT) {
         block_reduce_store<1, R>(dres, d.part, 0);
-        run_step(d, step, gridDim.x);
+        run_step<dfp_of<R>()>(d, step, gridDim.x);
     }
 }
 
@@ -1010,7 +1138,7 @@ k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_s
                                                         fromdbl<R>(d.ef), fromdbl<R>(d.eb), fromdbl<R>(d.bc), rt)};
     if (DOT) {
         block_reduce_store<1, R, kRowThreads>(dres, d.part, 0, blockIdx.x);
-        run_step(d, step, gridDim.x);
+        run_step<dfp_of<R>()>(d, step, gridDim.x);
     }
 }
 
@@ -1027,7 +1155,7 @@ k_hop1_rows(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag,
     cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv)};
     if (DOT) {
         block_reduce_store<1, R, kRowThreads>(dres, partials, 0, blockIdx.x);
-        run_step(ds[0], step, gridDim.x);
+        run_step<dfp_of<R>()>(ds[0], step, gridDim.x);
     }
 }
 
@@ -1053,7 +1181,7 @@ k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R ch
     }
     if (DOT) {
         block_reduce_store<1, R, NT>(dres, partials, 0, blockIdx.x);
-        run_step(ds[0], step, gridDim.x);
+        run_step<dfp_of<R>()>(ds[0], step, gridDim.x);
     }
 }
 
@@ -1062,14 +1190,16 @@ k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R ch
 // Rewrites the partials of <rt, r_0> (slot 0) and |r_0|^2 (slot 1) that the
 // convergence step reads, grid-stride like k_mr.
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_reliable(const SolverDev* __restrict__ ds, const double2* ax, int pass2, ScalarStep step) {
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
     typename Ch<R>::T* r0 = Vec<R>::r(d);
     const typename Ch<R>::T* rt = Vec<R>::rt(d);
     cx<R> dots[2] = {czero<R>(), czero<R>()};
-    for (int s = blockIdx.x * kThreads + threadIdx.x; s < d.V; s += gridDim.x * kThreads) {
+    int s0, s1;
+    site_range(d.V, blockIdx.x, gridDim.x, s0, s1);
+    for (int s = s0 + threadIdx.x; s < s1; s += kThreads) {
 #pragma unroll
         for (int q = 0; q < Ch<R>::N; ++q) {
             Ch<R> v;
@@ -1090,7 +1220,7 @@ k_reliable(const SolverDev* __restrict__ ds, const double2* ax, int pass2, Scala
         }
     }
     block_reduce_store<2, R>(dots, d.part, gridDim.x);
-    run_step(d, step, gridDim.x);
+    run_step<dfp_of<R>()>(d, step, gridDim.x);
 }
 
 // ------------------------------------------------------------------ pseudo-double-pass gather
