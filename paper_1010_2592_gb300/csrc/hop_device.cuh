@@ -156,10 +156,11 @@ __device__ __forceinline__ void hop_site(const Geom& g, const LinkView<R>& U, co
 }
 
 // ------------------------------------------------------------------ colour-row split (double-float)
-// The double-float sweep with one thread per site and output colour row a: a
-// thread projects the neighbour colour by colour and multiplies by row a of U
-// (column a of U^H) as it goes, so it holds two partial products and four
-// accumulators instead of whole spinors.
+// The double-float sweep with one thread per site and output colour row a: for
+// each hop the thread of row a projects colour a of the neighbour spinor and
+// shares the two spin rows through shared memory, then multiplies the three
+// colours by row a of U (column a of U^H), so it holds two partial products and
+// four accumulators instead of whole spinors.
 //
 // Its arithmetic is compensated rather than renormalised after every
 // operation: each row of U h is one compensated dot product (the Dot2 scheme of
@@ -250,24 +251,51 @@ __device__ __forceinline__ void recon1_c(dcs acc[4], dcs h0, dcs h1) {
     }
 }
 
-// one hop of row a: acc += w P (U or U^H) psi(nb), link at site ls
-template <int MU, int S, bool WEIGHT, bool G5IN>
-__device__ __forceinline__ void hop_row(dcs acc[4], const SpinorView<df>& in, const LinkView<df>& U, int ls, int nb,
-                                        int a, df w) {
-    dcs t0, t1;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        dcs p0 = dcs_of(in.ld1(nb, c)), p1 = dcs_of(in.ld1(nb, 3 + c));
-        dcs p2 = dcs_of(in.ld1(nb, 6 + c)), p3 = dcs_of(in.ld1(nb, 9 + c));
+// Thread layout of the row-split sweep: blocks of kRowThreads = 3 colour rows x
+// 64 sites; warps 2a and 2a+1 take row a of 32 consecutive sites each, so the
+// three rows of a site run on one SM and share its neighbour loads in L1.
+constexpr int kRowSites = 64;
+constexpr int kRowThreads = 3 * kRowSites;
+__device__ __forceinline__ int row_of_thread() { return (int)(threadIdx.x >> 6); }
+__device__ __forceinline__ int site_of_thread() {
+    return (int)blockIdx.x * kRowSites + (int)(threadIdx.x & (kRowSites - 1));
+}
+inline int row_blocks(int V) { return (V + kRowSites - 1) / kRowSites; }
+
+// The projection is shared through shared memory: for each hop the thread of
+// row a projects colour a of the neighbour spinor (four loads instead of
+// twelve) and stores the two spin rows; after a barrier every row reads the
+// three colours.  Double-buffered, one barrier per hop.
+__device__ __forceinline__ float4 dcs_pack(dcs v) { return make_float4(v.r.s, v.r.e, v.i.s, v.i.e); }
+__device__ __forceinline__ dcs dcs_unpack(float4 t) { return {{t.x, t.y}, {t.z, t.w}}; }
+
+// project colour a of psi(nb) and store the spin rows: buf[(2a + r) * kRowSites + i]
+template <int MU, int S, bool G5IN>
+__device__ __forceinline__ void proj_store(const SpinorView<df>& in, int nb, int a, float4* buf, int i, bool valid) {
+    dcs h0{{0.0f, 0.0f}, {0.0f, 0.0f}}, h1 = h0;
+    if (valid) {
+        dcs p0 = dcs_of(in.ld1(nb, a)), p1 = dcs_of(in.ld1(nb, 3 + a));
+        dcs p2 = dcs_of(in.ld1(nb, 6 + a)), p3 = dcs_of(in.ld1(nb, 9 + a));
         if (G5IN) {
             p2 = {dneg(p2.r), dneg(p2.i)};
             p3 = {dneg(p3.r), dneg(p3.i)};
         }
-        dcs h0, h1;
         project1_c<MU, S>(p0, p1, p2, p3, h0, h1);
-        // forward: row a of U_MU(s), L h; backward: column a of U_MU(nb)^H, conj(L) h
+    }
+    buf[(2 * a) * kRowSites + i] = dcs_pack(h0);
+    buf[(2 * a + 1) * kRowSites + i] = dcs_pack(h1);
+}
+
+// acc += w P (U or U^H) psi(nb) for row a, from the stored spin rows of all colours
+template <int MU, int S, bool WEIGHT>
+__device__ __forceinline__ void mul_recon(dcs acc[4], const LinkView<df>& U, int ls, int a, df w, const float4* buf,
+                                          int i) {
+    dcs t0, t1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const dcs h0 = dcs_unpack(buf[(2 * c) * kRowSites + i]), h1 = dcs_unpack(buf[(2 * c + 1) * kRowSites + i]);
         const dcs L = dcs_of(U.ld1(MU, ls, S > 0 ? a * 3 + c : c * 3 + a));
-        const dsum li = S > 0 ? L.i : dneg(L.i);     // imaginary part of L or conj(L)
+        const dsum li = S > 0 ? L.i : dneg(L.i);
         if (c == 0) {
             t0 = {dfma(dneg(li), h0.i, dmul(L.r, h0.r)), dfma(li, h0.r, dmul(L.r, h0.i))};
             t1 = {dfma(dneg(li), h1.i, dmul(L.r, h1.r)), dfma(li, h1.r, dmul(L.r, h1.i))};
@@ -284,13 +312,15 @@ __device__ __forceinline__ void hop_row(dcs acc[4], const SpinorView<df>& in, co
     recon1_c<MU, S>(acc, t0, t1);
 }
 
-// o[sp] = output component (spin sp, colour a) of the sweep
 template <bool G5IN, bool G5OUT>
-__device__ __forceinline__ void hop_site_row(const Geom& g, const LinkView<df>& U, const SpinorView<df>& in, int s,
-                                             int a, df cdiag, df chop, df ef, df eb, df bc, cx<df> o[4]) {
+__device__ __forceinline__ void hop_site_row_sh(const Geom& g, const LinkView<df>& U, const SpinorView<df>& in, int s,
+                                                int a, bool valid, df cdiag, df chop, df ef, df eb, df bc, cx<df> o[4]) {
+    __shared__ float4 hs[2][6 * kRowSites];
+    const int i = (int)(threadIdx.x & (kRowSites - 1));
     const int X = g.X, Y = g.Y, Z = g.Z, T = g.T;
-    const int x = s % X;
-    const int r1 = s / X;
+    const int sv = valid ? s : 0;
+    const int x = sv % X;
+    const int r1 = sv / X;
     const int y = r1 % Y;
     const int r2 = r1 / Y;
     const int z = r2 % Z;
@@ -300,24 +330,41 @@ __device__ __forceinline__ void hop_site_row(const Geom& g, const LinkView<df>& 
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[k] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     const df one(1.0f);
-    int nb = (x == X - 1) ? s - (X - 1) : s + 1;
-    hop_row<0, +1, false, G5IN>(acc, in, U, s, nb, a, one);
-    nb = (x == 0) ? s + (X - 1) : s - 1;
-    hop_row<0, -1, false, G5IN>(acc, in, U, nb, nb, a, one);
-    nb = (y == Y - 1) ? s - (Y - 1) * sY : s + sY;
-    hop_row<1, +1, false, G5IN>(acc, in, U, s, nb, a, one);
-    nb = (y == 0) ? s + (Y - 1) * sY : s - sY;
-    hop_row<1, -1, false, G5IN>(acc, in, U, nb, nb, a, one);
-    nb = (z == Z - 1) ? s - (Z - 1) * sZ : s + sZ;
-    hop_row<2, +1, false, G5IN>(acc, in, U, s, nb, a, one);
-    nb = (z == 0) ? s + (Z - 1) * sZ : s - sZ;
-    hop_row<2, -1, false, G5IN>(acc, in, U, nb, nb, a, one);
+    int nb = (x == X - 1) ? sv - (X - 1) : sv + 1;
+    proj_store<0, +1, G5IN>(in, nb, a, hs[0], i, valid);
+    __syncthreads();
+    mul_recon<0, +1, false>(acc, U, sv, a, one, hs[0], i);
+    nb = (x == 0) ? sv + (X - 1) : sv - 1;
+    proj_store<0, -1, G5IN>(in, nb, a, hs[1], i, valid);
+    __syncthreads();
+    mul_recon<0, -1, false>(acc, U, nb, a, one, hs[1], i);
+    nb = (y == Y - 1) ? sv - (Y - 1) * sY : sv + sY;
+    proj_store<1, +1, G5IN>(in, nb, a, hs[0], i, valid);
+    __syncthreads();
+    mul_recon<1, +1, false>(acc, U, sv, a, one, hs[0], i);
+    nb = (y == 0) ? sv + (Y - 1) * sY : sv - sY;
+    proj_store<1, -1, G5IN>(in, nb, a, hs[1], i, valid);
+    __syncthreads();
+    mul_recon<1, -1, false>(acc, U, nb, a, one, hs[1], i);
+    nb = (z == Z - 1) ? sv - (Z - 1) * sZ : sv + sZ;
+    proj_store<2, +1, G5IN>(in, nb, a, hs[0], i, valid);
+    __syncthreads();
+    mul_recon<2, +1, false>(acc, U, sv, a, one, hs[0], i);
+    nb = (z == 0) ? sv + (Z - 1) * sZ : sv - sZ;
+    proj_store<2, -1, G5IN>(in, nb, a, hs[1], i, valid);
+    __syncthreads();
+    mul_recon<2, -1, false>(acc, U, nb, a, one, hs[1], i);
     const df wf = (t == T - 1) ? mulR(ef, bc) : ef;
     const df wb = (t == 0) ? mulR(eb, bc) : eb;
-    nb = (t == T - 1) ? s - (T - 1) * sT : s + sT;
-    hop_row<3, +1, true, G5IN>(acc, in, U, s, nb, a, wf);
-    nb = (t == 0) ? s + (T - 1) * sT : s - sT;
-    hop_row<3, -1, true, G5IN>(acc, in, U, nb, nb, a, wb);
+    nb = (t == T - 1) ? sv - (T - 1) * sT : sv + sT;
+    proj_store<3, +1, G5IN>(in, nb, a, hs[0], i, valid);
+    __syncthreads();
+    mul_recon<3, +1, true>(acc, U, sv, a, wf, hs[0], i);
+    nb = (t == 0) ? sv + (T - 1) * sT : sv - sT;
+    proj_store<3, -1, G5IN>(in, nb, a, hs[1], i, valid);
+    __syncthreads();
+    mul_recon<3, -1, true>(acc, U, nb, a, wb, hs[1], i);
+    if (!valid) return;
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp) {
         cx<df> p = in.ld1(s, sp * 3 + a);
@@ -332,27 +379,17 @@ __device__ __forceinline__ void hop_site_row(const Geom& g, const LinkView<df>& 
     }
 }
 
-// Thread layout of the row-split sweep: blocks of kRowThreads = 3 colour rows x
-// 64 sites; warps 2a and 2a+1 take row a of 32 consecutive sites each, so the
-// three rows of a site run on one SM and share its neighbour loads in L1.
-constexpr int kRowSites = 64;
-constexpr int kRowThreads = 3 * kRowSites;
-__device__ __forceinline__ int row_of_thread() { return (int)(threadIdx.x >> 6); }
-__device__ __forceinline__ int site_of_thread() {
-    return (int)blockIdx.x * kRowSites + (int)(threadIdx.x & (kRowSites - 1));
-}
-inline int row_blocks(int V) { return (V + kRowSites - 1) / kRowSites; }
-
 // out(s, row) = hop_site(s) row; DOT: returns <dotv, out> over the thread's 4 components
+// (every thread of the block takes part: the sweep has block barriers)
 template <typename R, bool G5IN, bool G5OUT, bool DOT>
 __device__ __forceinline__ cx<R> hop_rows_body(const Geom& g, const LinkView<R>& U, const SpinorView<R>& in,
                                                const SpinorView<R>& out, R cdiag, R chop, R ef, R eb, R bc,
                                                const SpinorView<R>& dotv) {
     const int a = row_of_thread(), s = site_of_thread();
     cx<R> dres = czero<R>();
+    cx<R> o[4];
+    hop_site_row_sh<G5IN, G5OUT>(g, U, in, s, a, s < g.V, cdiag, chop, ef, eb, bc, o);
     if (s < g.V) {
-        cx<R> o[4];
-        hop_site_row<G5IN, G5OUT>(g, U, in, s, a, cdiag, chop, ef, eb, bc, o);
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp) out.st1(s, sp * 3 + a, o[sp]);
         if (DOT) {
@@ -378,9 +415,11 @@ __device__ __forceinline__ cx<R> hop_rows_body(const Geom& g, const LinkView<R>&
 #define FA_HOP_MINB_DF 2
 #endif
 // row-split double-float sweep: resident blocks of kRowThreads per SM.  Measured
-// per sweep (16^3 x 32 / 32^3 x 64): 3 blocks/SM 0.099 / 1.416 ms, 4 (80
-// registers) 0.099 / 1.409 ms, 5 (64 registers, 16 B spilled) 0.098 / 1.377 ms;
-// the whole-site double-float sweep took 0.169 / 2.65 ms.
+// per sweep (16^3 x 32 / 32^3 x 64) with the first, renormalised row split:
+// 3 blocks/SM 0.099 / 1.416 ms, 4 (80 registers) 0.099 / 1.409 ms, 5 (64
+// registers) 0.098 / 1.377 ms; the whole-site double-float sweep took 0.169 /
+// 2.65 ms.  The compensated sweep with the shared projection (64 registers, no
+// spill) takes 0.068 / 0.934 ms.
 // The variants that also form <dotv, out> and run a scalar step keep one block
 // less (80 registers, no spill).
 #ifndef FA_HOP_ROWS_MINB

@@ -263,17 +263,16 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     fa_ctx* c = B.c0;
     const int n = B.n, nb = B.Lo.nblk, rg = B.Lo.red_grid, vg = B.Lo.vgrid;
     const int p2 = pass2 ? 1 : 0;
-    // Balanced kernels run exactly one wave of vg blocks; their XS variants keep
-    // that total (vg - 1 vector blocks and the shift block), so that no block
-    // waits for a second wave.  k_gram / k_mr use the balanced grid where their
-    // register budget gives kVecBlocks resident blocks per SM, else the
-    // reduction grid.
-    const bool bal = vg >= 2 * kVecBlocks;
-    const dim3 gs(nb, n), gv(vg, n), gvx(bal ? vg : vg + 1, n);
+    // The vector kernels run vg blocks (one site per thread while the lattice
+    // fits one wave); their XS variants add the shift block, which finishes
+    // early (taking one of the vector blocks for it would give the others 257
+    // sites for 256 threads, a second pass for one thread of every block).
+    // k_gram / k_mr use vg where their register budget gives kVecBlocks
+    // resident blocks per SM, else the reduction grid.
+    const dim3 gs(nb, n), gv(vg, n), gvx(vg + 1, n);
     const dim3 gg(gram_min_blocks<R, L>() >= kVecBlocks ? vg : rg, n);
-    const bool mbal = mr_min_blocks<R, L>() >= kVecBlocks;
-    const int mg = mbal ? vg : rg;
-    const dim3 gm(mg, n), gmx(mbal && bal ? mg : mg + 1, n);
+    const int mg = mr_min_blocks<R, L>() >= kVecBlocks ? vg : rg;
+    const dim3 gm(mg, n), gmx(mg + 1, n);
     const SolverDev* ds = B.dev;
     cudaStream_t st = c->stream;
     constexpr int kind = rp_of<R>() == RP64 ? 0 : (rp_of<R>() == RP32 ? 1 : 2);

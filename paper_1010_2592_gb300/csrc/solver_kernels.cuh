@@ -439,18 +439,17 @@ __device__ __noinline__ void sc_init(const SolverDev& d, int nblk, double tol, d
 template <bool DFP>
 __device__ __noinline__ void sc_beta(const SolverDev& d, int j, int nblk) {
     DevState* S = d.st;
-    // state loads and the inverse of rho0 before the reduction
+    // the state loads are issued with the partial loads and consumed after the
+    // reduction (one memory round trip; the done flag only matters then)
     const int done = S->done, m = S->m;
     const dcx rho0 = ld(S->rho0), alpha = ld(S->alpha);
-    if (done) return;
-    dcx a_rho = mk(0.0);
-    if (threadIdx.x == 0 && zabs2(rho0) != 0.0) a_rho = zmul(alpha, zinv(rho0));
     __shared__ dcx red[1];
     reduce_slots<1, DFP>(d.part, nblk, 1, red);
+    if (done) return;
     if (threadIdx.x == 0) {
         const dcx rho1 = red[0];
         if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
-        const dcx beta = zmul(a_rho, rho1);
+        const dcx beta = zmul(zmul(alpha, rho1), zinv(rho0));
         if (!zfinite(beta)) { fail(S, FA_ENONFINITE); return; }
         S->rho0 = pk(rho1);
         d.rec_beta[m * d.L + j] = pk(beta);
@@ -463,9 +462,9 @@ __device__ __noinline__ void sc_alpha_seed(const SolverDev& d, int j, int nblk) 
     DevState* S = d.st;
     const int done = S->done, m = S->m;
     const dcx rho0 = ld(S->rho0);
-    if (done) return;
     __shared__ dcx red[1];
     reduce_slots<1, DFP>(d.part, nblk, 1, red);
+    if (done) return;
     if (threadIdx.x == 0) {
         const dcx den = red[0];
         if (zabs2(den) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
@@ -530,12 +529,11 @@ __device__ __noinline__ void sc_alpha_shifts(const SolverDev& d, int j) {
 template <int L, bool DFP>
 __device__ __noinline__ void sc_mr_seed(const SolverDev& d, int nblk) {
     DevState* S = d.st;
-    if (S->done) return;
-    const int m = S->m;
+    const int done = S->done, m = S->m;
     constexpr int NG = n_gram(L);
     __shared__ dcx G[NG];
     reduce_slots<NG, DFP>(d.part, nblk, NG, G);
-    if (threadIdx.x != 0) return;
+    if (done || threadIdx.x != 0) return;
     int bad = 0;
     // slot of (i, k), i <= k, in the row-major upper triangle
     auto slot = [](int i, int k) { return i * (L + 1) - i * (i - 1) / 2 + (k - i); };
@@ -659,29 +657,24 @@ __device__ __noinline__ void sc_mr_shifts(const SolverDev& d) {
 template <bool DFP>
 __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     DevState* S = d.st;
-    // every load the step needs is issued before the reduction, and the next
-    // beta's denominator is inverted while the partials arrive
+    // every load the step needs is issued with the partial loads and consumed
+    // after the reduction (one memory round trip)
     const int done = S->done, m = S->m;
     const double tol2b = S->tol2b, theta2b = S->theta2b;
     const dcx omega = ld(S->omega), rho_old = ld(S->rho0), alpha = ld(S->alpha);
-    const int sh = threadIdx.x;
-    const bool mine = sh < d.ns && d.active[sh];
-    const double z2 = mine ? zabs2(ld(d.zeta[sh])) : 0.0;
-    if (done) return;
-    dcx rho0 = mk(0.0), a_rho = mk(0.0);
-    if (threadIdx.x == 0) {
-        rho0 = zscale(-1.0, zmul(omega, rho_old));
-        if (zabs2(rho0) != 0.0) a_rho = zmul(alpha, zinv(rho0));
-    }
+    const int sh = threadIdx.x;     // one thread per shift (kMaxShifts <= blockDim.x)
+    const int act = sh < d.ns ? d.active[sh] : 0;
+    const double2 zv = sh < d.ns ? d.zeta[sh] : make_double2(0.0, 0.0);
     __shared__ dcx red[2];
     reduce_slots<2, DFP>(d.part, nblk, 2, red);
+    if (done) return;
     const dcx rtr = red[0];
     const double rn2 = red[1].r;
     __shared__ int n_act, all_small;
     if (threadIdx.x == 0) { n_act = 0; all_small = 1; }
     __syncthreads();
-    // one thread per shift (kMaxShifts <= blockDim.x)
-    if (mine) {
+    if (act) {
+        const double z2 = zabs2(ld(zv));
         if (rn2 <= tol2b * z2) {
             d.active[sh] = 0;
             d.iters[sh] = m + 1;
@@ -699,8 +692,9 @@ __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     if (head && all_small) S->switch_req = 1;
     if (n_act == 0) { S->done = 1; S->n_outer = m + 1; return; }
     if (m + 1 >= d.max_outer) { fail(S, FA_ENOCONV); S->n_outer = m + 1; return; }
+    const dcx rho0 = zscale(-1.0, zmul(omega, rho_old));
     if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); S->n_outer = m + 1; return; }
-    const dcx beta = zmul(a_rho, rtr);
+    const dcx beta = zmul(zmul(alpha, rtr), zinv(rho0));
     S->rho0 = pk(rtr);
     d.rec_beta[(m + 1) * d.L] = pk(beta);
 }
