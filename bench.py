@@ -512,11 +512,11 @@ def main():
               "frac": (hop64_tflops / 1.25) if hop64_tflops else None, "traffic": None,
               "peak_source": "nominal GB300 FP64 (no measured FP64 peak)", "algorithmic_flops_per_launch": hop64_flops,
               "mean_launch_ms": hop64_ms, "launches_timed": hop64_n, "total_ms": hop64_ms * hop64_n}
-    #   double-float hop (row split, compensated arithmetic): bound by FP32 issue;
-    #   13,050 thread instructions per site, the ncu instruction count of one
-    #   16^3 x 32 launch (smsp__inst_executed x 32 / V), against 152 SMs x 128
-    #   FP32 lanes x 2.07 GHz = 40.3 T instructions/s.
-    hopdf_instr = 13050.0 * V
+    #   double-float hop (row split, shared projection, compensated arithmetic):
+    #   bound by FP32 issue; 11,650 thread instructions per site, the ncu
+    #   instruction count of one 16^3 x 32 launch (smsp__inst_executed x 32 / V),
+    #   against 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3 T instructions/s.
+    hopdf_instr = 11650.0 * V
     hopdf_t = hopdf_instr / (hopdf_ms * 1e-3) / 1e12 if hopdf_ms > 0 else None
     roofdf = {"kernel": "k_hop1_rows<df> (one D_w sweep, double-float head, row split)", "bound": "alu",
               "measured_over": over, "achieved": hopdf_t, "peak": 40.3, "unit": "T FP32-instructions/s",
@@ -528,7 +528,7 @@ def main():
     # lattice (cold caches): dram__bytes_read.sum + dram__bytes_write.sum
     if V == 16 * 16 * 16 * 32:
         roof32["traffic"] = 37.775e6 + 0.106e6
-        roofdf["traffic"] = 102.528e6 + 10.682e6
+        roofdf["traffic"] = 102.586e6 + 10.553e6
     roofs = [roof32, roof64, roofdf]
     dominant = max(roofs, key=lambda r: r["total_ms"])
 

@@ -420,12 +420,13 @@ __device__ __forceinline__ cx<R> hop_rows_body(const Geom& g, const LinkView<R>&
 // registers) 0.098 / 1.377 ms; the whole-site double-float sweep took 0.169 /
 // 2.65 ms.  The compensated sweep with the shared projection (64 registers, no
 // spill) takes 0.068 / 0.934 ms.
-// The variants that also form <dotv, out> and run a scalar step keep one block
-// less (80 registers, no spill).
+// The batched variant that also forms <dotv, out> and runs a scalar step keeps
+// one block less (the descriptor fields cost registers).
 #ifndef FA_HOP_ROWS_MINB
 #define FA_HOP_ROWS_MINB 5
 #endif
-template <bool DOT> constexpr int rows_min_blocks() { return DOT ? FA_HOP_ROWS_MINB - 1 : FA_HOP_ROWS_MINB; }
+template <bool DOT> constexpr int rows_min_blocks() { return FA_HOP_ROWS_MINB; }
+template <bool DOT> constexpr int rows_sys_min_blocks() { return DOT ? FA_HOP_ROWS_MINB - 1 : FA_HOP_ROWS_MINB; }
 // FP32 narrow launch shape: 128-thread blocks, 7 per SM (72 registers), used
 // when the whole lattice then fits in one wave (7 x 128 x SMs sites); a lattice
 // a little larger than one wave of the 3 x 256 shape otherwise runs a second,

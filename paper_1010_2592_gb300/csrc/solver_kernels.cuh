@@ -543,10 +543,24 @@ __device__ __noinline__ void sc_mr_seed(const SolverDev& d, int nblk) {
         const double gii = G[slot(i, i)].r;
         if (!(gii > 0.0) || !isfinite(gii)) bad = FA_EBREAKDOWN;
     }
-    if (L == 1 && !bad) {
+    if constexpr (L == 1) {
         // gamma_1 = <r_1, r_0> / <r_1, r_1>
-        gam[1] = zscale(1.0 / G[slot(1, 1)].r, conjd(G[slot(0, 1)]));
-    } else if (!bad) {
+        if (!bad) gam[1] = zscale(1.0 / G[slot(1, 1)].r, conjd(G[slot(0, 1)]));
+    } else if constexpr (L == 2) {
+        // Cramer's rule on the Hermitian 2 x 2 normal equations (no scaling:
+        // the rule is covariant under it)
+        const double g11 = G[slot(1, 1)].r, g22 = G[slot(2, 2)].r;
+        const dcx g12 = G[slot(1, 2)];
+        const dcx b1 = conjd(G[slot(0, 1)]), b2 = conjd(G[slot(0, 2)]);   // <r_i, r_0>
+        const double det = __fma_rn(g11, g22, -zabs2(g12));
+        if (bad || !(det != 0.0) || !isfinite(det)) {
+            bad = bad ? bad : FA_EBREAKDOWN;
+        } else {
+            const double idet = 1.0 / det;
+            gam[1] = zscale(idet, zsub(zscale(g22, b1), zmul(g12, b2)));
+            gam[2] = zscale(idet, zsub(zscale(g11, b2), zmul(conjd(g12), b1)));
+        }
+    } else {
         // Diagonal scaling by powers of two (exact; integer work only), so that
         // the scaled diagonal lies in [1, 4).
         double dsc[L];
@@ -560,19 +574,7 @@ __device__ __noinline__ void sc_mr_seed(const SolverDev& d, int nblk) {
             Ab[i - 1][L] = zscale(dsc[i - 1], conjd(G[slot(0, i)]));   // <r_i, r_0>
         }
         dcx z[L];
-        if constexpr (L == 2) {
-            // Cramer's rule on the Hermitian 2 x 2 system
-            const double a11 = Ab[0][0].r, a22 = Ab[1][1].r;
-            const dcx a12 = Ab[0][1];
-            const double det = __fma_rn(a11, a22, -zabs2(a12));
-            if (!(det != 0.0) || !isfinite(det)) {
-                bad = FA_EBREAKDOWN;
-            } else {
-                const double idet = 1.0 / det;
-                z[0] = zscale(idet, zsub(zscale(a22, Ab[0][L]), zmul(a12, Ab[1][L])));
-                z[1] = zscale(idet, zsub(zscale(a11, Ab[1][L]), zmul(conjd(a12), Ab[0][L])));
-            }
-        } else {
+        {
             // elimination with partial pivoting (the power basis r_1..r_l can
             // make the normal equations numerically indefinite for large l; any
             // solution is a valid MR polynomial); one inverse per pivot
@@ -1118,7 +1120,7 @@ k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, i
 
 // double-float batches: the row-split sweep (kRowThreads per block)
 template <typename R, bool DOT>
-__global__ void __launch_bounds__(kRowThreads, rows_min_blocks<DOT>())
+__global__ void __launch_bounds__(kRowThreads, rows_sys_min_blocks<DOT>())
 k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
                ScalarStep step) {
     const SolverDev& d = ds[blockIdx.y];
