@@ -357,6 +357,7 @@ def main():
     ctx.set_params(w["mass"], w["mu"], w["t_bc"], c)
     om, sg = fa.neuberger_poles(ns)
     ctx.set_poles(om, sg)
+    tune = ctx.autotune(reps=20)        # FP32 sweep launch shape for this lattice (untimed)
     b = torch.from_numpy(w["b"]).cuda()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
@@ -547,6 +548,8 @@ def main():
         "stencil_gbs": achieved,
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": int(b_pin.numel() * 16),
                 "d2h_bytes_per_step": int(y_pin.numel() * 16), "rel_err": e2e_err},
+        "fp32_sweep_shape": {"chosen": ["auto", "wide", "narrow"][tune["shape"]],
+                             "ms_per_launch_wide_narrow": tune["times_ms"]},
         "gpu_launches": head_launches // max(1, args.steps),
         "gpu_launches_total_timed": head_launches,
         "clocks": clk,

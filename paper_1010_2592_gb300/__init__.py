@@ -35,7 +35,13 @@ EXPORTS = (
     "fa_apply_f", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
     "fa_hop_timing_reset", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
+    "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune",
 )
+
+# FP32 sweep launch shapes (fa_hop_shape)
+SHAPE_AUTO, SHAPE_WIDE, SHAPE_NARROW = 0, 1, 2
+_SHAPE = {"auto": SHAPE_AUTO, "wide": SHAPE_WIDE, "narrow": SHAPE_NARROW,
+          SHAPE_AUTO: SHAPE_AUTO, SHAPE_WIDE: SHAPE_WIDE, SHAPE_NARROW: SHAPE_NARROW}
 
 
 class FAError(RuntimeError):
@@ -107,6 +113,9 @@ def load_library(path=LIB_PATH):
         "fa_launch_count": (LL, [P]),
         "fa_hop_timing": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_reset": (I, [P]),
+        "fa_set_hop_shape": (I, [P, I]),
+        "fa_get_hop_shape": (I, [P]),
+        "fa_autotune": (I, [P, I, ctypes.POINTER(D)]),
         "fa_status_string": (ctypes.c_char_p, [I]),
         "fa_last_error": (ctypes.c_char_p, []),
         "fa_version": (ctypes.c_char_p, []),
@@ -329,3 +338,68 @@ class Context:
 
     def hop_timing_reset(self):
         _check(self.lib.fa_hop_timing_reset(self.h), "fa_hop_timing_reset")
+
+    def set_hop_shape(self, shape):
+        """FP32 sweep launch shape: "auto", "wide" or "narrow" (fa_set_hop_shape)."""
+        _check(self.lib.fa_set_hop_shape(self.h, _SHAPE[shape]), "fa_set_hop_shape")
+
+    def hop_shape(self):
+        return int(self.lib.fa_get_hop_shape(self.h))
+
+    def autotune(self, reps=20, cache=None):
+        """Pick the fastest FP32 sweep launch shape for this lattice (fa_autotune).
+
+        With `cache` (a JSON file path), a choice stored for the same lattice
+        dimensions and GPU is applied without timing, and a new timing is stored.
+        Returns {"shape": k, "times_ms": [wide, narrow] or None, "cached": bool}."""
+        key = tune_key(self.dims, _device_name())
+        if cache is not None:
+            entry = load_tune_cache(cache).get(key)
+            if entry is not None:
+                self.set_hop_shape(int(entry["shape"]))
+                return {"shape": int(entry["shape"]), "times_ms": entry.get("times_ms"), "cached": True}
+        times = (ctypes.c_double * SHAPE_NARROW)()
+        rc = self.lib.fa_autotune(self.h, int(reps), times)
+        if rc < 0:
+            _check(rc, "fa_autotune")
+        result = {"shape": int(rc), "times_ms": [float(t) for t in times], "cached": False}
+        if cache is not None:
+            store_tune_cache(cache, key, {"shape": result["shape"], "times_ms": result["times_ms"]})
+        return result
+
+
+# ------------------------------------------------------------------ autotuner cache
+def _device_name():
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device()) if torch.cuda.is_available() else "none"
+
+
+def tune_key(dims, device_name, precision="f32"):
+    """Cache key of an autotuned launch shape: lattice dimensions, precision, GPU."""
+    return f"{'x'.join(str(int(d)) for d in dims)}|{precision}|{device_name}"
+
+
+def load_tune_cache(path):
+    """The autotuner cache (a JSON object), or {} when the file is absent or unreadable."""
+    import json
+    import os
+    if not os.path.exists(path):
+        return {}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def store_tune_cache(path, key, entry):
+    """Add one entry to the autotuner cache (written to a temporary file, then renamed)."""
+    import json
+    import os
+    data = load_tune_cache(path)
+    data[key] = entry
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)

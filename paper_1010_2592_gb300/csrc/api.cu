@@ -345,4 +345,53 @@ int fa_hop_timing_reset(fa_ctx* c) {
     return FA_OK;
 }
 
+int fa_set_hop_shape(fa_ctx* c, int shape) {
+    if (!c || shape < FA_SHAPE_AUTO || shape > FA_SHAPE_NARROW) {
+        set_error("fa_set_hop_shape: unknown shape %d", shape);
+        return FA_EINVAL;
+    }
+    c->hop_shape = shape;
+    return FA_OK;
+}
+
+int fa_get_hop_shape(const fa_ctx* c) { return c ? c->hop_shape : FA_EINVAL; }
+
+// Time each FP32 sweep launch shape on the context's lattice: the sweep
+// g5 D_w(mu) on a scratch spinor, warm-up launches first, then `reps` launches
+// between two CUDA events on the context's stream (the mean is what a solve
+// sees back to back).  The fastest shape is set.
+int fa_autotune(fa_ctx* c, int reps, double* times_ms) {
+    if (!c || reps < 1 || !times_ms) return FA_EINVAL;
+    if (!c->have_gauge || !c->have_params) return FA_ESTATE;
+    const int V = c->g.V;
+    const size_t b = (size_t)6 * V * sizeof(float4);
+    CUDA_OR(c->io32a.ensure(b), "fa_autotune: alloc");
+    CUDA_OR(c->io32b.ensure(b), "fa_autotune: alloc");
+    CUDA_OR(cudaMemsetAsync(c->io32a.p, 0, b, c->stream), "fa_autotune: clear");
+    float4 *a = c->io32a.as<float4>(), *o = c->io32b.as<float4>();
+    const int saved = c->hop_shape;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_OR(cudaEventCreate(&e0), "fa_autotune: event");
+    CUDA_OR(cudaEventCreate(&e1), "fa_autotune: event");
+    int best = FA_SHAPE_WIDE, rc = FA_OK;
+    double best_ms = 0.0;
+    for (int shape = FA_SHAPE_WIDE; shape <= FA_SHAPE_NARROW && rc == FA_OK; ++shape) {
+        c->hop_shape = shape;
+        for (int k = 0; k < 3 && rc == FA_OK; ++k) rc = hop_f32(c, a, o, 1.0, false, true, false, nullptr, nullptr, nullptr);
+        if (rc != FA_OK) break;
+        cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < reps && rc == FA_OK; ++k) rc = hop_f32(c, a, o, 1.0, false, true, false, nullptr, nullptr, nullptr);
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "fa_autotune: timing"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        times_ms[shape - 1] = (double)ms / reps;
+        if (shape == FA_SHAPE_WIDE || times_ms[shape - 1] < best_ms) { best = shape; best_ms = times_ms[shape - 1]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->hop_shape = rc == FA_OK ? best : saved;
+    return rc == FA_OK ? best : rc;
+}
+
 }  // extern "C"

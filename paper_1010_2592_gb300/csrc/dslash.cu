@@ -72,7 +72,7 @@ hop_rows_kernel(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cd
 template <typename R, typename LP, typename SP>
 static int launch_hop_t(const Geom& g, const LP* links, const SP* in, SP* out, double diag, double ef,
                         double eb, double t_bc, double scale, bool g5in, bool g5out, const SP* dot_with,
-                        double2* partials, const int* done, cudaStream_t st) {
+                        double2* partials, const int* done, cudaStream_t st, int shape = 0) {
     LinkView<R> U{links, g.V};
     SpinorView<R> vin{const_cast<SP*>(in), g.V};
     SpinorView<R> vout{out, g.V};
@@ -81,7 +81,7 @@ static int launch_hop_t(const Geom& g, const LP* links, const SP* in, SP* out, d
     const R ref = (R)ef, reb = (R)eb, rbc = (R)t_bc;
     const bool dot = dot_with != nullptr;
     if constexpr (std::is_same<R, float>::value) {
-      if (hop_narrow(g.V)) {
+      if (hop_use_narrow(shape, g.V)) {
         constexpr int NT = kHopNarrowThreads, MB = kHopNarrowBlocks;
         const int nb = (g.V + NT - 1) / NT;
 #define FA_HOPN(A, B, C) hop_kernel<R, A, B, C, NT, MB><<<nb, NT, 0, st>>>(g, U, vin, vout, cdiag, chop, ref, reb, rbc, vd, partials, done)
@@ -138,9 +138,9 @@ int launch_hop_df(const Geom& g, const float4* links, const float4* in, float4* 
 
 int launch_hop_f32(const Geom& g, const float4* links, const float4* in, float4* out, double diag,
                    double ef, double eb, double t_bc, double scale, bool g5in, bool g5out,
-                   const float4* dot_with, double2* partials, const int* done, cudaStream_t st) {
+                   const float4* dot_with, double2* partials, const int* done, cudaStream_t st, int shape) {
     return launch_hop_t<float>(g, links, in, out, diag, ef, eb, t_bc, scale, g5in, g5out, dot_with,
-                               partials, done, st);
+                               partials, done, st, shape);
 }
 
 // ------------------------------------------------------------------ link force (adjoint)

@@ -93,6 +93,7 @@ struct fa_ctx {
     double hop_ms[3] = {0.0, 0.0, 0.0};   // FP64, FP32, double-float
     long long hop_count[3] = {0, 0, 0};
     bool hop_timing = false;
+    int hop_shape = 0;                   // FP32 sweep launch shape (fa_hop_shape; 0: automatic)
     std::vector<cudaEvent_t> hop_ev;     // start/stop pairs, reused across solves
     std::vector<int> hop_ev_kind;        // precision index of each recorded pair
     size_t hop_ev_used = 0;              // pairs recorded since the last collection

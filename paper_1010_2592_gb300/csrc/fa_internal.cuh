@@ -383,10 +383,12 @@ int launch_hop_f64(const Geom& g, const double2* links, const double2* in, doubl
                    double diag, double ef, double eb, double t_bc, double scale,
                    bool g5in, bool g5out, const double2* dot_with, double2* partials,
                    const int* done, cudaStream_t st);
+// shape: 0 narrow when the lattice fits one wave of it, 1 wide (kThreads x
+// FA_HOP_MINB per SM), 2 narrow (kHopNarrowThreads x kHopNarrowBlocks per SM)
 int launch_hop_f32(const Geom& g, const float4* links, const float4* in, float4* out,
                    double diag, double ef, double eb, double t_bc, double scale,
                    bool g5in, bool g5out, const float4* dot_with, double2* partials,
-                   const int* done, cudaStream_t st);
+                   const int* done, cudaStream_t st, int shape = 0);
 
 int launch_hop_df(const Geom& g, const float4* links, const float4* in, float4* out,
                   double diag, double ef, double eb, double t_bc, double scale,
@@ -403,6 +405,8 @@ int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* 
 // launch shape (kHopNarrowThreads x kHopNarrowBlocks per SM, one wave)
 int sm_count();
 bool hop_narrow(int V);
+// the narrow shape for a sweep of V sites under launch shape `shape`
+inline bool hop_use_narrow(int shape, int V) { return shape == 2 || (shape == 0 && hop_narrow(V)); }
 int launch_convert_f64_to_f32(const Geom& g, const double2* in, float4* out, cudaStream_t st);
 // double-float spinors: [12][V] float4 = (re.hi, re.lo, im.hi, im.lo)
 int launch_pack_spinor_df(const Geom& g, const double* canon, float4* out, cudaStream_t st);

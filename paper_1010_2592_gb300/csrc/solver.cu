@@ -79,7 +79,7 @@ int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, b
     const double mu = dagger_mu ? -c->mu : c->mu;
     hop_timing_begin(c, 1);
     int rc = launch_hop_f32(c->g, links32_of(c), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu),
-                            c->t_bc, scale, g5in, g5out, dot_with, partials, done, c->stream);
+                            c->t_bc, scale, g5in, g5out, dot_with, partials, done, c->stream, c->hop_shape);
     hop_timing_end(c);
     c->launches++;
     if (rc == FA_ECUDA) return cuda_fail(cudaGetLastError(), "hop_f32");
@@ -315,7 +315,7 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
             } else {
                 bool narrow = false;
                 if constexpr (rp_of<R>() == RP32) {
-                    if (hop_narrow(V)) {
+                    if (hop_use_narrow(c->hop_shape, V)) {
                         narrow = true;
                         constexpr int NT = kHopNarrowThreads, MB = kHopNarrowBlocks;
                         const int nbh = (V + NT - 1) / NT;
