@@ -62,6 +62,9 @@ def parse():
                    help="precision of the head of the headline solve: double-float or FP64")
     p.add_argument("--store-gb", type=float, default=0.0,
                    help="pseudo-double-pass store budget (0: the library default)")
+    p.add_argument("--ns-sweep", action="store_true",
+                   help="runtime against the number of poles at a fixed number of BiCG steps "
+                        "(M l = 64) for the single-pass, double-pass and pseudo-double-pass forms")
     return p.parse_args()
 
 
@@ -251,6 +254,53 @@ def run_hop_only(args):
 
 
 # ------------------------------------------------------------------ batched workload
+def run_ns_sweep(args):
+    """Runtime against N_s at a fixed number of BiCG steps (the setting of the
+    paper's Fig. 2, Sec. 3, which uses M l = 256 on 4^3 x 8): every solve runs
+    exactly 64 / l outer iterations (the fixed-cost flag; the seed needs about
+    100 BiCG steps to reach tol 1e-10 on this operator, so none stops early),
+    FP64, on the workload's lattice (or --dims).  Shifts freeze when they
+    converge, as in any solve (unfrozen, the zeta of the large shifts overflow
+    FP64 within a few hundred steps).  One JSON line per (form, l): ms per solve
+    for each N_s."""
+    import torch
+    import inputs
+    import paper_1010_2592_gb300 as fa
+    w = inputs.make_workload(args.workload, args.dims)
+    dims = w["dims"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = fa.Context(dims, stream)
+    ctx.set_gauge(torch.from_numpy(w["U"]).cuda())
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], 1.0)
+    c = ctx.estimate_scale(torch.from_numpy(w["v0"]).cuda(), 100)
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], c)
+    b = torch.from_numpy(w["b"]).cuda()
+    ns_list = (2, 4, 8, 16, 32, 64)
+    for ell in (1, 2, 4, 8):
+        M = 64 // ell
+        for form in ("single", "double", "pseudo"):
+            row = {"mode": "ns_sweep", "lattice": "x".join(map(str, dims)), "ell": ell, "outer_iters": M,
+                   "form": form, "precision": "f64", "ms": {}}
+            for ns in ns_list:
+                ctx.set_poles(*fa.neuberger_poles(ns))
+                kw = dict(ell=ell, tol=1e-10, max_outer=M, mode=form, precision="f64", fixed_iters=True)
+                ctx.apply_f(b, **kw)
+                times = []
+                for _ in range(max(1, args.steps)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    r = ctx.apply_f(b, **kw)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                row["ms"][str(ns)] = statistics.median(times)
+                row.setdefault("status", r.stats["status"])
+            print(json.dumps(row), flush=True)
+    ctx.close()
+
+
 def run_batched(args):
     """72 systems: 12 spin-colour point sources on each of 6 lattices of three
     shapes (2 x 8^4, 2 x 12^3 x 24, 2 x 16^3 x 32), mu_k ~ U[0, 0.2], 16 Neuberger
@@ -331,6 +381,9 @@ def main():
     if args.hop_only:
         run_hop_only(args)
         return
+    if args.ns_sweep:
+        run_ns_sweep(args)
+        return
     if args.workload == "wilson_batched_72":
         run_batched(args)
         return
@@ -377,6 +430,12 @@ def main():
         "double_f64": dict(mode="double", precision="f64"),
         "single_f64": dict(mode="single", precision="f64"),
         "double_f32": dict(mode="double", precision="f32"),
+        # the 16^3 x 32 configuration's literal form: FP32 bulk with reliable updates
+        # every 50 BiCG iterations (25 outer iterations of BiCGstab(2)), and the
+        # headline with the same reliable updates
+        "double_f32_reliable": dict(mode="double", precision="f32", reliable_every=25),
+        "pseudo_mixed_reliable": dict(mode="pseudo", precision=args.head, switch_resid=args.switch_resid,
+                                      graph=True, store_gb=args.store_gb, reliable_every=25),
     }
     chosen = {}
     if args.quick:
@@ -444,7 +503,9 @@ def main():
     # comparison variants (fewer steps)
     other = {}
     for name in ([] if args.quick else ["pseudo_mixed_fp64head", "double_mixed", "double_f64", "single_f64",
-                                        "double_f32"]):
+                                        "double_f32", "double_f32_reliable", "pseudo_mixed_reliable"]):
+        if name not in variants:
+            continue
         k = max(1, min(args.steps, 3))
         lst, _, res = timed(name, k, 1)
         tol, e, _ = chosen[name]

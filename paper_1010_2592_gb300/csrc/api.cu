@@ -1,6 +1,7 @@
 // C-ABI entry points of libfapath (declared in include/fapath.h).
 #include <cmath>
 #include <cstdarg>
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -356,10 +357,13 @@ int fa_set_hop_shape(fa_ctx* c, int shape) {
 
 int fa_get_hop_shape(const fa_ctx* c) { return c ? c->hop_shape : FA_EINVAL; }
 
-// Time each FP32 sweep launch shape on the context's lattice: the sweep
-// g5 D_w(mu) on a scratch spinor, warm-up launches first, then `reps` launches
-// between two CUDA events on the context's stream (the mean is what a solve
-// sees back to back).  The fastest shape is set.
+// Time each FP32 sweep launch shape on the context's lattice: chains of sweeps
+// g5 D_w(mu) that read the previous sweep's output (as in a solve), `reps`
+// launches between two CUDA events on the context's stream, three rounds with
+// the shapes interleaved, the best round per shape.  The automatic choice is
+// kept unless the other shape is faster by more than 3 % (single-launch timings
+// of the two shapes are close; inside a solve the automatic choice measured
+// better).
 int fa_autotune(fa_ctx* c, int reps, double* times_ms) {
     if (!c || reps < 1 || !times_ms) return FA_EINVAL;
     if (!c->have_gauge || !c->have_params) return FA_ESTATE;
@@ -368,30 +372,43 @@ int fa_autotune(fa_ctx* c, int reps, double* times_ms) {
     CUDA_OR(c->io32a.ensure(b), "fa_autotune: alloc");
     CUDA_OR(c->io32b.ensure(b), "fa_autotune: alloc");
     CUDA_OR(cudaMemsetAsync(c->io32a.p, 0, b, c->stream), "fa_autotune: clear");
-    float4 *a = c->io32a.as<float4>(), *o = c->io32b.as<float4>();
+    CUDA_OR(cudaMemsetAsync(c->io32b.p, 0, b, c->stream), "fa_autotune: clear");
+    float4* buf[2] = {c->io32a.as<float4>(), c->io32b.as<float4>()};
     const int saved = c->hop_shape;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_OR(cudaEventCreate(&e0), "fa_autotune: event");
     CUDA_OR(cudaEventCreate(&e1), "fa_autotune: event");
-    int best = FA_SHAPE_WIDE, rc = FA_OK;
-    double best_ms = 0.0;
-    for (int shape = FA_SHAPE_WIDE; shape <= FA_SHAPE_NARROW && rc == FA_OK; ++shape) {
-        c->hop_shape = shape;
-        for (int k = 0; k < 3 && rc == FA_OK; ++k) rc = hop_f32(c, a, o, 1.0, false, true, false, nullptr, nullptr, nullptr);
-        if (rc != FA_OK) break;
-        cudaEventRecord(e0, c->stream);
-        for (int k = 0; k < reps && rc == FA_OK; ++k) rc = hop_f32(c, a, o, 1.0, false, true, false, nullptr, nullptr, nullptr);
-        cudaEventRecord(e1, c->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "fa_autotune: timing"); break; }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        times_ms[shape - 1] = (double)ms / reps;
-        if (shape == FA_SHAPE_WIDE || times_ms[shape - 1] < best_ms) { best = shape; best_ms = times_ms[shape - 1]; }
+    double best_ms[2] = {1e30, 1e30};
+    int rc = FA_OK;
+    auto chain = [&](int n) {
+        for (int k = 0; k < n && rc == FA_OK; ++k)
+            rc = hop_f32(c, buf[k & 1], buf[(k + 1) & 1], 1.0, false, true, false, nullptr, nullptr, nullptr);
+    };
+    for (int round = 0; round < 3 && rc == FA_OK; ++round) {
+        for (int shape = FA_SHAPE_WIDE; shape <= FA_SHAPE_NARROW && rc == FA_OK; ++shape) {
+            c->hop_shape = shape;
+            chain(3);
+            cudaEventRecord(e0, c->stream);
+            chain(reps);
+            cudaEventRecord(e1, c->stream);
+            if (rc != FA_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "fa_autotune: timing"); break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_ms[shape - 1] = std::min(best_ms[shape - 1], (double)ms / reps);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->hop_shape = rc == FA_OK ? best : saved;
-    return rc == FA_OK ? best : rc;
+    if (rc != FA_OK) {
+        c->hop_shape = saved;
+        return rc;
+    }
+    times_ms[0] = best_ms[0];
+    times_ms[1] = best_ms[1];
+    const int deflt = hop_narrow(V) ? FA_SHAPE_NARROW : FA_SHAPE_WIDE, other = 3 - deflt;
+    c->hop_shape = best_ms[other - 1] < 0.97 * best_ms[deflt - 1] ? other : deflt;
+    return c->hop_shape;
 }
 
 }  // extern "C"

@@ -226,6 +226,7 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     d.part = c->partials.as<double2>();
     d.x64 = nullptr;
     d.b64 = nullptr;
+    d.fixed_iters = 0;
     return d;
 }
 
@@ -615,6 +616,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     // graphs need a capturable stream (not the legacy default stream)
     B.use_graph = (p->flags & 4) != 0 && c0->stream != nullptr && c0->stream != cudaStreamLegacy;
     for (auto* c : B.sys) B.host.push_back(make_dev(c, Lo));
+    for (auto& h : B.host) h.fixed_iters = (p->flags & 8) ? 1 : 0;
     cudaStream_t st = c0->stream;
     const bool timing = (p->flags & 1) != 0;
     c0->hop_timing = (p->flags & 2) != 0;

@@ -94,6 +94,9 @@ struct SolverDev {
     // recurrence when not null) and the packed source b (FP64)
     double2* x64;
     const double2* b64;
+    // nonzero: max_outer is the planned number of outer iterations, reaching it
+    // freezes the remaining shifts instead of failing (fixed-cost runs)
+    int fixed_iters;
 };
 
 template <typename R> struct Vec;
@@ -269,6 +272,7 @@ __device__ __forceinline__ bool last_block(DevState* S) {
     return is_last != 0;
 }
 
+__device__ __forceinline__ dcx zneg(dcx a) { return {-a.r, -a.i}; }   // a sign flip, free on FMA operands
 __device__ __forceinline__ dcx zmul(dcx a, dcx b) {
     return {__fma_rn(a.r, b.r, -__dmul_rn(a.i, b.i)), __fma_rn(a.r, b.i, __dmul_rn(a.i, b.r))};
 }
@@ -675,9 +679,10 @@ __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     __shared__ int n_act, all_small;
     if (threadIdx.x == 0) { n_act = 0; all_small = 1; }
     __syncthreads();
+    const bool last = d.fixed_iters && m + 1 >= d.max_outer;
     if (act) {
         const double z2 = zabs2(ld(zv));
-        if (rn2 <= tol2b * z2) {
+        if (last || rn2 <= tol2b * z2) {
             d.active[sh] = 0;
             d.iters[sh] = m + 1;
         } else {
@@ -694,7 +699,7 @@ __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     if (head && all_small) S->switch_req = 1;
     if (n_act == 0) { S->done = 1; S->n_outer = m + 1; return; }
     if (m + 1 >= d.max_outer) { fail(S, FA_ENOCONV); S->n_outer = m + 1; return; }
-    const dcx rho0 = zscale(-1.0, zmul(omega, rho_old));
+    const dcx rho0 = zneg(zmul(omega, rho_old));
     if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); S->n_outer = m + 1; return; }
     const dcx beta = zmul(zmul(alpha, rtr), zinv(rho0));
     S->rho0 = pk(rtr);
@@ -1359,6 +1364,7 @@ __global__ void k_sweep(const SolverDev* __restrict__ ds) {
     dcx lU[L + 1];
 #pragma unroll
     for (int i = 0; i <= L; ++i) lU[i] = mk(0.0);
+    // fused multiply-adds throughout (the sweep is bound by FP64 issue in one warp)
     for (int m = Ms - 1; m >= 0; --m) {
         const double2* P = d.prec + ((size_t)sh * d.max_outer + m) * ps_stride(L);
         const double2* G = d.rec_gamma + m * (L + 1);
@@ -1367,31 +1373,31 @@ __global__ void k_sweep(const SolverDev* __restrict__ ds) {
         for (int k = 0; k < NC; ++k) c[k] = mk(0.0);
         // MR, reversed: u0 <- (u0 - sum gamma_j u_j)/p_s, then x += sum cx_k r_k
         {
-            const dcx t = lU[0] * ld(P[5 * L]);
+            const dcx t = zmul(lU[0], ld(P[5 * L]));
 #pragma unroll
-            for (int jj = 1; jj <= L; ++jj) lU[jj] = lU[jj] - ld(G[jj]) * t;
+            for (int jj = 1; jj <= L; ++jj) lU[jj] = zfma(zneg(ld(G[jj])), t, lU[jj]);
             lU[0] = t;
 #pragma unroll
-            for (int k = 0; k < L; ++k) c[slot_mr(L, k)] = c[slot_mr(L, k)] + lX * ld(P[5 * L + 1 + k]);
+            for (int k = 0; k < L; ++k) c[slot_mr(L, k)] = zfma(lX, ld(P[5 * L + 1 + k]), c[slot_mr(L, k)]);
         }
 #pragma unroll
         for (int j = L - 1; j >= 0; --j) {
             const double2* Q = P + 5 * j;
             // x += alpha_s u_0
-            lU[0] = lU[0] + ld(Q[0]) * lX;
+            lU[0] = zfma(ld(Q[0]), lX, lU[0]);
             // u_{j+1} <- r_old_j/(alpha_s zeta) - r_j/(alpha_s zeta_new) - sigma u_j
             const dcx lu = lU[j + 1];
-            c[slot_old(j, j)] = c[slot_old(j, j)] + lu * ld(Q[3]);
+            c[slot_old(j, j)] = zfma(lu, ld(Q[3]), c[slot_old(j, j)]);
             const int snew = (j < L - 1) ? slot_old(j + 1, j) : slot_mr(L, L - 1);
-            c[snew] = c[snew] - lu * ld(Q[4]);
-            lU[j] = lU[j] - sg * lu;
+            c[snew] = zfma(lu, zneg(ld(Q[4])), c[snew]);
+            lU[j] = zrfma(-sg, lu, lU[j]);
             lU[j + 1] = mk(0.0);
             // u_i <- r_old_i/zeta - beta_s u_i
-            const dcx iz = ld(Q[2]), bs = ld(Q[1]);
+            const dcx iz = ld(Q[2]), nbs = zneg(ld(Q[1]));
 #pragma unroll
             for (int i = 0; i <= j; ++i) {
-                c[slot_old(j, i)] = c[slot_old(j, i)] + lU[i] * iz;
-                lU[i] = -1.0 * (bs * lU[i]);
+                c[slot_old(j, i)] = zfma(lU[i], iz, c[slot_old(j, i)]);
+                lU[i] = zmul(nbs, lU[i]);
             }
         }
         double2* out = d.cs + ((size_t)sh * d.max_outer + m) * NC;

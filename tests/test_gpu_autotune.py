@@ -29,10 +29,16 @@ def test_autotune_picks_the_faster_shape_and_caches(tmp_path):
     dims = (16, 16, 16, 32)
     w = inputs.make_workload("wilson_16x16x16x32", dims)
     ctx = make_context(dims, w["U"], w["mass"], w["mu"], 0.03)
+    import torch
     r = ctx.autotune(reps=10)
     t = r["times_ms"]
     assert not r["cached"] and all(x > 0 for x in t)
-    assert r["shape"] == 1 + int(np.argmin(t)) and ctx.hop_shape() == r["shape"]
+    # the automatic shape is kept unless the other is faster by more than 3 %
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    deflt = fa.SHAPE_NARROW if (np.prod(dims) + 127) // 128 <= 7 * sms else fa.SHAPE_WIDE
+    other = 3 - deflt
+    expect = other if t[other - 1] < 0.97 * t[deflt - 1] else deflt
+    assert r["shape"] == expect and ctx.hop_shape() == expect
     cache = str(tmp_path / "tune.json")
     r1 = ctx.autotune(reps=5, cache=cache)
     ctx.set_hop_shape("auto")

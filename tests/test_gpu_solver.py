@@ -247,3 +247,22 @@ def test_reliable_updates(precision):
     assert rel(to_host(rq.y), to_host(rd.y)) < max(wide, 1e-7 if precision != "f64" else 0)
     with pytest.raises(fa.FAError):
         fa.apply_f_batched([ctx, ctx_for(w)], [b, b], ell=2, precision="f64", reliable_every=5)
+
+
+def test_fixed_cost_runs_agree_across_forms():
+    """flags bit 3: exactly max_outer outer iterations, remaining shifts frozen, status OK;
+    single-, double- and pseudo-double-pass forms then give the same y (same iterates)."""
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    b = to_dev(w["b"])
+    ys = {}
+    for mode in ("single", "double", "pseudo"):
+        r = ctx.apply_f(b, ell=2, tol=1e-300, max_outer=6, mode=mode, precision="f64", fixed_iters=True)
+        assert r.stats["status"] == 0 and r.stats["outer_iters"] == 6
+        assert max(r.stats["iters_per_shift"][:w["ns"]]) == 6
+        ys[mode] = to_host(r.y)
+    assert rel(ys["double"], ys["single"]) < 1e-12
+    assert rel(ys["pseudo"], ys["double"]) < 1e-13
+    with pytest.raises(fa.FAError) as e:
+        ctx.apply_f(b, ell=2, tol=1e-300, max_outer=6, mode="double", precision="f64")
+    assert e.value.status == fa.FA_ENOCONV
