@@ -296,6 +296,7 @@ def run_ns_sweep(args):
                     torch.cuda.synchronize()
                     times.append(e0.elapsed_time(e1))
                 row["ms"][str(ns)] = statistics.median(times)
+                row.setdefault("outer_iters_run", {})[str(ns)] = r.stats["outer_iters"]
                 row.setdefault("status", r.stats["status"])
             print(json.dumps(row), flush=True)
     ctx.close()
