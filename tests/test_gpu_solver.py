@@ -266,3 +266,31 @@ def test_fixed_cost_runs_agree_across_forms():
     with pytest.raises(fa.FAError) as e:
         ctx.apply_f(b, ell=2, tol=1e-300, max_outer=6, mode="double", precision="f64")
     assert e.value.status == fa.FA_ENOCONV
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "mixed_df"])
+def test_error_paths_return_status(precision):
+    """Non-finite input, a non-finite link and a forced breakdown come back as
+    status codes through the device-resident state (no trap, no hang)."""
+    w = workload_case(C1)
+    kw = dict(ell=2, tol=1e-10, mode="pseudo" if precision == "mixed_df" else "double", precision=precision,
+              check=False)
+    # NaN in the source: rejected when the solve reads |b|^2
+    ctx = ctx_for(w)
+    b = w["b"].copy()
+    b[0, 0, 0, 0, 0, 0] = np.nan
+    assert ctx.apply_f(to_dev(b), **kw).stats["status"] == fa.FA_EINVAL
+    # one non-finite link: the inner products turn non-finite
+    U = w["U"].copy()
+    U[1, 2, 3, 0, 3, 0, 0] = np.inf
+    ctx = make_context(w["dims"], U, w["mass"], w["mu"], w["c"], w["t_bc"], w["omega"], w["sigma"])
+    st = ctx.apply_f(to_dev(w["b"]), **kw).stats["status"]
+    assert st in (fa.FA_ENONFINITE, fa.FA_EBREAKDOWN)
+    # A = 0 (zero links, 4 + m = 0): <rt, A u_0> = 0, breakdown in the first sub-step
+    ctx = make_context(w["dims"], np.zeros_like(w["U"]), -4.0, 0.0, 1.0, -1, w["omega"], w["sigma"])
+    assert ctx.apply_f(to_dev(w["b"]), **kw).stats["status"] == fa.FA_EBREAKDOWN
+    # the context stays usable after an error status
+    ctx = ctx_for(w)
+    r = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, precision=precision,
+                    mode="pseudo" if precision == "mixed_df" else "double")
+    assert r.stats["status"] == 0
