@@ -268,11 +268,11 @@ class Context:
     @staticmethod
     def params(ell=2, tol=1e-10, max_outer=2000, mode="double", precision="f64",
                switch_resid=0.0, timing=False, hop_timing=False, store_gb=0.0, graph=False,
-               reliable_every=0, fixed_iters=False):
+               reliable_every=0, fixed_iters=False, overlap=True):
         return SolverParams(int(ell), float(tol), int(max_outer), _MODE[mode], _PREC[precision],
                             float(switch_resid),
                             (1 if timing else 0) | (2 if hop_timing else 0) | (4 if graph else 0)
-                            | (8 if fixed_iters else 0),
+                            | (8 if fixed_iters else 0) | (0 if overlap else 16),
                             float(store_gb), int(reliable_every))
 
     def apply_f(self, b, out=None, check=True, **kw):

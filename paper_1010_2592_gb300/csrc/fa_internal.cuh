@@ -28,6 +28,18 @@ struct Geom {
     int V;
 };
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may be placed on the SMs while its predecessor in the stream
+// is still running; it must not touch global memory before `griddepcontrol.wait`
+// returns, which happens once the predecessor grid has completed and its writes
+// are visible.  `launch_dependents` then lets the successor start its own launch.
+// For an ordinary launch both instructions return at once.  Every kernel that
+// the solver may launch this way calls this first.
+__device__ __forceinline__ void dep_sync() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ complex
 template <typename R> struct cx { R r, i; };
 

@@ -240,7 +240,27 @@ struct Batch {
     Layout Lo{};
     int n = 0;
     bool use_graph = false;
+    bool pdl = true;                      // programmatic dependent launch inside an outer iteration
 };
+
+// Kernel launch, with programmatic stream serialization when `pdl` is set: the
+// kernel may then be placed on the SMs while its predecessor (a kernel) finishes,
+// and it waits in dep_sync() before its first memory access.  Used only for
+// kernels that call dep_sync() first and follow another kernel in the stream.
+template <typename... KArgs, typename... Args>
+static void launch(bool pdl, void (*k)(KArgs...), dim3 grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    (void)cudaLaunchKernelEx(&cfg, k, args...);   // errors surface through cudaGetLastError
+}
 
 static int upload(Batch& B) {
     FA_CUDA(cudaMemcpyAsync(B.dev, B.host.data(), B.n * sizeof(SolverDev), cudaMemcpyHostToDevice, B.c0->stream),
@@ -278,6 +298,7 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     cudaStream_t st = c->stream;
     constexpr int kind = rp_of<R>() == RP64 ? 0 : (rp_of<R>() == RP32 ? 1 : 2);
     const bool timing = c->hop_timing && !B.use_graph;
+    const bool pdl = B.pdl && !timing;
     // One system: the stand-alone hop kernel with its pointers as kernel
     // parameters (no descriptor fields held in registers).  A batch: the
     // descriptor-driven hop, one launch for all systems.
@@ -308,10 +329,10 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
             if constexpr (rp_of<R>() == RPDF) {
                 const int nbh = row_blocks(V);
                 if (dot)
-                    k_hop1_rows<R, true><<<nbh, kRowThreads, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
+                    launch(pdl, k_hop1_rows<R, true>, nbh, kRowThreads, st, h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
                                                                        vdot, h0.part, done, ds, step);
                 else
-                    k_hop1_rows<R, false><<<nbh, kRowThreads, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
+                    launch(pdl, k_hop1_rows<R, false>, nbh, kRowThreads, st, h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
                                                                         vdot, nullptr, done, ds, none);
             } else {
                 bool narrow = false;
@@ -321,20 +342,20 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
                         constexpr int NT = kHopNarrowThreads, MB = kHopNarrowBlocks;
                         const int nbh = (V + NT - 1) / NT;
                         if (dot)
-                            k_hop1<R, true, NT, MB><<<nbh, NT, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
+                            launch(pdl, k_hop1<R, true, NT, MB>, nbh, NT, st, h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
                                                                         vdot, h0.part, done, ds, step);
                         else
-                            k_hop1<R, false, NT, MB><<<nbh, NT, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
+                            launch(pdl, k_hop1<R, false, NT, MB>, nbh, NT, st, h0.g, U, vin, vout, cdiag, chop, ef, eb, bc,
                                                                          vdot, nullptr, done, ds, none);
                     }
                 }
                 if (!narrow) {
                     const int nbh = nblocks(V);
                     if (dot)
-                        k_hop1<R, true><<<nbh, kThreads, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc, vdot,
+                        launch(pdl, k_hop1<R, true>, nbh, kThreads, st, h0.g, U, vin, vout, cdiag, chop, ef, eb, bc, vdot,
                                                                   h0.part, done, ds, step);
                     else
-                        k_hop1<R, false><<<nbh, kThreads, 0, st>>>(h0.g, U, vin, vout, cdiag, chop, ef, eb, bc, vdot,
+                        launch(pdl, k_hop1<R, false>, nbh, kThreads, st, h0.g, U, vin, vout, cdiag, chop, ef, eb, bc, vdot,
                                                                    nullptr, done, ds, none);
                 }
             }
@@ -344,11 +365,11 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
         }
         if constexpr (rp_of<R>() == RPDF) {
             const dim3 gw(row_blocks(h0.V), n);
-            if (dot) k_hop_sys_rows<R, true><<<gw, kRowThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2, step);
-            else k_hop_sys_rows<R, false><<<gw, kRowThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2, none);
+            if (dot) launch(pdl, k_hop_sys_rows<R, true>, gw, kRowThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, step);
+            else launch(pdl, k_hop_sys_rows<R, false>, gw, kRowThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, none);
         } else {
-            if (dot) k_hop_sys<R, true><<<gs, kThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2, step);
-            else k_hop_sys<R, false><<<gs, kThreads, 0, st>>>(ds, in_sel, in_j, out_sel, out_j, second, p2, none);
+            if (dot) launch(pdl, k_hop_sys<R, true>, gs, kThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, step);
+            else launch(pdl, k_hop_sys<R, false>, gs, kThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, none);
         }
         if (timing) hop_timing_end(c);
         FA_LAUNCHED(c, "k_hop_sys");
@@ -360,18 +381,18 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     // convergence after |r_0|^2); the shift parts in block 0 of the next
     // vector kernel (double-pass forms) or with the seed part (single pass).
     for (int j = 0; j < L; ++j) {
-        k_update_u<R><<<gv, kThreads, 0, st>>>(ds, j, p2);
+        launch(j > 0 && pdl, k_update_u<R>, gv, kThreads, st, ds, j, p2);
         FA_LAUNCHED(c, "k_update_u");
         FA_TRY(hop(0, j, 2, 0, 0, false, none));                                   // tmp = g5 D u_j
         const ScalarStep alpha{single ? STEP_ALPHA_ALL : STEP_ALPHA, j};
         FA_TRY(hop(2, 0, 0, j + 1, 1, !pass2, pass2 ? none : alpha));              // u_{j+1}
         if (pass2) {
-            k_update_r<R, true, false><<<gv, kThreads, 0, st>>>(ds, j, p2);
+            launch(pdl, k_update_r<R, true, false>, gv, kThreads, st, ds, j, p2);
         } else if (single) {
-            if constexpr (rp_of<R>() == RP64) k_update_r<R, false, true><<<gv, kThreads, 0, st>>>(ds, j, p2);
+            if constexpr (rp_of<R>() == RP64) launch(pdl, k_update_r<R, false, true>, gv, kThreads, st, ds, j, p2);
         } else {
             // block 0: shift part of sub-step j beside the vector blocks
-            k_update_r<R, false, false, true><<<gvx, kThreads, 0, st>>>(ds, j, p2);
+            launch(pdl, k_update_r<R, false, false, true>, gvx, kThreads, st, ds, j, p2);
         }
         FA_LAUNCHED(c, "k_update_r");
         FA_TRY(hop(1, j, 2, 0, 0, false, none));                                   // tmp = g5 D r_j
@@ -379,18 +400,18 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
         FA_TRY(hop(2, 0, 1, j + 1, 1, next_beta, next_beta ? ScalarStep{STEP_BETA, j + 1} : none));   // r_{j+1}
     }
     if (!pass2) {
-        k_gram<R, L><<<gg, kThreads, 0, st>>>(ds, single ? 1 : 0);
+        launch(pdl, k_gram<R, L>, gg, kThreads, st, ds, single ? 1 : 0);
         FA_LAUNCHED(c, "k_gram");
     }
     const ScalarStep conv = pass2 ? none : ScalarStep{STEP_CONV, head ? 1 : 0};
     if (pass2) {
-        k_mr<R, L, true, false, false><<<gm, kThreads, 0, st>>>(ds, p2, none);
+        launch(pdl, k_mr<R, L, true, false, false>, gm, kThreads, st, ds, p2, none);
     } else if (single) {
         if constexpr (rp_of<R>() == RP64)
-            k_mr<R, L, false, true, true><<<gm, kThreads, 0, st>>>(ds, p2, reliable ? none : conv);
+            launch(pdl, k_mr<R, L, false, true, true>, gm, kThreads, st, ds, p2, reliable ? none : conv);
     } else {
         // block 0: shift part of the MR step beside the vector blocks
-        k_mr<R, L, false, false, true, true><<<gmx, kThreads, 0, st>>>(ds, p2, reliable ? none : conv);
+        launch(pdl, k_mr<R, L, false, false, true, true>, gmx, kThreads, st, ds, p2, reliable ? none : conv);
     }
     FA_LAUNCHED(c, "k_mr");
     if (reliable) {
@@ -410,7 +431,7 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
         FA_LAUNCHED(c, "k_reliable");
     }
     if (pass2) {
-        k_advance<<<n, 1, 0, st>>>(ds);
+        launch(pdl, k_advance, dim3(n), 1, st, ds);
         FA_LAUNCHED(c, "k_advance");
     }
     return FA_OK;
@@ -615,6 +636,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     B.flags = c0->flagbuf.as<int>();
     // graphs need a capturable stream (not the legacy default stream)
     B.use_graph = (p->flags & 4) != 0 && c0->stream != nullptr && c0->stream != cudaStreamLegacy;
+    B.pdl = (p->flags & 16) == 0;
     for (auto* c : B.sys) B.host.push_back(make_dev(c, Lo));
     for (auto& h : B.host) h.fixed_iters = (p->flags & 8) ? 1 : 0;
     cudaStream_t st = c0->stream;

@@ -751,6 +751,7 @@ __device__ __forceinline__ void site_range(int V, unsigned bx, unsigned nbx, int
 template <typename R>
 __global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
+    dep_sync();
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
     int s0, s1;
@@ -784,6 +785,7 @@ k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
 template <typename R, bool ACC, bool SHIFTS, bool XS = false>
 __global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
+    dep_sync();
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
     if (XS && blockIdx.x == 0) {
@@ -879,6 +881,7 @@ template <typename R, int L> constexpr int gram_min_blocks() { return L <= 2 ? 4
 template <typename R, int L>
 __global__ void __launch_bounds__(kThreads, gram_min_blocks<R, L>())
 k_gram(const SolverDev* __restrict__ ds, int shifts) {
+    dep_sync();
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, 0)) return;
     const typename Ch<R>::T* r = Vec<R>::r(d);
@@ -934,6 +937,7 @@ template <typename R, int L> constexpr int mr_min_blocks() {
 template <typename R, int L, bool ACC, bool SHIFTS, bool DOT, bool XS = false>
 __global__ void __launch_bounds__(kThreads, mr_min_blocks<R, L>())
 k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
+    dep_sync();
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
     const unsigned bx = blockIdx.x - (XS ? 1u : 0u), nbx = gridDim.x - (XS ? 1u : 0u);
@@ -1095,6 +1099,7 @@ template <typename R, bool DOT>
 __global__ void __launch_bounds__(kThreads, hop_min_blocks<R>())
 k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
           ScalarStep step) {
+    dep_sync();
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
     const int s = blockIdx.x * kThreads + threadIdx.x;
@@ -1128,6 +1133,7 @@ template <typename R, bool DOT>
 __global__ void __launch_bounds__(kRowThreads, rows_sys_min_blocks<DOT>())
 k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
                ScalarStep step) {
+    dep_sync();
     const SolverDev& d = ds[blockIdx.y];
     if (sys_idle(d, pass2)) return;
     const double sc = second ? d.scale : 1.0;
@@ -1152,6 +1158,7 @@ __global__ void __launch_bounds__(kRowThreads, rows_min_blocks<DOT>())
 k_hop1_rows(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb, R bc,
             SpinorView<R> dotv, double2* partials, const int* done, const SolverDev* __restrict__ ds,
             ScalarStep step) {
+    dep_sync();
     if (done != nullptr && *done) return;
     cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv)};
     if (DOT) {
@@ -1164,6 +1171,7 @@ template <typename R, bool DOT, int NT = kThreads, int MB = hop_min_blocks<R>()>
 __global__ void __launch_bounds__(NT, MB)
 k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb, R bc,
        SpinorView<R> dotv, double2* partials, const int* done, const SolverDev* __restrict__ ds, ScalarStep step) {
+    dep_sync();
     if (done != nullptr && *done) return;
     const int s = blockIdx.x * NT + threadIdx.x;
     cx<R> dres[1] = {czero<R>()};
@@ -1331,6 +1339,7 @@ k_gather(const SolverDev* __restrict__ ds) {
 
 // pass 2: advance the outer-iteration counter
 __global__ void k_advance(const SolverDev* __restrict__ ds) {
+    dep_sync();
     DevState* S = ds[blockIdx.x].st;
     if (S->m < S->n_outer) S->m += 1;
 }

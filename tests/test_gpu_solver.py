@@ -294,3 +294,34 @@ def test_error_paths_return_status(precision):
     r = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, precision=precision,
                     mode="pseudo" if precision == "mixed_df" else "double")
     assert r.stats["status"] == 0
+
+
+@pytest.mark.parametrize("mode,precision,graph", [("pseudo", "mixed_df", True), ("pseudo", "mixed_df", False),
+                                                  ("double", "f32", True), ("single", "f64", False)])
+def test_launch_overlap_is_bit_identical(mode, precision, graph):
+    """Kernels of an outer iteration launched with programmatic stream
+    serialization (the default) give the same bits as plain stream order, on
+    the 16^3 x 32 lattice (1064 blocks per sweep, so a kernel reading before
+    its predecessor finished would show)."""
+    import torch
+    w = inputs.make_workload("wilson_16x16x16x32")
+    stream = torch.cuda.Stream()
+    ctx = fa.Context(w["dims"], stream)
+    ctx.set_gauge(to_dev(w["U"]))
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wilson_16x16x16x32.json")))
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], g["scale_c"])
+    ctx.set_poles(*fa.neuberger_poles(w["ns"]))
+    with torch.cuda.stream(stream):
+        b = to_dev(w["b"])
+    stream.synchronize()
+    kw = dict(ell=2, tol=1e-9, mode=mode, precision=precision, graph=graph, max_outer=400)
+    r0 = ctx.apply_f(b, overlap=False, **kw)
+    y0 = to_host(r0.y)
+    for _ in range(2):
+        r1 = ctx.apply_f(b, **kw)
+        stream.synchronize()
+        assert np.array_equal(to_host(r1.y), y0)
+        assert r1.stats["outer_iters"] == r0.stats["outer_iters"]
+    assert r0.stats["status"] == 0
