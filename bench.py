@@ -51,7 +51,10 @@ def parse():
     p.add_argument("--impl", default="fapath", choices=["fapath", "reference"])
     p.add_argument("--workload", default="wilson_16x16x16x32")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--switch-resid", type=float, default=0.0)
+    p.add_argument("--switch-resid", type=float, default=-1.0,
+                   help="head/tail switch threshold of the mixed forms; < 0: 0.08/l^2 (on 16^3 x 32, "
+                        "l = 2 the fastest threshold whose error floor stays below half of 1e-8); "
+                        "0: the library default 0.04/l^2")
     p.add_argument("--quick", action="store_true",
                    help="headline solve only at tol 1e-9 (no comparisons, e2e or CPU baseline)")
     p.add_argument("--hop-only", action="store_true",
@@ -422,6 +425,8 @@ def main():
     def err(y):
         return (torch.linalg.vector_norm(y - yref) / yref_norm).item()
 
+    if args.switch_resid < 0:
+        args.switch_resid = 0.08 / ell ** 2
     variants = {
         "pseudo_mixed": dict(mode="pseudo", precision=args.head, switch_resid=args.switch_resid, graph=True,
                              store_gb=args.store_gb),
@@ -601,6 +606,7 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": config_of(args.workload, w),
         "variants": other,
+        "switch_resid": args.switch_resid,
         "speedup_vs_single_f64": other["single_f64"]["ms"] / ms_step,
         "speedup_vs_double_f64": other["double_f64"]["ms"] / ms_step,
         "roofline": dominant,
