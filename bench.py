@@ -146,9 +146,13 @@ def oracle_sample(w, c, outer=1):
     of one outer iteration of either pass of the oracle's double-pass form)."""
     from oracle import dirac, msbicgstab as ms
     op = dirac.Operator(w["U"], w["mass"], w["mu"], c, w["t_bc"])
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     ms.seed_recurrence(op.A, w["b"], w["ell"], outer)
-    return time.perf_counter() - t0
+    t, cpu = time.perf_counter() - t0, time.process_time() - c0
+    # threads actually used: process CPU time over wall time (numpy's stacked
+    # 3x3 products and elementwise loops run on one thread)
+    oracle_sample.threads = max(1, round(cpu / t))
+    return t
 
 
 def golden_outer_iters(name, tol=1e-9):
@@ -172,11 +176,12 @@ def cpu_baseline(w, c, outer_ref, outer=2, ref_tol=None):
     t = oracle_sample(w, c, outer)
     per_solve_ms = t / outer * 2 * outer_ref * 1e3
     at = f" (the oracle's own count at tol {ref_tol:g})" if ref_tol else ""
-    return {"value": per_solve_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+    return {"value": per_solve_ms, "unit": "ms", "cores": oracle_sample.threads, "kind": "oracle",
             "sample": f"{outer} outer iterations of the FP64 numpy oracle's BiCGstab({w['ell']}) "
                       f"recurrence on {'x'.join(map(str, w['dims']))} ({t:.1f} s), scaled by "
                       f"2 x {outer_ref} outer iterations{at} (pass 1 + pass 2 of the double-pass form); "
-                      f"numpy elementwise, 1 thread of {os.cpu_count()} host cores"}
+                      f"numpy, {oracle_sample.threads} thread(s) by CPU time / wall time, of "
+                      f"{os.cpu_count()} host cores"}
 
 
 def run_reference(args, ws, rank):
@@ -200,7 +205,7 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args.workload, w),
-        "cpu_baseline": {"value": per_solve, "unit": "ms", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": per_solve, "unit": "ms", "cores": oracle_sample.threads, "kind": "oracle",
                          "sample": f"each step: 1 outer iteration of the FP64 numpy oracle's "
                                    f"BiCGstab({w['ell']}) recurrence, scaled by 2 x {outer_ref} outer "
                                    f"iterations (both passes of the oracle's double-pass solve; the "
@@ -592,11 +597,13 @@ def main():
               "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal)",
               "algorithmic_instructions_per_launch": hopdf_instr, "mean_launch_ms": hopdf_ms,
               "launches_timed": hopdf_n, "total_ms": hopdf_ms * hopdf_n}
-    # DRAM traffic per launch from one ncu capture of the same kernels on this
-    # lattice (cold caches): dram__bytes_read.sum + dram__bytes_write.sum
+    # DRAM traffic per launch from one ncu capture of the same kernels in the
+    # timed solve on this lattice (dram__bytes_read.sum + dram__bytes_write.sum,
+    # 16 FP32 and 48 double-float sweeps): the mean over the sweeps without and
+    # with the inner product and seed step, in the solve's 5 : 3 proportion
     if V == 16 * 16 * 16 * 32:
-        roof32["traffic"] = 37.775e6 + 0.106e6
-        roofdf["traffic"] = 102.586e6 + 10.553e6
+        roof32["traffic"] = (5 * (37.776e6 + 0.001e6) + 3 * (50.415e6 + 0.029e6)) / 8
+        roofdf["traffic"] = (5 * (102.530e6 + 7.053e6) + 3 * (128.135e6 + 10.071e6)) / 8
     roofs = [roof32, roof64, roofdf]
     dominant = max(roofs, key=lambda r: r["total_ms"])
 
