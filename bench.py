@@ -507,9 +507,11 @@ def main():
     clk = clocks.stop()
     torch.cuda.synchronize()
     ms_step = max_over_ranks(statistics.mean(head_ms), dist, "cuda")
-    hop32_ms, hop32_n = ctx.hop_timing("f32")
+    hop32_ms, hop32_n = ctx.hop_timing("f32", dot=False)      # k_hop1<float, false>
+    hop32d_ms, hop32d_n = ctx.hop_timing("f32", dot=True)     # k_hop1<float, true>
     hop64_ms, hop64_n = ctx.hop_timing("f64")
-    hopdf_ms, hopdf_n = ctx.hop_timing("df")
+    hopdf_ms, hopdf_n = ctx.hop_timing("df", dot=False)       # k_hop1_rows<df, false>
+    hopdfd_ms, hopdfd_n = ctx.hop_timing("df", dot=True)      # k_hop1_rows<df, true>
 
     # comparison variants (fewer steps)
     other = {}
@@ -531,7 +533,8 @@ def main():
 
     if args.quick:
         print(json.dumps({"mode": "quick", "ms_per_solve": ms_step, "variant": other["pseudo_mixed"],
-                          "hop_f32_ms": hop32_ms, "hop_f64_ms": hop64_ms, "hop_df_ms": hopdf_ms,
+                          "hop_f32_ms": hop32_ms, "hop_f32_dot_ms": hop32d_ms, "hop_f64_ms": hop64_ms,
+                          "hop_df_ms": hopdf_ms, "hop_df_dot_ms": hopdfd_ms,
                           "hop_f32_gbs": 384.0 * V / (hop32_ms * 1e-3) / 1e9 if hop32_ms else None,
                           "launches_per_solve": head_launches // max(1, args.steps), "clocks": clk}),
               flush=True)
@@ -556,55 +559,56 @@ def main():
             e2e_ms.append((t1 - t0) * 1e3)
     e2e_err = float(np.linalg.norm(y_pin.numpy() - yref.cpu().numpy()) / yref_norm)
 
-    # rooflines of the two hop kernels; the one with more device time in the
-    # timed solves is reported as "roofline".
-    #   FP32 hop: HBM-bound, 96 B in + 96 B out + 4 x 48 B links = 384 B/site.
-    #   FP64 hop: FP64-ALU-bound on GB300; 1704 FP64 flops/site counted from the
+    # rooflines of the sweep kernels, each template instance on its own (the
+    # plain sweep and the sweep that also forms <rt, out> and runs a seed step
+    # are different kernels with different bytes); the one with the most device
+    # time in the timed solves is reported as "roofline".
+    #   FP32 sweep: HBM-bound, 96 B in + 96 B out + 4 x 48 B links = 384 B/site;
+    #   with the inner product + 96 B of rt = 480 B/site.
+    #   FP64 sweep: FP64-ALU-bound on GB300; 1704 FP64 flops/site counted from the
     #   kernel source (8 hops x (24 add projection + 12 mul + 60 fma link product
     #   + 48 add reconstruction) + 12 time-weight mul x 2 + 24 mul + 24 fma
     #   centre term; fma = 2 flops), against the nominal 1.25 TFLOP/s FP64.
+    #   double-float sweep (row split, shared projection, compensated arithmetic):
+    #   bound by FP32 issue; 11,650 thread instructions per site, the ncu
+    #   instruction count of one plain 16^3 x 32 launch (smsp__inst_executed x 32
+    #   / V), against 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3 T instructions/s.
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6800.0, "fallback"
     if os.path.exists(peaks_path):
         with open(peaks_path) as f:
             peak, peak_src = float(json.load(f)["hbm_gbs"]), "measured"
-    hop_bytes = 384.0 * V
-    achieved = hop_bytes / (hop32_ms * 1e-3) / 1e9 if hop32_ms > 0 else None
-    hop64_flops = 1704.0 * V
-    hop64_tflops = hop64_flops / (hop64_ms * 1e-3) / 1e12 if hop64_ms > 0 else None
-    over = "the instrumented repeat of the timed steps (direct launches, CUDA events around each hop launch)"
-    roof32 = {"kernel": "k_hop1<float> (one D_w sweep, FP32 12-real links; 128-thread blocks, 7/SM)", "bound": "hbm",
-              "measured_over": over,
-              "achieved": achieved, "peak": peak, "unit": "GB/s",
-              "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": peak_src,
-              "algorithmic_bytes_per_launch": hop_bytes, "mean_launch_ms": hop32_ms, "launches_timed": hop32_n,
-              "total_ms": hop32_ms * hop32_n}
-    roof64 = {"kernel": "k_hop1<double> (one D_w sweep, FP64, head of the mixed solve)", "bound": "alu",
-              "measured_over": over,
-              "achieved": hop64_tflops, "peak": 1.25, "unit": "TFLOP/s",
-              "frac": (hop64_tflops / 1.25) if hop64_tflops else None, "traffic": None,
-              "peak_source": "nominal GB300 FP64 (no measured FP64 peak)", "algorithmic_flops_per_launch": hop64_flops,
-              "mean_launch_ms": hop64_ms, "launches_timed": hop64_n, "total_ms": hop64_ms * hop64_n}
-    #   double-float hop (row split, shared projection, compensated arithmetic):
-    #   bound by FP32 issue; 11,650 thread instructions per site, the ncu
-    #   instruction count of one 16^3 x 32 launch (smsp__inst_executed x 32 / V),
-    #   against 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3 T instructions/s.
-    hopdf_instr = 11650.0 * V
-    hopdf_t = hopdf_instr / (hopdf_ms * 1e-3) / 1e12 if hopdf_ms > 0 else None
-    roofdf = {"kernel": "k_hop1_rows<df> (one D_w sweep, double-float head, row split)", "bound": "alu",
-              "measured_over": over, "achieved": hopdf_t, "peak": 40.3, "unit": "T FP32-instructions/s",
-              "frac": (hopdf_t / 40.3) if hopdf_t else None, "traffic": None,
-              "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal)",
-              "algorithmic_instructions_per_launch": hopdf_instr, "mean_launch_ms": hopdf_ms,
-              "launches_timed": hopdf_n, "total_ms": hopdf_ms * hopdf_n}
+    over = "the instrumented repeat of the timed steps (direct launches, CUDA events around each sweep launch)"
+
+    def roof(kernel, bound, per_launch, ms, n, unit, pk, pk_src, what, scale):
+        ach = per_launch / (ms * 1e-3) / scale if ms > 0 else None
+        return {"kernel": kernel, "bound": bound, "measured_over": over, "achieved": ach, "peak": pk,
+                "unit": unit, "frac": (ach / pk) if ach else None, "traffic": None, "peak_source": pk_src,
+                what: per_launch, "mean_launch_ms": ms, "launches_timed": n, "total_ms": ms * n}
+
+    roof32 = roof("k_hop1<float, false> (one D_w sweep, FP32 12-real links; 128-thread blocks, 7/SM)", "hbm",
+                  384.0 * V, hop32_ms, hop32_n, "GB/s", peak, peak_src, "algorithmic_bytes_per_launch", 1e9)
+    roof32d = roof("k_hop1<float, true> (D_w sweep + <rt, out> + seed step in the last block)", "hbm",
+                   480.0 * V, hop32d_ms, hop32d_n, "GB/s", peak, peak_src, "algorithmic_bytes_per_launch", 1e9)
+    roof64 = roof("k_hop1<double> (one D_w sweep, FP64; both instances)", "alu", 1704.0 * V, hop64_ms, hop64_n,
+                  "TFLOP/s", 1.25, "nominal GB300 FP64 (no measured FP64 peak)", "algorithmic_flops_per_launch",
+                  1e12)
+    nom = "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal)"
+    roofdf = roof("k_hop1_rows<df, false> (one D_w sweep, double-float head, row split)", "alu", 11650.0 * V,
+                  hopdf_ms, hopdf_n, "T FP32-instructions/s", 40.3, nom, "algorithmic_instructions_per_launch", 1e12)
+    roofdfd = roof("k_hop1_rows<df, true> (sweep + <rt, out> + seed step; the sweep's instructions only)", "alu",
+                   11650.0 * V, hopdfd_ms, hopdfd_n, "T FP32-instructions/s", 40.3, nom,
+                   "algorithmic_instructions_per_launch", 1e12)
+    achieved = roof32["achieved"]
     # DRAM traffic per launch from one ncu capture of the same kernels in the
-    # timed solve on this lattice (dram__bytes_read.sum + dram__bytes_write.sum,
-    # 16 FP32 and 48 double-float sweeps): the mean over the sweeps without and
-    # with the inner product and seed step, in the solve's 5 : 3 proportion
+    # timed solve on this lattice (dram__bytes_read.sum + dram__bytes_write.sum;
+    # means over 10 + 6 FP32 and 30 + 18 double-float launches)
     if V == 16 * 16 * 16 * 32:
-        roof32["traffic"] = (5 * (37.776e6 + 0.001e6) + 3 * (50.415e6 + 0.029e6)) / 8
-        roofdf["traffic"] = (5 * (102.530e6 + 7.053e6) + 3 * (128.135e6 + 10.071e6)) / 8
-    roofs = [roof32, roof64, roofdf]
+        roof32["traffic"] = 37.776e6 + 0.001e6
+        roof32d["traffic"] = 50.415e6 + 0.029e6
+        roofdf["traffic"] = 102.530e6 + 7.053e6
+        roofdfd["traffic"] = 128.135e6 + 10.071e6
+    roofs = [roof32, roof32d, roof64, roofdf, roofdfd]
     dominant = max(roofs, key=lambda r: r["total_ms"])
 
     line = {
@@ -618,8 +622,10 @@ def main():
         "speedup_vs_double_f64": other["double_f64"]["ms"] / ms_step,
         "roofline": dominant,
         "roofline_hop_f32": roof32,
+        "roofline_hop_f32_dot": roof32d,
         "roofline_hop_f64": roof64,
         "roofline_hop_df": roofdf,
+        "roofline_hop_df_dot": roofdfd,
         "stencil_gbs": achieved,
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": int(b_pin.numel() * 16),
                 "d2h_bytes_per_step": int(y_pin.numel() * 16), "rel_err": e2e_err},

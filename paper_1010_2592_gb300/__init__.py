@@ -33,7 +33,7 @@ EXPORTS = (
     "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
     "fa_set_poles", "fa_neuberger_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
     "fa_apply_f", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
-    "fa_hop_timing_reset", "fa_status_string", "fa_last_error", "fa_version",
+    "fa_hop_timing_split", "fa_hop_timing_reset", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune",
 )
@@ -112,6 +112,7 @@ def load_library(path=LIB_PATH):
         "fa_sync": (I, [P]),
         "fa_launch_count": (LL, [P]),
         "fa_hop_timing": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
+        "fa_hop_timing_split": (I, [P, I, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_reset": (I, [P]),
         "fa_set_hop_shape": (I, [P, I]),
         "fa_get_hop_shape": (I, [P]),
@@ -330,11 +331,14 @@ class Context:
     def launch_count(self):
         return int(self.lib.fa_launch_count(self.h))
 
-    def hop_timing(self, precision="f32"):
+    def hop_timing(self, precision="f32", dot=None):
+        """Mean event-timed ms per sweep and the count; dot: None (all sweeps),
+        False (plain sweeps), True (sweeps that also form an inner product)."""
         ms = ctypes.c_double()
         n = ctypes.c_longlong()
-        _check(self.lib.fa_hop_timing(self.h, _PREC[precision], ctypes.byref(ms), ctypes.byref(n)),
-               "fa_hop_timing")
+        with_dot = -1 if dot is None else int(bool(dot))
+        _check(self.lib.fa_hop_timing_split(self.h, _PREC[precision], with_dot, ctypes.byref(ms),
+                                            ctypes.byref(n)), "fa_hop_timing_split")
         return ms.value, n.value
 
     def hop_timing_reset(self):

@@ -330,19 +330,33 @@ int fa_sync(fa_ctx* c) {
 
 long long fa_launch_count(const fa_ctx* c) { return c ? c->launches : -1; }
 
-int fa_hop_timing(const fa_ctx* c, int precision, double* mean_ms, long long* count) {
-    if (!c || !mean_ms || !count || (precision != FA_F64 && precision != FA_F32 && precision != FA_DF))
+int fa_hop_timing_split(const fa_ctx* c, int precision, int with_dot, double* mean_ms, long long* count) {
+    if (!c || !mean_ms || !count || (precision != FA_F64 && precision != FA_F32 && precision != FA_DF) ||
+        with_dot < -1 || with_dot > 1)
         return FA_EINVAL;
     const int k = precision == FA_F64 ? 0 : (precision == FA_F32 ? 1 : 2);
-    *count = c->hop_count[k];
-    *mean_ms = c->hop_count[k] ? c->hop_ms[k] / (double)c->hop_count[k] : 0.0;
+    double ms = 0.0;
+    long long n = 0;
+    for (int d = 0; d < 2; ++d) {
+        if (with_dot >= 0 && d != with_dot) continue;
+        ms += c->hop_ms[k + 3 * d];
+        n += c->hop_count[k + 3 * d];
+    }
+    *count = n;
+    *mean_ms = n ? ms / (double)n : 0.0;
     return FA_OK;
+}
+
+int fa_hop_timing(const fa_ctx* c, int precision, double* mean_ms, long long* count) {
+    return fa_hop_timing_split(c, precision, -1, mean_ms, count);
 }
 
 int fa_hop_timing_reset(fa_ctx* c) {
     if (!c) return FA_EINVAL;
-    c->hop_ms[0] = c->hop_ms[1] = c->hop_ms[2] = 0.0;
-    c->hop_count[0] = c->hop_count[1] = c->hop_count[2] = 0;
+    for (int k = 0; k < 6; ++k) {
+        c->hop_ms[k] = 0.0;
+        c->hop_count[k] = 0;
+    }
     return FA_OK;
 }
 

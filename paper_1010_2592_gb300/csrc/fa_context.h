@@ -89,14 +89,17 @@ struct fa_ctx {
     size_t pinned_bytes = 0;
 
     long long launches = 0;
-    // hop-kernel timing (index 0: FP64, 1: FP32)
-    double hop_ms[3] = {0.0, 0.0, 0.0};   // FP64, FP32, double-float
-    long long hop_count[3] = {0, 0, 0};
+    // hop-kernel timing: index FP64 0, FP32 1, double-float 2; + 3 for the
+    // sweeps that also form <dot_with, out> (and run a scalar step in a solve)
+    double hop_ms[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    long long hop_count[6] = {0, 0, 0, 0, 0, 0};
     bool hop_timing = false;
     int hop_shape = 0;                   // FP32 sweep launch shape (fa_hop_shape; 0: automatic)
     std::vector<cudaEvent_t> hop_ev;     // start/stop pairs, reused across solves
-    std::vector<int> hop_ev_kind;        // precision index of each recorded pair
+    std::vector<int> hop_ev_kind;        // timing index of each recorded pair
     size_t hop_ev_used = 0;              // pairs recorded since the last collection
+    std::vector<int> hop_ev_outer;       // pass-1 outer iteration of each pair (-1: other)
+    int hop_outer = -1;                  // outer iteration being enqueued in pass 1
 };
 
 namespace fa {

@@ -42,7 +42,9 @@ static void hop_timing_begin(fa_ctx* c, int kind) {
         c->hop_ev.push_back(e);
     }
     if (c->hop_ev_kind.size() < c->hop_ev_used + 1) c->hop_ev_kind.resize(c->hop_ev_used + 1);
+    if (c->hop_ev_outer.size() < c->hop_ev_used + 1) c->hop_ev_outer.resize(c->hop_ev_used + 1);
     c->hop_ev_kind[c->hop_ev_used] = kind;
+    c->hop_ev_outer[c->hop_ev_used] = c->hop_outer;
     cudaEventRecord(c->hop_ev[2 * c->hop_ev_used], c->stream);
 }
 static void hop_timing_end(fa_ctx* c) {
@@ -50,9 +52,12 @@ static void hop_timing_end(fa_ctx* c) {
     cudaEventRecord(c->hop_ev[2 * c->hop_ev_used + 1], c->stream);
     c->hop_ev_used++;
 }
-// after a stream synchronisation: fold the recorded pairs into the means
-static void hop_timing_collect(fa_ctx* c) {
+// after a stream synchronisation: fold the recorded pairs into the means.
+// Pass-1 outer iterations from `m_run` on were enqueued ahead of the host's
+// convergence poll and returned at once (the done flag): not counted.
+static void hop_timing_collect(fa_ctx* c, int m_run = 1 << 30) {
     for (size_t k = 0; k < c->hop_ev_used; ++k) {
+        if (c->hop_ev_outer[k] >= m_run) continue;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->hop_ev[2 * k], c->hop_ev[2 * k + 1]) == cudaSuccess) {
             c->hop_ms[c->hop_ev_kind[k]] += ms;
@@ -65,7 +70,7 @@ static void hop_timing_collect(fa_ctx* c) {
 int hop_f64(fa_ctx* c, const double2* in, double2* out, double scale, bool g5in, bool g5out, bool dagger_mu,
             const double2* dot_with, double2* partials, const int* done) {
     const double mu = dagger_mu ? -c->mu : c->mu;
-    hop_timing_begin(c, 0);
+    hop_timing_begin(c, 0 + (dot_with ? 3 : 0));
     int rc = launch_hop_f64(c->g, links64_of(c), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu),
                             c->t_bc, scale, g5in, g5out, dot_with, partials, done, c->stream);
     hop_timing_end(c);
@@ -77,7 +82,7 @@ int hop_f64(fa_ctx* c, const double2* in, double2* out, double scale, bool g5in,
 int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, bool g5out, bool dagger_mu,
             const float4* dot_with, double2* partials, const int* done) {
     const double mu = dagger_mu ? -c->mu : c->mu;
-    hop_timing_begin(c, 1);
+    hop_timing_begin(c, 1 + (dot_with ? 3 : 0));
     int rc = launch_hop_f32(c->g, links32_of(c), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu),
                             c->t_bc, scale, g5in, g5out, dot_with, partials, done, c->stream, c->hop_shape);
     hop_timing_end(c);
@@ -89,7 +94,7 @@ int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, b
 int hop_df(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, bool g5out, bool dagger_mu,
            const float4* dot_with, double2* partials, const int* done) {
     const double mu = dagger_mu ? -c->mu : c->mu;
-    hop_timing_begin(c, 2);
+    hop_timing_begin(c, 2 + (dot_with ? 3 : 0));
     int rc = launch_hop_df(c->g, linksdf_of(c), in, out, 4.0 + c->mass, std::exp(mu), std::exp(-mu), c->t_bc, scale,
                            g5in, g5out, dot_with, partials, done, c->stream);
     hop_timing_end(c);
@@ -312,7 +317,7 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     };
     const ScalarStep none{STEP_NONE, 0};
     auto hop = [&](int in_sel, int in_j, int out_sel, int out_j, int second, bool dot, ScalarStep step) -> int {
-        if (timing) hop_timing_begin(c, kind);
+        if (timing) hop_timing_begin(c, kind + (dot ? 3 : 0));
         if (n == 1) {
             const T* rt = rp_of<R>() != RP32 ? (const T*)(const void*)h0.rt64 : (const T*)(const void*)h0.rt32;
             const int* done = pass2 ? nullptr : &h0.st->done;
@@ -642,6 +647,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     cudaStream_t st = c0->stream;
     const bool timing = (p->flags & 1) != 0;
     c0->hop_timing = (p->flags & 2) != 0;
+    c0->hop_outer = -1;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (timing)
         for (auto& e : ev) FA_CUDA(cudaEventCreate(&e), "event");
@@ -749,6 +755,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     // head of FA_MIXED / FA_MIXED_DF (one system): one outer iteration at a time until the switch
     while (head && enq < Lo.max_outer) {
         FA_TRY(before_outer(enq, rp));
+        c0->hop_outer = enq;
         FA_TRY(enqueue_outer_any(B, rp, false, single, true, reliable_at(enq)));
         ++enq;
         FA_TRY(read_states(B, hs));
@@ -778,6 +785,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         while (!stop && enq < Lo.max_outer) {
             for (int i = 0; i < chunk && enq < Lo.max_outer; ++i, ++enq) {
                 rc = before_outer(enq, rp);
+                c0->hop_outer = enq;
                 if (rc == FA_OK) rc = enqueue_outer_any(B, rp, false, single, false, reliable_at(enq));
                 if (rc != FA_OK) break;
             }
@@ -798,6 +806,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         FA_TRY(rc);
         FA_TRY(read_states(B, hs));
     }
+    c0->hop_outer = -1;
     if (timing) cudaEventRecord(ev[1], st);
     std::vector<int> status(n);
     int M = 0, rc_all = FA_OK;
@@ -879,7 +888,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         }
     }
     FA_CUDA(cudaStreamSynchronize(st), "sync solve");
-    if (c0->hop_timing) hop_timing_collect(c0);
+    if (c0->hop_timing) hop_timing_collect(c0, M);
     c0->hop_timing = false;
 
     if (stats) {

@@ -325,3 +325,27 @@ def test_launch_overlap_is_bit_identical(mode, precision, graph):
         assert np.array_equal(to_host(r1.y), y0)
         assert r1.stats["outer_iters"] == r0.stats["outer_iters"]
     assert r0.stats["status"] == 0
+
+
+def test_hop_timing_split_by_kernel():
+    """Event timing of the sweeps, split into the plain sweeps and the sweeps
+    that also form <rt, out>: the two counts add up to the total, each mean is
+    positive, and an invalid selector is rejected."""
+    import ctypes
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    ctx.hop_timing_reset()
+    ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, mode="pseudo", precision="f32", hop_timing=True)
+    ms_all, n_all = ctx.hop_timing("f32")
+    ms0, n0 = ctx.hop_timing("f32", dot=False)
+    ms1, n1 = ctx.hop_timing("f32", dot=True)
+    assert n0 > 0 and n1 > 0 and n0 + n1 == n_all
+    assert ms0 > 0 and ms1 > 0
+    assert abs(ms_all * n_all - (ms0 * n0 + ms1 * n1)) <= 1e-9 * ms_all * n_all
+    # per BiCG sub-step: two hops of A for u and two for r, one of each pair with
+    # the inner product except for the last sub-step's r (its product is in the Gram matrix)
+    r = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, mode="pseudo", precision="f32")
+    M = r.stats["outer_iters"]
+    assert n_all == 8 * M and n1 == 3 * M
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    assert ctx.lib.fa_hop_timing_split(ctx.h, fa.F32, 2, ctypes.byref(ms), ctypes.byref(n)) == fa.FA_EINVAL

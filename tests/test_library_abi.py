@@ -62,3 +62,5 @@ def test_invalid_arguments_rejected_before_any_device_call():
     assert lib.fa_neuberger_poles(65, None, None) == fa.FA_EINVAL
     assert lib.fa_destroy(None) == fa.FA_OK
     assert lib.fa_set_params(None, -1.8, 0.1, -1, 1.0) == fa.FA_EINVAL
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    assert lib.fa_hop_timing_split(None, fa.F32, 0, ctypes.byref(ms), ctypes.byref(n)) == fa.FA_EINVAL
