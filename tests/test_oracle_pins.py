@@ -306,3 +306,60 @@ def test_workload_c1_against_per_shift_gmres():
     y = ms.multishift_double(op.A, w["b"], sg, om, w["ell"], w["tol"])
     ystar = direct.pfe_per_shift(op.A, w["b"], om, sg, rtol=1e-13)
     assert rel(y, ystar) < 1e-9
+
+
+def _multishift_cg(A, b, sigma, tol, max_iter=5000):
+    """Textbook multi-shift CG for (A + sigma_s) x_s = b with A Hermitian
+    positive definite (Jegerlehner, hep-lat/9612014): one CG on A, and for
+    every shift the collinear residual r_s = zeta_s r with zeta_s from the
+    three-term recurrence of the CG residual polynomials at -sigma_s."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    ns = len(sigma)
+    x = [np.zeros_like(b) for _ in range(ns)]
+    p_s = [b.copy() for _ in range(ns)]
+    r, p = b.copy(), b.copy()
+    z_prev, z = np.ones(ns), np.ones(ns)
+    a_prev, b_prev = 1.0, 0.0
+    rr = np.vdot(r, r).real
+    bn = np.sqrt(rr)
+    live = np.ones(ns, dtype=bool)           # a shift stops once |zeta_s r| <= tol |b|
+    for _ in range(max_iter):
+        Ap = A(p)
+        a = rr / np.vdot(p, Ap).real
+        z_new = z.copy()
+        for s in np.flatnonzero(live):
+            z_new[s] = z[s] * z_prev[s] * a_prev / (a * b_prev * (z_prev[s] - z[s])
+                                                     + z_prev[s] * a_prev * (1.0 + sigma[s] * a))
+            x[s] = x[s] + (a * z_new[s] / z[s]) * p_s[s]
+        r = r - a * Ap
+        rr_new = np.vdot(r, r).real
+        bt = rr_new / rr
+        for s in np.flatnonzero(live):
+            p_s[s] = z_new[s] * r + bt * (z_new[s] / z[s]) ** 2 * p_s[s]
+        p = r + bt * p
+        z_prev, z = np.where(live, z, z_prev), z_new
+        a_prev, b_prev, rr = a, bt, rr_new
+        live &= np.sqrt(rr) * np.abs(z) > tol * bn
+        if not live.any():
+            return x
+    raise RuntimeError("multi-shift CG did not converge")
+
+
+@pytest.mark.parametrize("ell", [1, 2, 4])
+def test_mu0_multishift_cg_gives_the_same_sum(ell):
+    """At mu = 0, A = c (g5 D)^2 is Hermitian positive definite: textbook
+    multi-shift CG on it gives the same pole sum and the same x_s as the
+    oracle's single- and double-pass multi-shift BiCGstab(l)."""
+    U = inputs.su3_exp_gauge(TINY, 0.5, 61)
+    op0 = dirac.Operator(U, -1.8, 0.0)
+    c = scale.power_scale(op0.A, inputs.gaussian_spinor(TINY, 62), 100)
+    op = dirac.Operator(U, -1.8, 0.0, c)
+    b = inputs.gaussian_spinor(TINY, 63)
+    om, sg = poles.neuberger_poles(10)
+    x_cg = _multishift_cg(op.A, b, sg, 1e-13)
+    xs = ms.multishift_single(op.A, b, sg, ell, 1e-13)
+    for s in range(len(sg)):
+        assert rel(xs[s], x_cg[s]) < 1e-10, s
+    y_cg = ms.pfe_from_shifts(x_cg, om)
+    assert rel(ms.pfe_from_shifts(xs, om), y_cg) < 1e-10
+    assert rel(ms.multishift_double(op.A, b, sg, om, ell, 1e-13), y_cg) < 1e-10
