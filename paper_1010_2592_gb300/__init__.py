@@ -33,7 +33,7 @@ EXPORTS = (
     "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
     "fa_set_poles", "fa_neuberger_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
     "fa_apply_f", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
-    "fa_hop_timing_split", "fa_hop_timing_reset", "fa_status_string", "fa_last_error", "fa_version",
+    "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune",
 )
@@ -114,6 +114,7 @@ def load_library(path=LIB_PATH):
         "fa_hop_timing": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_split": (I, [P, I, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_reset": (I, [P]),
+        "fa_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
         "fa_set_hop_shape": (I, [P, I]),
         "fa_get_hop_shape": (I, [P]),
         "fa_autotune": (I, [P, I, ctypes.POINTER(D)]),
@@ -340,6 +341,12 @@ class Context:
         _check(self.lib.fa_hop_timing_split(self.h, _PREC[precision], with_dot, ctypes.byref(ms),
                                             ctypes.byref(n)), "fa_hop_timing_split")
         return ms.value, n.value
+
+    def device_bytes(self):
+        """(lattice-sized bytes, scalar bytes) of device memory the context owns."""
+        f, sc = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+        _check(self.lib.fa_device_bytes(self.h, ctypes.byref(f), ctypes.byref(sc)), "fa_device_bytes")
+        return f.value, sc.value
 
     def hop_timing_reset(self):
         _check(self.lib.fa_hop_timing_reset(self.h), "fa_hop_timing_reset")

@@ -330,6 +330,25 @@ int fa_sync(fa_ctx* c) {
 
 long long fa_launch_count(const fa_ctx* c) { return c ? c->launches : -1; }
 
+int fa_device_bytes(const fa_ctx* c, unsigned long long* field_bytes, unsigned long long* scalar_bytes) {
+    if (!c || !field_bytes || !scalar_bytes) return FA_EINVAL;
+    // lattice-sized buffers: links, spinors, stores, staging, reduction partials
+    const fa::DevBuf* field[] = {&c->links64, &c->links32, &c->linksdf, &c->io64a, &c->io64b, &c->io32a,
+                                 &c->io32b, &c->tmp64, &c->tmp32, &c->partials, &c->r64, &c->u64, &c->rt64,
+                                 &c->r32, &c->u32, &c->rt32, &c->y64, &c->xs64, &c->us64, &c->bhost_dev,
+                                 &c->yhost_dev, &c->gx, &c->gpart, &c->store64, &c->store32, &c->snap64,
+                                 &c->snap32, &c->xrel, &c->brel, &c->snapx};
+    // scalars: solver state, shifts, records, pass-2 weights, batch descriptors
+    const fa::DevBuf* scal[] = {&c->state, &c->shiftbuf, &c->rec, &c->prec, &c->coef, &c->cs, &c->coef4,
+                                &c->descbuf, &c->flagbuf};
+    unsigned long long f = 0, s = 0;
+    for (const fa::DevBuf* b : field) f += b->bytes;
+    for (const fa::DevBuf* b : scal) s += b->bytes;
+    *field_bytes = f;
+    *scalar_bytes = s;
+    return FA_OK;
+}
+
 int fa_hop_timing_split(const fa_ctx* c, int precision, int with_dot, double* mean_ms, long long* count) {
     if (!c || !mean_ms || !count || (precision != FA_F64 && precision != FA_F32 && precision != FA_DF) ||
         with_dot < -1 || with_dot > 1)

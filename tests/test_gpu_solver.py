@@ -349,3 +349,27 @@ def test_hop_timing_split_by_kernel():
     assert n_all == 8 * M and n1 == 3 * M
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     assert ctx.lib.fa_hop_timing_split(ctx.h, fa.F32, 2, ctypes.byref(ms), ctypes.byref(n)) == fa.FA_EINVAL
+
+
+def test_two_pass_memory_is_independent_of_the_number_of_poles():
+    """Sec. 2: the double-pass and pseudo-double-pass forms keep the seed
+    vectors only, whatever N_s; the single-pass form adds N_s (l + 2) FP64
+    shift vectors (x_s, u^s_0..u^s_l).  Scalar records grow with N_s alone."""
+    w = workload_case(C1)
+    V = int(np.prod(w["dims"]))
+    spinor64 = 12 * V * 16
+    b = to_dev(w["b"])
+    got = {}
+    for ns in (4, 64):
+        om, sg = fa.neuberger_poles(ns)
+        for mode in ("double", "pseudo", "single"):
+            ctx = make_context(w["dims"], w["U"], w["mass"], w["mu"], w["c"], w["t_bc"], om, sg)
+            r = ctx.apply_f(b, ell=2, tol=1e-10, mode=mode, precision="f64", max_outer=300)
+            assert r.stats["status"] == 0
+            got[mode, ns] = ctx.device_bytes()
+    assert got["double", 4][0] == got["double", 64][0]
+    assert got["pseudo", 4][0] == got["pseudo", 64][0]
+    assert got["single", 64][0] - got["single", 4][0] == (64 - 4) * (2 + 2) * spinor64
+    assert got["single", 4][0] - got["double", 4][0] == 4 * (2 + 2) * spinor64
+    for mode in ("double", "pseudo", "single"):
+        assert got[mode, 64][1] > got[mode, 4][1]
