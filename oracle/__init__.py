@@ -13,6 +13,7 @@ Modules
                double-pass form of Sec. 2 (Eqs. 2-3)
     direct     y* by per-shift library solves, dense LU and eigendecomposition
     scale      power-iteration estimate of the largest eigenvalue of A
+    overlap    sign(gamma_5 D_w) b and the overlap operator D_ov(mu) b of Sec. 1
 
 Parity status: every function is pinned by the `-m "not gpu"` tests except
 the closed-form double-pass coefficients of Sec. 4 (A_mj, B_m^s, D, E, F, G,

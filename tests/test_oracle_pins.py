@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import inputs
-from oracle import dirac, direct, msbicgstab as ms, poles, scale
+from oracle import dirac, direct, msbicgstab as ms, overlap, poles, scale
 from closed_forms import (GAMMA_DR, free_A_eigenvalues, free_dw, free_matfunc,
                           gauge_rotate_spinor, neuberger_eps)
 
@@ -363,3 +363,51 @@ def test_mu0_multishift_cg_gives_the_same_sum(ell):
     y_cg = ms.pfe_from_shifts(x_cg, om)
     assert rel(ms.pfe_from_shifts(xs, om), y_cg) < 1e-10
     assert rel(ms.multishift_double(op.A, b, sg, om, ell, 1e-13), y_cg) < 1e-10
+
+
+def _overlap_problem(mu):
+    """Tiny lattice, Wilson mass 1: the spectrum of A = c H^2 stays away from 0,
+    so 32 Neuberger poles approximate z^{-1/2} on it to better than 1e-11."""
+    U = inputs.su3_exp_gauge(TINY, 0.5, 81)
+    op0 = dirac.Operator(U, 1.0, mu)
+    c = scale.power_scale(op0.A, inputs.gaussian_spinor(TINY, 82), 200)
+    return dirac.Operator(U, 1.0, mu, c), inputs.gaussian_spinor(TINY, 83)
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.2])
+def test_sign_and_overlap_against_dense_exact_sign(mu):
+    """Sec. 1: sign(H) b = sqrt(c) H f(A) b (sign z = z / sqrt(z^2)) against the
+    exact matrix sign V sign(Re lambda) V^{-1} b of the dense H = g5 D_w(mu);
+    D_ov b = b + g5 sign(H) b; sign(H)^2 b = b."""
+    op, b = _overlap_problem(mu)
+    om, sg = poles.neuberger_poles(32)
+    y = ms.multishift_double(op.A, b, sg, om, 2, 1e-13)
+    S = overlap.sign_dense(overlap.dense_H(op))
+    s_exact = (S @ b.reshape(-1)).reshape(b.shape)
+    s = overlap.sign_apply(op, y)
+    assert rel(s, s_exact) < 1e-10
+    assert rel(overlap.overlap_apply(op, b, y), b + dirac.gamma5(s_exact)) < 1e-10
+    y2 = ms.multishift_double(op.A, s, sg, om, 2, 1e-13)
+    assert rel(overlap.sign_apply(op, y2), b) < 1e-10
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.2])
+def test_overlap_ginsparg_wilson_relation(mu):
+    """D_ov = 1 + g5 sign(H) satisfies g5 D_ov + D_ov g5 = D_ov g5 D_ov, which
+    is sign(H)^2 = 1 written out (any mu), here through the pole form."""
+    op, b = _overlap_problem(mu)
+    om, sg = poles.neuberger_poles(32)
+
+    def D(v):
+        return overlap.overlap_apply(op, v, ms.multishift_double(op.A, v, sg, om, 2, 1e-13))
+
+    g5 = dirac.gamma5
+    lhs = g5(D(b)) + D(g5(b))
+    rhs = D(g5(D(b)))
+    assert rel(lhs, rhs) < 1e-10
+    # a control: 1 + sign(H) without the gamma_5 does not satisfy it
+
+    def Dx(v):
+        return v + overlap.sign_apply(op, ms.multishift_double(op.A, v, sg, om, 2, 1e-13))
+
+    assert rel(g5(Dx(b)) + Dx(g5(b)), Dx(g5(Dx(b)))) > 1e-3
