@@ -32,7 +32,7 @@ _MODE = {"single": SINGLE, "double": DOUBLE, "pseudo": PSEUDO, SINGLE: SINGLE, D
 EXPORTS = (
     "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
     "fa_set_poles", "fa_neuberger_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
-    "fa_apply_f", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
+    "fa_apply_f", "fa_apply_sign", "fa_apply_overlap", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
     "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune",
@@ -105,6 +105,8 @@ def load_library(path=LIB_PATH):
         "fa_apply_A_noalloc": (I, [P, P, P, I]),
         "fa_solve_multishift": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+        "fa_apply_sign": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+        "fa_apply_overlap": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f_host": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f_batched": (I, [P, I, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_grad": (I, [P, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P,
@@ -285,6 +287,24 @@ class Context:
         rc = self.lib.fa_apply_f(self.h, b.data_ptr(), y.data_ptr(), ctypes.byref(p), ctypes.byref(st))
         if check:
             _check(rc, "fa_apply_f")
+        return Result(y, st.as_dict())
+
+    def apply_sign(self, b, out=None, check=True, **kw):
+        """sign(g5 D_w(mu)) b = sqrt(c) g5 D_w f(A) b (Sec. 1); keywords as apply_f."""
+        return self._sign_call(self.lib.fa_apply_sign, "fa_apply_sign", b, out, check, kw)
+
+    def apply_overlap(self, b, out=None, check=True, **kw):
+        """D_ov(mu) b = b + g5 sign(g5 D_w(mu)) b (Sec. 1); keywords as apply_f."""
+        return self._sign_call(self.lib.fa_apply_overlap, "fa_apply_overlap", b, out, check, kw)
+
+    def _sign_call(self, fn, name, b, out, check, kw):
+        b = _spinor_check(b, self.spinor_shape, "b")
+        y = self.empty_spinor() if out is None else _spinor_check(out, self.spinor_shape, "out")
+        p = self.params(**kw)
+        st = SolverStats()
+        rc = fn(self.h, b.data_ptr(), y.data_ptr(), ctypes.byref(p), ctypes.byref(st))
+        if check:
+            _check(rc, name)
         return Result(y, st.as_dict())
 
     def apply_f_host(self, b, check=True, **kw):

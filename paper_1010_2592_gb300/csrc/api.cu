@@ -261,6 +261,17 @@ int fa_apply_f(fa_ctx* c, const double* b, double* y, const fa_solver_params* p,
     return solve(c, b, y, nullptr, p, stats);
 }
 
+int fa_apply_sign(fa_ctx* c, const double* b, double* out, const fa_solver_params* p, fa_solver_stats* stats) {
+    if (!c || !b || !out || !p || b == out) return FA_EINVAL;
+    return apply_sign(c, b, out, p, stats, false);
+}
+
+int fa_apply_overlap(fa_ctx* c, const double* b, double* out, const fa_solver_params* p,
+                     fa_solver_stats* stats) {
+    if (!c || !b || !out || !p || b == out) return FA_EINVAL;
+    return apply_sign(c, b, out, p, stats, true);
+}
+
 int fa_apply_f_batched(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y,
                        const fa_solver_params* p, fa_solver_stats* stats) {
     if (!ctxs || !b || !y || !p || n < 1 || n > 4096) return FA_EINVAL;

@@ -124,6 +124,8 @@ int solve(fa_ctx* c, const double* b_canon, double* y_canon, double* const* xs_c
 int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y_canon,
                 double* const* xs_canon, const fa_solver_params* p, fa_solver_stats* stats);
 int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out);
+int apply_sign(fa_ctx* c, const double* b, double* out, const fa_solver_params* p, fa_solver_stats* stats,
+               bool overlap);
 int grad(fa_ctx* c, const double* b, const double* eta, double* dLdU, double* dLdmu, double* L, double* dLdb,
          const fa_solver_params* p, fa_solver_stats* stats);
 }  // namespace fa

@@ -127,6 +127,14 @@ __global__ void k_scale_f64(int n, double2* v, const double* s) {
     v[idx] = make_double2(t.x * a, t.y * a);
 }
 
+// y += x over n double2 elements
+__global__ void k_add_f64(int n, const double2* __restrict__ x, double2* __restrict__ y) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;
+    if (idx >= n) return;
+    const double2 a = x[idx], t = y[idx];
+    y[idx] = make_double2(t.x + a.x, t.y + a.y);
+}
+
 // ------------------------------------------------------------------ workspace
 struct Layout {
     int L, ns, max_outer, V;
@@ -929,6 +937,36 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
 int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, const fa_solver_params* p,
           fa_solver_stats* stats) {
     return solve_batch(&c, 1, &b, y_canon ? &y_canon : nullptr, xs_canon, p, stats);
+}
+
+// ------------------------------------------------------------------ sign function, overlap operator
+// Sec. 1: D_ov(mu) = 1 + g5 sign(g5 D_w(mu)), sign z = z / sqrt(z^2).  With
+// A = c H^2, H = g5 D_w: sign(H) b = sqrt(c) H f(A) b, f(A) b the solver's y
+// (poles approximating z^{-1/2}); D_ov b = b + g5 sign(H) b = b + sqrt(c) D_w y.
+// One FP64 sweep on the solver's internal y after the solve.
+int apply_sign(fa_ctx* c, const double* b, double* out, const fa_solver_params* p, fa_solver_stats* stats,
+               bool overlap) {
+    const int rc = solve(c, b, out, nullptr, p, stats);   // out holds y for now
+    if (rc != FA_OK) return rc;
+    const int V = c->g.V;
+    const size_t s64 = (size_t)12 * V * sizeof(double2);
+    cudaStream_t st = c->stream;
+    FA_CUDA(c->io64b.ensure(s64), "alloc");
+    double2* o = c->io64b.as<double2>();
+    FA_TRY(hop_f64(c, c->y64.as<double2>(), o, std::sqrt(c->scale_c), false, !overlap, false, nullptr, nullptr,
+                   nullptr));
+    if (overlap) {
+        FA_CUDA(c->io64a.ensure(s64), "alloc");
+        double2* bp = c->io64a.as<double2>();
+        FA_TRY(launch_pack_spinor_f64(c->g, b, bp, st));
+        k_add_f64<<<(12 * V + kThreads - 1) / kThreads, kThreads, 0, st>>>(12 * V, bp, o);
+        c->launches++;
+        FA_LAUNCHED(c, "k_add_f64");
+    }
+    FA_TRY(launch_unpack_spinor_f64(c->g, o, out, st));
+    c->launches++;
+    FA_CUDA(cudaStreamSynchronize(st), "sync sign");
+    return FA_OK;
 }
 
 // ------------------------------------------------------------------ adjoint gradient
