@@ -525,6 +525,32 @@ def main():
         other[name] = {"ms": statistics.mean(lst), "tol": tol, "rel_err": e,
                        "outer_iters": res.stats["outer_iters"], "meets_1e-8": e <= TARGET}
     tol_h, e_h, _ = chosen["pseudo_mixed"]
+    if not args.quick:
+        # the overlap operator of Sec. 1 with the headline's solve settings:
+        # D_ov(mu) b = b + g5 sign(g5 D_w(mu)) b = b + sqrt(c) D_w f(A) b, error
+        # against the same operator with an FP64 solve at tol 1e-12
+        try:
+            kw = dict(variants["pseudo_mixed"])
+            ov_ref = ctx.apply_overlap(b, ell=ell, tol=1e-12, max_outer=4000, precision="f64").y
+            for _ in range(2):
+                ov = ctx.apply_overlap(b, ell=ell, tol=tol_h, max_outer=4000, **kw)
+            lst = []
+            for _ in range(max(1, min(args.steps, 3))):
+                flush.zero_()
+                s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                s_ev.record(stream)
+                ov = ctx.apply_overlap(b, ell=ell, tol=tol_h, max_outer=4000, **kw)
+                e_ev.record(stream)
+                torch.cuda.synchronize()
+                lst.append(s_ev.elapsed_time(e_ev))
+            e_ov = (torch.linalg.vector_norm(ov.y - ov_ref) / torch.linalg.vector_norm(ov_ref)).item()
+            other["overlap_pseudo_mixed"] = {
+                "ms": statistics.mean(lst), "tol": tol_h, "rel_err_vs_f64_overlap": e_ov,
+                "outer_iters": ov.stats["outer_iters"],
+                "what": "D_ov(mu) b = b + g5 sign(g5 D_w(mu)) b through fa_apply_overlap (solve + one FP64 sweep)"}
+        except Exception as ex:   # reported, never fatal to the bench line
+            other["overlap_pseudo_mixed"] = {"error": f"{type(ex).__name__}: {ex}"}
     other["pseudo_mixed_events"] = {"ms": statistics.mean(inst_ms), "note": "direct launches, hop events on"}
     other["pseudo_mixed"] = {"ms": ms_step, "tol": tol_h, "rel_err": e_h,
                              "outer_iters": head_res.stats["outer_iters"],
