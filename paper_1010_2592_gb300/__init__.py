@@ -31,7 +31,7 @@ _MODE = {"single": SINGLE, "double": DOUBLE, "pseudo": PSEUDO, SINGLE: SINGLE, D
 
 EXPORTS = (
     "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
-    "fa_set_poles", "fa_neuberger_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
+    "fa_set_poles", "fa_neuberger_poles", "fa_zolotarev_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
     "fa_apply_f", "fa_apply_sign", "fa_apply_overlap", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
     "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
@@ -100,6 +100,7 @@ def load_library(path=LIB_PATH):
         "fa_estimate_scale": (I, [P, P, I, ctypes.POINTER(D)]),
         "fa_set_poles": (I, [P, I, P, P]),
         "fa_neuberger_poles": (I, [I, P, P]),
+        "fa_zolotarev_poles": (I, [I, D, P, P, ctypes.POINTER(D)]),
         "fa_apply_dw": (I, [P, P, P, I, I]),
         "fa_apply_A": (I, [P, P, P, I, I]),
         "fa_apply_A_noalloc": (I, [P, P, P, I]),
@@ -143,6 +144,17 @@ def neuberger_poles(ns):
     sg = np.empty(ns, dtype=np.float64)
     _check(lib.fa_neuberger_poles(ns, om.ctypes.data, sg.ctypes.data), "fa_neuberger_poles")
     return om, sg
+
+
+def zolotarev_poles(ns, eps):
+    """(omega, sigma, delta) of Zolotarev's expansion on [eps^2, 1], computed by the library."""
+    lib = load_library()
+    om = np.empty(ns, dtype=np.float64)
+    sg = np.empty(ns, dtype=np.float64)
+    d = ctypes.c_double()
+    _check(lib.fa_zolotarev_poles(ns, float(eps), om.ctypes.data, sg.ctypes.data, ctypes.byref(d)),
+           "fa_zolotarev_poles")
+    return om, sg, d.value
 
 
 def apply_f_batched(contexts, sources, check=True, **kw):

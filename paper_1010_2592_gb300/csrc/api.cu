@@ -175,6 +175,84 @@ int fa_neuberger_poles(int ns, double* omega, double* sigma) {
     return FA_OK;
 }
 
+// Jacobi elliptic functions by the arithmetic-geometric mean scale
+// (Abramowitz & Stegun 16.4, 17.6), written with the complementary modulus kc
+// so that moduli near 1 keep their precision: a_0 = 1, b_0 = kc,
+// c_0 = sqrt(1 - kc^2); a_n = (a + b)/2, b_n = sqrt(a b), c_n = (a - b)/2 until
+// c_N is negligible; K = pi / (2 a_N); phi_N = 2^N a_N u,
+// phi_{n-1} = (phi_n + asin(c_n sin(phi_n) / a_n)) / 2; sn = sin phi_0,
+// cn = cos phi_0, dn = cos phi_0 / cos(phi_1 - phi_0).
+namespace {
+struct AgmScale {
+    double a[40], c[40];
+    int n = 0;
+};
+AgmScale agm_scale(double kc) {
+    AgmScale g;
+    double a = 1.0, b = kc;
+    g.a[0] = 1.0;
+    g.c[0] = std::sqrt((1.0 - kc) * (1.0 + kc));
+    while (g.n < 38 && std::fabs(g.c[g.n]) > 1e-17 * g.a[g.n]) {
+        const double an = 0.5 * (a + b), bn = std::sqrt(a * b), cn = 0.5 * (a - b);
+        a = an;
+        b = bn;
+        ++g.n;
+        g.a[g.n] = an;
+        g.c[g.n] = cn;
+    }
+    return g;
+}
+double ellip_K(const AgmScale& g) { return 3.14159265358979323846 / (2.0 * g.a[g.n]); }
+void ellip_sncndn(const AgmScale& g, double u, double* sn, double* cn, double* dn) {
+    double phi = std::ldexp(g.a[g.n] * u, g.n);
+    double phi1 = phi;
+    for (int k = g.n; k >= 1; --k) {
+        phi1 = phi;
+        phi = 0.5 * (phi + std::asin(g.c[k] * std::sin(phi) / g.a[k]));
+    }
+    *sn = std::sin(phi);
+    *cn = std::cos(phi);
+    *dn = g.n > 0 ? std::cos(phi) / std::cos(phi1 - phi) : 1.0;
+}
+}  // namespace
+
+int fa_zolotarev_poles(int ns, double eps, double* omega, double* sigma, double* delta) {
+    if (ns < 1 || ns > kMaxShifts || !omega || !sigma || !(eps > 0.0) || !(eps < 1.0)) return FA_EINVAL;
+    // modulus kappa' = sqrt(1 - eps^2), complementary modulus eps
+    const AgmScale g = agm_scale(eps);
+    const double K = ellip_K(g);
+    double c[2 * kMaxShifts];
+    for (int l = 1; l <= 2 * ns - 1; ++l) {
+        double sn, cn, dn;
+        ellip_sncndn(g, l * K / (2.0 * ns), &sn, &cn, &dn);
+        c[l] = eps * eps * (sn * sn) / (cn * cn);
+    }
+    // sigma_s = c_{2s-1}; residues of prod_{i<ns} (z + c_{2i}) / prod_s (z + c_{2s-1})
+    for (int s = 0; s < ns; ++s) {
+        const double sg = c[2 * s + 1];
+        double r = 1.0;
+        for (int i = 1; i < ns; ++i) r *= c[2 * i] - sg;
+        for (int t = 0; t < ns; ++t)
+            if (t != s) r /= c[2 * t + 1] - sg;
+        sigma[s] = sg;
+        omega[s] = r;
+    }
+    // D centres the error at the first two alternation points x = eps / dn(j K / (2 ns))
+    double p[2];
+    for (int j = 0; j < 2; ++j) {
+        double sn, cn, dn;
+        ellip_sncndn(g, j * K / (2.0 * ns), &sn, &cn, &dn);
+        const double x = eps / dn;
+        double acc = 0.0;
+        for (int s = 0; s < ns; ++s) acc += omega[s] / (x * x + sigma[s]);
+        p[j] = x * acc;
+    }
+    const double D = 2.0 / (p[0] + p[1]);
+    for (int s = 0; s < ns; ++s) omega[s] *= D;
+    if (delta) *delta = std::fabs(D * p[0] - 1.0);
+    return FA_OK;
+}
+
 int fa_estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out) {
     if (!c) return FA_EINVAL;
     return estimate_scale(c, v0, iters, scale_out);

@@ -88,3 +88,16 @@ def neuberger_eps(x, n):
 def gauge_rotate_spinor(g, psi):
     """(G psi)(x) = g(x) psi(x) on the colour index."""
     return psi @ np.swapaxes(g, -1, -2)
+
+
+def alternation(om, sg, eps, npts=400001):
+    """Error of x R(x^2) against sign(x) = 1 on a log grid of [eps, 1]: its
+    maximum modulus and the signs at the grid's local extrema that reach it."""
+    x = np.geomspace(eps, 1.0, npts)
+    err = x * np.sum(om[None, :] / (x[:, None] ** 2 + sg[None, :]), axis=1) - 1.0
+    d = np.abs(err).max()
+    a = np.abs(err)
+    i = np.flatnonzero((a[1:-1] >= a[:-2]) & (a[1:-1] >= a[2:])) + 1
+    ends = [0, len(err) - 1]
+    pts = sorted(set(j for j in list(i) + ends if a[j] > (1 - 1e-6) * d))
+    return d, np.sign(err[pts])

@@ -52,6 +52,28 @@ def test_library_neuberger_poles_match_oracle(ns):
     assert np.allclose(sg, sg_o, rtol=1e-15, atol=1e-300)
 
 
+@pytest.mark.parametrize("ns,eps", [(1, 0.5), (4, 0.05), (10, 0.01), (20, 0.003), (32, 1e-3)])
+def test_library_zolotarev_poles_match_oracle(ns, eps):
+    """Host code: the library's own elliptic functions (AGM scale) against the
+    oracle's library routines (scipy.special)."""
+    om, sg, d = fa.zolotarev_poles(ns, eps)
+    om_o, sg_o, d_o = poles.zolotarev_poles(ns, eps)
+    assert np.allclose(om, om_o, rtol=1e-10, atol=0)
+    assert np.allclose(sg, sg_o, rtol=1e-10, atol=0)
+    assert abs(d - d_o) <= 1e-9 * d_o + 1e-15
+
+
+def test_library_zolotarev_poles_equioscillate_at_small_eps():
+    """Where scipy's elliptic functions lose digits (modulus near 1), the
+    library's poles still give the alternation of the best approximation."""
+    from closed_forms import alternation
+    ns, eps = 5, 1e-4
+    om, sg, d = fa.zolotarev_poles(ns, eps)
+    dd, signs = alternation(om, sg, eps, npts=2000001)
+    assert len(signs) == 2 * ns + 1 and np.all(signs[1:] != signs[:-1])
+    assert abs(dd - d) <= 1e-5 * d
+
+
 def test_invalid_arguments_rejected_before_any_device_call():
     import ctypes
     lib = fa.load_library()
@@ -62,5 +84,9 @@ def test_invalid_arguments_rejected_before_any_device_call():
     assert lib.fa_neuberger_poles(65, None, None) == fa.FA_EINVAL
     assert lib.fa_destroy(None) == fa.FA_OK
     assert lib.fa_set_params(None, -1.8, 0.1, -1, 1.0) == fa.FA_EINVAL
+    om = np.empty(4)
+    for bad_eps in (0.0, 1.0, -0.1, float("nan")):
+        assert lib.fa_zolotarev_poles(4, bad_eps, om.ctypes.data, om.ctypes.data, None) == fa.FA_EINVAL
+    assert lib.fa_zolotarev_poles(65, 0.1, om.ctypes.data, om.ctypes.data, None) == fa.FA_EINVAL
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     assert lib.fa_hop_timing_split(None, fa.F32, 0, ctypes.byref(ms), ctypes.byref(n)) == fa.FA_EINVAL
