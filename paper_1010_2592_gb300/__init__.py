@@ -32,7 +32,7 @@ _MODE = {"single": SINGLE, "double": DOUBLE, "pseudo": PSEUDO, SINGLE: SINGLE, D
 EXPORTS = (
     "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
     "fa_set_poles", "fa_neuberger_poles", "fa_zolotarev_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
-    "fa_apply_f", "fa_apply_sign", "fa_apply_overlap", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
+    "fa_apply_f", "fa_apply_sign", "fa_apply_overlap", "fa_apply_sign_deflated", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
     "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune",
@@ -108,6 +108,8 @@ def load_library(path=LIB_PATH):
         "fa_apply_f": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_sign": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_overlap": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+        "fa_apply_sign_deflated": (I, [P, P, P, I, P, P, P, I, ctypes.POINTER(SolverParams),
+                                       ctypes.POINTER(SolverStats)]),
         "fa_apply_f_host": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_apply_f_batched": (I, [P, I, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_grad": (I, [P, P, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P,
@@ -308,6 +310,29 @@ class Context:
     def apply_overlap(self, b, out=None, check=True, **kw):
         """D_ov(mu) b = b + g5 sign(g5 D_w(mu)) b (Sec. 1); keywords as apply_f."""
         return self._sign_call(self.lib.fa_apply_overlap, "fa_apply_overlap", b, out, check, kw)
+
+    def apply_sign_deflated(self, b, lam, R, Lv, overlap=False, out=None, check=True, **kw):
+        """sign(H) b (or D_ov b) with k eigenpairs of H = g5 D_w treated exactly:
+        lam (k complex), R and Lv (complex128 CUDA tensors of shape (k,) + the
+        spinor shape: right and left eigenvectors, Lv_i^H R_j = delta_ij)."""
+        b = _spinor_check(b, self.spinor_shape, "b")
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128))
+        k = lam.size
+        shape = (k,) + tuple(self.spinor_shape)
+        for t, nm in ((R, "R"), (Lv, "Lv")):
+            torch = _torch()
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128
+                    and t.is_contiguous() and tuple(t.shape) == shape):
+                raise ValueError(f"{nm}: expected a contiguous complex128 CUDA tensor of shape {shape}")
+        y = self.empty_spinor() if out is None else _spinor_check(out, self.spinor_shape, "out")
+        p = self.params(**kw)
+        st = SolverStats()
+        rc = self.lib.fa_apply_sign_deflated(self.h, b.data_ptr(), y.data_ptr(), k, lam.ctypes.data,
+                                             R.data_ptr(), Lv.data_ptr(), int(bool(overlap)), ctypes.byref(p),
+                                             ctypes.byref(st))
+        if check:
+            _check(rc, "fa_apply_sign_deflated")
+        return Result(y, st.as_dict())
 
     def _sign_call(self, fn, name, b, out, check, kw):
         b = _spinor_check(b, self.spinor_shape, "b")

@@ -350,6 +350,13 @@ int fa_apply_overlap(fa_ctx* c, const double* b, double* out, const fa_solver_pa
     return apply_sign(c, b, out, p, stats, true);
 }
 
+int fa_apply_sign_deflated(fa_ctx* c, const double* b, double* out, int k, const double* lambda, const double* R,
+                           const double* Lv, int overlap, const fa_solver_params* p, fa_solver_stats* stats) {
+    if (!c || !b || !out || !p || b == out || k < 0 || k > 1024) return FA_EINVAL;
+    if (k > 0 && (!lambda || !R || !Lv || R == out || Lv == out)) return FA_EINVAL;
+    return apply_sign_deflated(c, b, out, k, lambda, R, Lv, overlap != 0, p, stats);
+}
+
 int fa_apply_f_batched(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y,
                        const fa_solver_params* p, fa_solver_stats* stats) {
     if (!ctxs || !b || !y || !p || n < 1 || n > 4096) return FA_EINVAL;
@@ -426,7 +433,7 @@ int fa_device_bytes(const fa_ctx* c, unsigned long long* field_bytes, unsigned l
                                  &c->io32b, &c->tmp64, &c->tmp32, &c->partials, &c->r64, &c->u64, &c->rt64,
                                  &c->r32, &c->u32, &c->rt32, &c->y64, &c->xs64, &c->us64, &c->bhost_dev,
                                  &c->yhost_dev, &c->gx, &c->gpart, &c->store64, &c->store32, &c->snap64,
-                                 &c->snap32, &c->xrel, &c->brel, &c->snapx};
+                                 &c->snap32, &c->xrel, &c->brel, &c->snapx, &c->defl};
     // scalars: solver state, shifts, records, pass-2 weights, batch descriptors
     const fa::DevBuf* scal[] = {&c->state, &c->shiftbuf, &c->rec, &c->prec, &c->coef, &c->cs, &c->coef4,
                                 &c->descbuf, &c->flagbuf};

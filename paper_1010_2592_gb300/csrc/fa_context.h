@@ -84,6 +84,7 @@ struct fa_ctx {
     fa::DevBuf snap64, snap32;           // seed state at the first unstored outer iteration
     fa::DevBuf descbuf, flagbuf;         // batch descriptors and done flags (first context of a batch)
     fa::DevBuf xrel, brel, snapx;        // reliable updates: seed solution, packed source, snapshot
+    fa::DevBuf defl;                     // deflated sign: partial sums, coefficients, projected source
     std::vector<fa::GraphEntry> graphs;  // captured outer iterations
     void* pinned = nullptr;              // host copy of DevState
     size_t pinned_bytes = 0;
@@ -126,6 +127,8 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
 int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out);
 int apply_sign(fa_ctx* c, const double* b, double* out, const fa_solver_params* p, fa_solver_stats* stats,
                bool overlap);
+int apply_sign_deflated(fa_ctx* c, const double* b, double* out, int k, const double* lambda, const double* R,
+                        const double* Lv, bool overlap, const fa_solver_params* p, fa_solver_stats* stats);
 int grad(fa_ctx* c, const double* b, const double* eta, double* dLdU, double* dLdmu, double* L, double* dLdb,
          const fa_solver_params* p, fa_solver_stats* stats);
 }  // namespace fa

@@ -135,6 +135,52 @@ __global__ void k_add_f64(int n, const double2* __restrict__ x, double2* __restr
     y[idx] = make_double2(t.x + a.x, t.y + a.y);
 }
 
+// Deflation on canonical spinors (n = 12 V complex elements each).
+// part[i * gridDim.x + block] = partial sum of conj(V_i) b over the block's elements
+__global__ void __launch_bounds__(kThreads) k_dots_canon(int n, const double2* __restrict__ V,
+                                                         const double2* __restrict__ b, double2* __restrict__ part) {
+    const double2* v = V + (size_t)blockIdx.y * n;
+    double re = 0.0, im = 0.0;
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < n; e += gridDim.x * kThreads) {
+        const double2 x = v[e], y = b[e];
+        re = fma(x.x, y.x, fma(x.y, y.y, re));
+        im = fma(x.x, y.y, fma(-x.y, y.x, im));
+    }
+    __shared__ double sre[kThreads], sim[kThreads];
+    const int t = threadIdx.x;
+    sre[t] = re;
+    sim[t] = im;
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            sre[t] += sre[t + h];
+            sim[t] += sim[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(sre[0], sim[0]);
+}
+// out[e] = base[e] + g(e) sum_i coef[i] V_i[e]; g(e) = -1 on spins 2, 3 (the
+// canonical site holds 4 spins x 3 colours) when g5, else 1.  base may be out.
+__global__ void __launch_bounds__(kThreads) k_lincomb_canon(int n, int k, const double2* __restrict__ coef,
+                                                            const double2* __restrict__ V, const double2* base,
+                                                            double2* out, int g5) {
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < n; e += gridDim.x * kThreads) {
+        double re = 0.0, im = 0.0;
+        for (int i = 0; i < k; ++i) {
+            const double2 a = coef[i], x = V[(size_t)i * n + e];
+            re = fma(a.x, x.x, fma(-a.y, x.y, re));
+            im = fma(a.x, x.y, fma(a.y, x.x, im));
+        }
+        if (g5 && (e % 12) >= 6) {
+            re = -re;
+            im = -im;
+        }
+        const double2 c = base[e];
+        out[e] = make_double2(c.x + re, c.y + im);
+    }
+}
+
 // ------------------------------------------------------------------ workspace
 struct Layout {
     int L, ns, max_outer, V;
@@ -966,6 +1012,63 @@ int apply_sign(fa_ctx* c, const double* b, double* out, const fa_solver_params* 
     FA_TRY(launch_unpack_spinor_f64(c->g, o, out, st));
     c->launches++;
     FA_CUDA(cudaStreamSynchronize(st), "sync sign");
+    return FA_OK;
+}
+
+// sign(H) b with k eigenpairs of H = g5 D_w treated exactly: a_i = <l_i, b>,
+// sign(H) b = sum_i sign(Re lambda_i) a_i r_i + sign-by-poles(b - sum_i a_i r_i);
+// D_ov b = b + g5 sign(H) b.  The k inner products are summed on the host in
+// a fixed order (deterministic).
+int apply_sign_deflated(fa_ctx* c, const double* b, double* out, int k, const double* lambda, const double* R,
+                        const double* Lv, bool overlap, const fa_solver_params* p, fa_solver_stats* stats) {
+    if (k == 0) return apply_sign(c, b, out, p, stats, overlap);
+    if (!c->have_gauge || !c->have_params || !c->have_poles) return FA_ESTATE;
+    const int n = 12 * c->g.V;
+    const int nb = std::min((n + kThreads - 1) / kThreads, 4 * sms());
+    cudaStream_t st = c->stream;
+    const size_t part_n = (size_t)k * nb, coef_n = (size_t)3 * k;
+    FA_CUDA(c->defl.ensure((part_n + coef_n + (size_t)n) * sizeof(double2)), "alloc deflation");
+    double2* part = c->defl.as<double2>();
+    double2* coef = part + part_n;     // [-a_i | sign(Re lambda_i) a_i | a_i]
+    double2* bp = coef + coef_n;       // b - sum_i a_i r_i
+    const double2* Rv = reinterpret_cast<const double2*>(R);
+    const double2* Lw = reinterpret_cast<const double2*>(Lv);
+    const double2* bv = reinterpret_cast<const double2*>(b);
+    k_dots_canon<<<dim3(nb, k), kThreads, 0, st>>>(n, Lw, bv, part);
+    FA_LAUNCHED(c, "k_dots_canon");
+    std::vector<double2> hp(part_n), hc(coef_n);
+    FA_CUDA(cudaMemcpyAsync(hp.data(), part, part_n * sizeof(double2), cudaMemcpyDeviceToHost, st), "copy partials");
+    FA_CUDA(cudaStreamSynchronize(st), "sync deflation");
+    for (int i = 0; i < k; ++i) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < nb; ++j) {
+            re += hp[(size_t)i * nb + j].x;
+            im += hp[(size_t)i * nb + j].y;
+        }
+        const double lr = lambda[2 * i];
+        if (!std::isfinite(re) || !std::isfinite(im) || !std::isfinite(lr) || lr == 0.0) return FA_EINVAL;
+        const double sg = lr > 0.0 ? 1.0 : -1.0;
+        hc[i] = make_double2(-re, -im);
+        hc[k + i] = make_double2(sg * re, sg * im);
+        hc[2 * k + i] = make_double2(re, im);
+    }
+    FA_CUDA(cudaMemcpyAsync(coef, hc.data(), coef_n * sizeof(double2), cudaMemcpyHostToDevice, st), "copy coefficients");
+    k_lincomb_canon<<<nb, kThreads, 0, st>>>(n, k, coef, Rv, bv, bp, 0);
+    FA_LAUNCHED(c, "k_lincomb_canon");
+    const int rc = apply_sign(c, reinterpret_cast<const double*>(bp), out, p, stats, overlap);
+    if (rc != FA_OK) return rc;
+    double2* o = reinterpret_cast<double2*>(out);
+    if (!overlap) {
+        k_lincomb_canon<<<nb, kThreads, 0, st>>>(n, k, coef + k, Rv, o, o, 0);
+        FA_LAUNCHED(c, "k_lincomb_canon");
+    } else {
+        // out = b' + g5 sign(H) b'; add back sum_i a_i r_i and g5 sum_i sign_i a_i r_i
+        k_lincomb_canon<<<nb, kThreads, 0, st>>>(n, k, coef + 2 * k, Rv, o, o, 0);
+        FA_LAUNCHED(c, "k_lincomb_canon");
+        k_lincomb_canon<<<nb, kThreads, 0, st>>>(n, k, coef + k, Rv, o, o, 1);
+        FA_LAUNCHED(c, "k_lincomb_canon");
+    }
+    FA_CUDA(cudaStreamSynchronize(st), "sync deflation");
     return FA_OK;
 }
 

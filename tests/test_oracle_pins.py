@@ -442,3 +442,33 @@ def test_zolotarev_beats_neuberger_on_its_interval():
         assert delta < 1e-2 * e_n
         assert delta < 1e-2 * prev
         prev = delta
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.1])
+def test_deflated_sign_converges_to_the_exact_sign(mu):
+    """Treating the k eigenpairs of H = g5 D_w smallest in magnitude exactly
+    leaves the pole form only the rest of the spectrum, where 20 Neuberger poles
+    are accurate: against the dense exact sign the error falls as k grows, and
+    deflating every eigenpair gives the exact sign."""
+    U = inputs.su3_exp_gauge(TINY, 0.5, 51)
+    c = scale.power_scale(dirac.Operator(U, -1.8, mu).A, inputs.gaussian_spinor(TINY, 52), 100)
+    op = dirac.Operator(U, -1.8, mu, c)
+    b = inputs.gaussian_spinor(TINY, 53)
+    Hm = overlap.dense_H(op)
+    s_exact = (overlap.sign_dense(Hm) @ b.reshape(-1)).reshape(b.shape)
+    Am = direct.dense_matrix(op.A, op.shape)
+    om, sg = poles.neuberger_poles(20)
+
+    def f(v):
+        return direct.pfe_dense(Am, v, om, sg)
+
+    errs = []
+    for k in (0, 4, 16, 64):
+        lam, R, Lv = overlap.smallest_eigenpairs(Hm, k, op.shape)
+        errs.append(rel(overlap.sign_deflated(op, b, lam, R, Lv, f), s_exact))
+    assert all(e1 < 0.7 * e0 for e0, e1 in zip(errs, errs[1:]))
+    assert errs[0] > 1e-3 and errs[-1] < 1e-5
+    lam, R, Lv = overlap.smallest_eigenpairs(Hm, Hm.shape[0], op.shape)
+    assert rel(overlap.sign_deflated(op, b, lam, R, Lv, f), s_exact) < 1e-10
+    d_ov = overlap.overlap_deflated(op, b, lam, R, Lv, f)
+    assert rel(d_ov, b + dirac.gamma5(s_exact)) < 1e-10
