@@ -472,3 +472,25 @@ def test_deflated_sign_converges_to_the_exact_sign(mu):
     assert rel(overlap.sign_deflated(op, b, lam, R, Lv, f), s_exact) < 1e-10
     d_ov = overlap.overlap_deflated(op, b, lam, R, Lv, f)
     assert rel(d_ov, b + dirac.gamma5(s_exact)) < 1e-10
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.15])
+def test_free_field_sign_closed_form(mu):
+    """U = 1 on 4^3 x 8: H(p)^2 = a(p)^2 + sum_nu s_nu(p)^2 is a scalar per mode,
+    so sign(H) b = H (H^2)^{-1/2} b = sqrt(c) H [A^{-1/2} b] with A^{-1/2} applied
+    mode by mode (principal root; FFT).  The oracle's pole form with Zolotarev
+    poles for the interval the free spectrum spans (16 poles: uniform error at
+    round-off there) and its overlap operator against it."""
+    dims = (4, 4, 4, 8)
+    U = inputs.unit_gauge(dims)
+    lam = free_A_eigenvalues(dims, 1.0, mu, 1.0)
+    c = 1.0 / np.abs(lam).max()
+    op = dirac.Operator(U, 1.0, mu, c)
+    b = inputs.gaussian_spinor(dims, 99)
+    isqrt = free_matfunc(b, dims, 1.0, mu, c, lambda z: 1.0 / np.sqrt(z.astype(np.complex128)))
+    s_exact = np.sqrt(c) * dirac.gamma5(op.D(isqrt))
+    om, sg, delta = poles.zolotarev_poles(16, 0.99 * np.sqrt(np.abs(lam * c).min()))
+    assert delta < 1e-13
+    y = ms.multishift_double(op.A, b, sg, om, 2, 1e-13)
+    assert rel(overlap.sign_apply(op, y), s_exact) < 1e-11
+    assert rel(overlap.overlap_apply(op, b, y), b + dirac.gamma5(s_exact)) < 1e-11
