@@ -8,12 +8,14 @@ generators in `inputs/`.
 
 Modules
     dirac      Wilson-Dirac operator D_w(mu), gamma_5, A = c (gamma_5 D_w)^2
-    poles      Neuberger partial-fraction poles {omega_s, sigma_s}, Eq. (1)
+    poles      Neuberger and Zolotarev partial-fraction poles {omega_s, sigma_s}, Eq. (1)
     msbicgstab BiCGstab(l) seed recurrence, single-pass multi-shift, and the
                double-pass form of Sec. 2 (Eqs. 2-3)
     direct     y* by per-shift library solves, dense LU and eigendecomposition
     scale      power-iteration estimate of the largest eigenvalue of A
-    overlap    sign(gamma_5 D_w) b and the overlap operator D_ov(mu) b of Sec. 1
+    overlap    sign(gamma_5 D_w) b and the overlap operator D_ov(mu) b of Sec. 1,
+               deflated by exactly treated eigenpairs
+    grad       gradient of L = Re <eta, f(A) b> with respect to the links and mu
 
 Parity status: every function is pinned by the `-m "not gpu"` tests except
 the closed-form double-pass coefficients of Sec. 4 (A_mj, B_m^s, D, E, F, G,
