@@ -224,8 +224,15 @@ int fa_zolotarev_poles(int ns, double eps, double* omega, double* sigma, double*
     double c[2 * kMaxShifts];
     for (int l = 1; l <= 2 * ns - 1; ++l) {
         double sn, cn, dn;
-        ellip_sncndn(g, l * K / (2.0 * ns), &sn, &cn, &dn);
-        c[l] = eps * eps * (sn * sn) / (cn * cn);
+        if (2 * l <= 2 * ns) {
+            ellip_sncndn(g, l * K / (2.0 * ns), &sn, &cn, &dn);
+            c[l] = eps * eps * (sn * sn) / (cn * cn);
+        } else {
+            // past K/2, cn(u) is small and cos(phi) loses its digits: with u' = K - u,
+            // sn(u) = cn(u')/dn(u') and cn(u) = eps sn(u')/dn(u'), so c_l = cn^2(u')/sn^2(u')
+            ellip_sncndn(g, (2 * ns - l) * K / (2.0 * ns), &sn, &cn, &dn);
+            c[l] = (cn * cn) / (sn * sn);
+        }
     }
     // sigma_s = c_{2s-1}; residues of prod_{i<ns} (z + c_{2i}) / prod_s (z + c_{2s-1})
     for (int s = 0; s < ns; ++s) {
@@ -237,19 +244,46 @@ int fa_zolotarev_poles(int ns, double eps, double* omega, double* sigma, double*
         sigma[s] = sg;
         omega[s] = r;
     }
-    // D centres the error at the first two alternation points x = eps / dn(j K / (2 ns))
-    double p[2];
-    for (int j = 0; j < 2; ++j) {
-        double sn, cn, dn;
-        ellip_sncndn(g, j * K / (2.0 * ns), &sn, &cn, &dn);
-        const double x = eps / dn;
+    // the error alternates at x_j = eps / dn(j K / (2 ns)), j = 0..2 ns (past K/2:
+    // dn(K - u') = eps / dn(u'), so x_j = dn(u')); D centres it at x_0 and x_1
+    double p[2 * kMaxShifts + 1];
+    for (int j = 0; j <= 2 * ns; ++j) {
+        double sn, cn, dn, x;
+        if (2 * j <= 2 * ns) {
+            ellip_sncndn(g, j * K / (2.0 * ns), &sn, &cn, &dn);
+            x = eps / dn;
+        } else {
+            ellip_sncndn(g, (2 * ns - j) * K / (2.0 * ns), &sn, &cn, &dn);
+            x = dn;
+        }
         double acc = 0.0;
         for (int s = 0; s < ns; ++s) acc += omega[s] / (x * x + sigma[s]);
         p[j] = x * acc;
     }
     const double D = 2.0 / (p[0] + p[1]);
+    const double d0 = std::fabs(D * p[0] - 1.0);
+    // self-check: residues positive, and the error equal in size (to 1 % above the
+    // rounding level of about 1e-12) with alternating signs at every alternation
+    // point.  With more poles than double precision resolves at this eps (small eps
+    // puts cn near 0 in the middle of the range, where it loses digits), the
+    // residues lose theirs and the check fails.
+    const double floor_err = 1e-12;
+    bool ok = std::isfinite(D) && D > 0.0;
+    for (int s = 0; s < ns; ++s) ok = ok && omega[s] > 0.0 && std::isfinite(omega[s]);
+    double dmax = 0.0;
+    for (int j = 0; j <= 2 * ns; ++j) {
+        const double e = D * p[j] - 1.0;
+        dmax = std::max(dmax, std::fabs(e));
+        ok = ok && std::fabs(std::fabs(e) - d0) <= 0.01 * d0 + floor_err;
+        if (d0 > 100.0 * floor_err) ok = ok && (e > 0.0) == (j % 2 == 1);
+    }
+    if (!ok) {
+        set_error("fa_zolotarev_poles: %d poles exceed what double precision resolves at eps = %g; "
+                  "fewer poles reach the rounding floor", ns, eps);
+        return FA_EINVAL;
+    }
     for (int s = 0; s < ns; ++s) omega[s] *= D;
-    if (delta) *delta = std::fabs(D * p[0] - 1.0);
+    if (delta) *delta = dmax;
     return FA_OK;
 }
 
