@@ -172,6 +172,19 @@ def golden_outer_iters(name, tol=1e-9):
     return (best[1], best[2]) if best else (None, None)
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(w, c, outer_ref, outer=2, ref_tol=None):
     t = oracle_sample(w, c, outer)
     per_solve_ms = t / outer * 2 * outer_ref * 1e3
@@ -181,7 +194,7 @@ def cpu_baseline(w, c, outer_ref, outer=2, ref_tol=None):
                       f"recurrence on {'x'.join(map(str, w['dims']))} ({t:.1f} s), scaled by "
                       f"2 x {outer_ref} outer iterations{at} (pass 1 + pass 2 of the double-pass form); "
                       f"numpy, {oracle_sample.threads} thread(s) by CPU time / wall time, of "
-                      f"{os.cpu_count()} host cores"}
+                      f"{os.cpu_count()} host cores ({cpu_model()})"}
 
 
 def run_reference(args, ws, rank):
@@ -206,10 +219,13 @@ def run_reference(args, ws, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args.workload, w),
         "cpu_baseline": {"value": per_solve, "unit": "ms", "cores": oracle_sample.threads, "kind": "oracle",
-                         "sample": f"each step: 1 outer iteration of the FP64 numpy oracle's "
-                                   f"BiCGstab({w['ell']}) recurrence, scaled by 2 x {outer_ref} outer "
-                                   f"iterations (both passes of the oracle's double-pass solve; the "
-                                   f"oracle's own iteration count at tol {ref_tol})"},
+                         "sample": (f"each step: 1 outer iteration of the FP64 numpy oracle's "
+                                    f"BiCGstab({w['ell']}) recurrence, scaled by 2 x {outer_ref} outer "
+                                    f"iterations (both passes of the oracle's double-pass solve; "
+                                    + (f"the oracle's own iteration count at tol {ref_tol}); " if ref_tol
+                                       else "no stored oracle count for this workload, 100 assumed); ")
+                                    + f"{oracle_sample.threads} thread(s) of {os.cpu_count()} host cores "
+                                    f"({cpu_model()})")},
         "e2e": {"value": per_solve, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
