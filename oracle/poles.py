@@ -50,10 +50,12 @@ def zolotarev_poles(ns, eps):
     c = eps * eps * sn * sn / (cn * cn)      # c_1 .. c_{2 ns - 1}, increasing
     sigma = c[0::2]                          # c_1, c_3, .., c_{2 ns - 1}
     zeros = c[1::2]                          # c_2, .., c_{2 ns - 2}
+    # partial fractions: residue at -sigma_s of prod (z + zeros) / prod (z + sigma),
+    # each zero divided by its interlacing neighbour pole (factors in (0, 1))
     res = np.empty(ns)
     for s in range(ns):
-        others = np.delete(sigma, s)
-        res[s] = np.prod(zeros - sigma[s]) / np.prod(others - sigma[s])
+        others = np.delete(sigma, s)           # the poles t != s, in order: one per zero
+        res[s] = np.prod((zeros - sigma[s]) / (others - sigma[s]))
     # R with D = 1 at the first two alternation points; D centres the error there
     _, _, dn, _ = special.ellipj(np.array([0.0, K / (2 * ns)]), m)
     x = eps / dn

@@ -175,85 +175,109 @@ int fa_neuberger_poles(int ns, double* omega, double* sigma) {
     return FA_OK;
 }
 
-// Jacobi elliptic functions by the arithmetic-geometric mean scale
-// (Abramowitz & Stegun 16.4, 17.6), written with the complementary modulus kc
-// so that moduli near 1 keep their precision: a_0 = 1, b_0 = kc,
-// c_0 = sqrt(1 - kc^2); a_n = (a + b)/2, b_n = sqrt(a b), c_n = (a - b)/2 until
-// c_N is negligible; K = pi / (2 a_N); phi_N = 2^N a_N u,
-// phi_{n-1} = (phi_n + asin(c_n sin(phi_n) / a_n)) / 2; sn = sin phi_0,
-// cn = cos phi_0, dn = cos phi_0 / cos(phi_1 - phi_0).
+// Elliptic functions for Zolotarev's expansion.  K(k) = pi / (2 AGM(1, k')) with
+// k' the complementary modulus (Abramowitz & Stegun 17.6).  The expansion needs
+// sc(u | kappa') and dn(u | kappa') for kappa' = sqrt(1 - eps^2), a modulus close
+// to 1 where cn(u) is small and amplitude-based methods lose digits.  Jacobi's
+// imaginary transformation (A&S 16.20) turns them into functions of the small
+// modulus eps at the imaginary argument iu: sc(u | kappa') = -i sn(iu | eps) and
+// dn(u | kappa') = dn(iu | eps) / cn(iu | eps), evaluated by the theta series
+// (A&S 16.36) of nome q = exp(-pi K(kappa') / K(eps)) at v = i w,
+// w = pi u / (2 K(eps)):
+//   sc = (th3(0) / th2(0)) * 2 sum_n (-1)^n q^{(n+1/2)^2} sinh((2n+1) w) / th4(iw),
+//   dn = (th2(0) / th3(0)) * th3(iw) / th2(iw),
+// th3(iw) = 1 + 2 sum q^{n^2} cosh(2nw), th4(iw) = 1 + 2 sum (-1)^n q^{n^2} cosh(2nw),
+// th2(iw) = 2 sum q^{(n+1/2)^2} cosh((2n+1)w).  For u <= K(kappa')/2 the terms
+// fall like q^{n^2 - n} and th4(iw) >= 1 - 2 sqrt(q).
 namespace {
-struct AgmScale {
-    double a[40], c[40];
-    int n = 0;
-};
-AgmScale agm_scale(double kc) {
-    AgmScale g;
+double ellip_K_of_complement(double kc) {
     double a = 1.0, b = kc;
-    g.a[0] = 1.0;
-    g.c[0] = std::sqrt((1.0 - kc) * (1.0 + kc));
-    while (g.n < 38 && std::fabs(g.c[g.n]) > 1e-17 * g.a[g.n]) {
-        const double an = 0.5 * (a + b), bn = std::sqrt(a * b), cn = 0.5 * (a - b);
+    for (int it = 0; it < 64 && std::fabs(a - b) > 1e-17 * a; ++it) {
+        const double an = 0.5 * (a + b);
+        b = std::sqrt(a * b);
         a = an;
-        b = bn;
-        ++g.n;
-        g.a[g.n] = an;
-        g.c[g.n] = cn;
     }
-    return g;
+    return 3.14159265358979323846 / (2.0 * a);
 }
-double ellip_K(const AgmScale& g) { return 3.14159265358979323846 / (2.0 * g.a[g.n]); }
-void ellip_sncndn(const AgmScale& g, double u, double* sn, double* cn, double* dn) {
-    double phi = std::ldexp(g.a[g.n] * u, g.n);
-    double phi1 = phi;
-    for (int k = g.n; k >= 1; --k) {
-        phi1 = phi;
-        phi = 0.5 * (phi + std::asin(g.c[k] * std::sin(phi) / g.a[k]));
+struct ZoloElliptic {
+    double K_eps, K_kp, log_q, th2_0, th3_0;
+    explicit ZoloElliptic(double eps) {
+        const double kp = std::sqrt((1.0 - eps) * (1.0 + eps));
+        K_eps = ellip_K_of_complement(kp);   // K(eps)
+        K_kp = ellip_K_of_complement(eps);   // K(kappa')
+        log_q = -3.14159265358979323846 * K_kp / K_eps;
+        th2_0 = 0.0;
+        th3_0 = 1.0;
+        for (int n = 0; n < 64; ++n) {
+            const double e = std::exp(log_q * (n + 0.5) * (n + 0.5));
+            th2_0 += 2.0 * e;
+            if (n >= 1) th3_0 += 2.0 * std::exp(log_q * n * n);
+            if (e < 1e-300) break;
+        }
     }
-    *sn = std::sin(phi);
-    *cn = std::cos(phi);
-    *dn = g.n > 0 ? std::cos(phi) / std::cos(phi1 - phi) : 1.0;
-}
+    // sc(u | kappa') and dn(u | kappa') for 0 <= u <= K(kappa') / 2
+    void sc_dn(double u, double* sc, double* dn) const {
+        const double w = 3.14159265358979323846 * u / (2.0 * K_eps);
+        double t1 = 0.0, t2 = 0.0, th3 = 1.0, th4 = 1.0;
+        for (int n = 0; n < 64; ++n) {
+            const double e = std::exp(log_q * (n + 0.5) * (n + 0.5));
+            const double sgn = (n % 2) ? -1.0 : 1.0;
+            t1 += 2.0 * sgn * e * std::sinh((2 * n + 1) * w);
+            t2 += 2.0 * e * std::cosh((2 * n + 1) * w);
+            if (n >= 1) {
+                const double f = 2.0 * std::exp(log_q * n * n) * std::cosh(2.0 * n * w);
+                th3 += f;
+                th4 += sgn * f;
+            }
+            if (e * std::cosh((2 * n + 1) * w) < 1e-300) break;
+        }
+        *sc = (th3_0 / th2_0) * t1 / th4;
+        *dn = (th2_0 / th3_0) * th3 / t2;
+    }
+};
 }  // namespace
 
 int fa_zolotarev_poles(int ns, double eps, double* omega, double* sigma, double* delta) {
     if (ns < 1 || ns > kMaxShifts || !omega || !sigma || !(eps > 0.0) || !(eps < 1.0)) return FA_EINVAL;
-    // modulus kappa' = sqrt(1 - eps^2), complementary modulus eps
-    const AgmScale g = agm_scale(eps);
-    const double K = ellip_K(g);
+    // modulus kappa' = sqrt(1 - eps^2); u_l = l K(kappa') / (2 ns).  Past K/2 the
+    // reflection u -> K - u: sc(K - u) = cs(u) / eps and dn(K - u) = eps / dn(u).
+    const ZoloElliptic z(eps);
+    const double Kp = z.K_kp;
     double c[2 * kMaxShifts];
     for (int l = 1; l <= 2 * ns - 1; ++l) {
-        double sn, cn, dn;
+        double sc, dn;
         if (2 * l <= 2 * ns) {
-            ellip_sncndn(g, l * K / (2.0 * ns), &sn, &cn, &dn);
-            c[l] = eps * eps * (sn * sn) / (cn * cn);
+            z.sc_dn(l * Kp / (2.0 * ns), &sc, &dn);
+            c[l] = eps * eps * sc * sc;
         } else {
-            // past K/2, cn(u) is small and cos(phi) loses its digits: with u' = K - u,
-            // sn(u) = cn(u')/dn(u') and cn(u) = eps sn(u')/dn(u'), so c_l = cn^2(u')/sn^2(u')
-            ellip_sncndn(g, (2 * ns - l) * K / (2.0 * ns), &sn, &cn, &dn);
-            c[l] = (cn * cn) / (sn * sn);
+            z.sc_dn((2 * ns - l) * Kp / (2.0 * ns), &sc, &dn);
+            c[l] = 1.0 / (sc * sc);
         }
     }
-    // sigma_s = c_{2s-1}; residues of prod_{i<ns} (z + c_{2i}) / prod_s (z + c_{2s-1})
+    // sigma_s = c_{2s-1}; residues of prod_{i<ns} (z + c_{2i}) / prod_s (z + c_{2s-1}).
+    // Zeros and poles interlace, so each zero is paired with the neighbouring pole
+    // on the far side from sigma_s: every factor lies in (0, 1) and the product
+    // neither overflows nor underflows to 0/0 when the c span many decades.
     for (int s = 0; s < ns; ++s) {
         const double sg = c[2 * s + 1];
         double r = 1.0;
-        for (int i = 1; i < ns; ++i) r *= c[2 * i] - sg;
-        for (int t = 0; t < ns; ++t)
-            if (t != s) r /= c[2 * t + 1] - sg;
+        for (int i = 1; i < ns; ++i) {
+            const double pole = i <= s ? c[2 * (i - 1) + 1] : c[2 * i + 1];
+            r *= (c[2 * i] - sg) / (pole - sg);
+        }
         sigma[s] = sg;
         omega[s] = r;
     }
     // the error alternates at x_j = eps / dn(j K / (2 ns)), j = 0..2 ns (past K/2:
-    // dn(K - u') = eps / dn(u'), so x_j = dn(u')); D centres it at x_0 and x_1
+    // x_j = dn(K - u_j)); D centres it at x_0 and x_1
     double p[2 * kMaxShifts + 1];
     for (int j = 0; j <= 2 * ns; ++j) {
-        double sn, cn, dn, x;
+        double sc, dn, x;
         if (2 * j <= 2 * ns) {
-            ellip_sncndn(g, j * K / (2.0 * ns), &sn, &cn, &dn);
+            z.sc_dn(j * Kp / (2.0 * ns), &sc, &dn);
             x = eps / dn;
         } else {
-            ellip_sncndn(g, (2 * ns - j) * K / (2.0 * ns), &sn, &cn, &dn);
+            z.sc_dn((2 * ns - j) * Kp / (2.0 * ns), &sc, &dn);
             x = dn;
         }
         double acc = 0.0;
@@ -264,9 +288,7 @@ int fa_zolotarev_poles(int ns, double eps, double* omega, double* sigma, double*
     const double d0 = std::fabs(D * p[0] - 1.0);
     // self-check: residues positive, and the error equal in size (to 1 % above the
     // rounding level of about 1e-12) with alternating signs at every alternation
-    // point.  With more poles than double precision resolves at this eps (small eps
-    // puts cn near 0 in the middle of the range, where it loses digits), the
-    // residues lose theirs and the check fails.
+    // point.  A pole set that double precision does not resolve fails it.
     const double floor_err = 1e-12;
     bool ok = std::isfinite(D) && D > 0.0;
     for (int s = 0; s < ns; ++s) ok = ok && omega[s] > 0.0 && std::isfinite(omega[s]);
