@@ -172,6 +172,33 @@ def golden_outer_iters(name, tol=1e-9):
     return (best[1], best[2]) if best else (None, None)
 
 
+def oracle_site_samples(name):
+    """y* of the workload at sampled sites (all 12 spin-colour components of 48
+    sites in every time slice), stored by tests/golden/make_golden.py --sites
+    from the FP64 oracle at tol 1e-12; None when no such file exists."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_sites.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        g = json.load(f)
+    idx = np.asarray(g["site_index_tzyx"])
+    want = np.asarray(g["y_re"]) + 1j * np.asarray(g["y_im"])
+    return {"index": idx, "y": want, "tol": g["tol"], "entries": int(want.size),
+            "source": f"tests/golden/{name}_sites.json (FP64 oracle, tol {g['tol']:g})"}
+
+
+def err_vs_oracle(y, samples):
+    """Relative 2-norm of y - y* over the stored oracle samples, and max |dy| / max |y*|."""
+    if samples is None:
+        return None
+    idx = samples["index"]
+    yy = np.asarray(y)[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]].reshape(len(idx), 12)
+    d = yy - samples["y"]
+    return {"rel_2norm": float(np.linalg.norm(d) / np.linalg.norm(samples["y"])),
+            "max_abs_over_max": float(np.abs(d).max() / np.abs(samples["y"]).max()),
+            "entries": samples["entries"], "reference": samples["source"]}
+
+
 def cpu_model():
     """The host CPU's model name (lscpu), else the machine type."""
     import platform
@@ -185,11 +212,33 @@ def cpu_model():
     return platform.machine()
 
 
+def oracle_anchor(name="wilson_4x4x4x8", tol=1e-10):
+    """One whole double-pass solve of the FP64 oracle, timed end to end (no
+    extrapolation): the power-iteration scale c, then f(A) b."""
+    import inputs
+    from oracle import dirac, msbicgstab as ms, poles, scale
+    w = inputs.make_workload(name)
+    t0 = time.perf_counter()
+    op = dirac.Operator(w["U"], w["mass"], w["mu"], 1.0, w["t_bc"])
+    c = scale.power_scale(op.A, w["v0"], 100)
+    op = dirac.Operator(w["U"], w["mass"], w["mu"], c, w["t_bc"])
+    om, sg = poles.neuberger_poles(w["ns"])
+    st = ms.Stats()
+    t1 = time.perf_counter()
+    ms.multishift_double(op.A, w["b"], sg, om, w["ell"], tol, stats=st)
+    t2 = time.perf_counter()
+    return {"workload": name, "tol": tol, "solve_ms": (t2 - t1) * 1e3, "scale_ms": (t1 - t0) * 1e3,
+            "outer_iters": st.n_outer, "extrapolated": False,
+            "what": "one whole FP64 oracle double-pass solve, timed end to end"}
+
+
 def cpu_baseline(w, c, outer_ref, outer=2, ref_tol=None):
     t = oracle_sample(w, c, outer)
     per_solve_ms = t / outer * 2 * outer_ref * 1e3
     at = f" (the oracle's own count at tol {ref_tol:g})" if ref_tol else ""
     return {"value": per_solve_ms, "unit": "ms", "cores": oracle_sample.threads, "kind": "oracle",
+            "extrapolated": True, "per_outer_iteration_ms": t / outer * 1e3,
+            "outer_iterations_scaled_to": 2 * outer_ref, "anchor": oracle_anchor(),
             "sample": f"{outer} outer iterations of the FP64 numpy oracle's BiCGstab({w['ell']}) "
                       f"recurrence on {'x'.join(map(str, w['dims']))} ({t:.1f} s), scaled by "
                       f"2 x {outer_ref} outer iterations{at} (pass 1 + pass 2 of the double-pass form); "
@@ -219,6 +268,8 @@ def run_reference(args, ws, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args.workload, w),
         "cpu_baseline": {"value": per_solve, "unit": "ms", "cores": oracle_sample.threads, "kind": "oracle",
+                         "extrapolated": True, "per_outer_iteration_ms": statistics.mean(ts) * 1e3,
+                         "outer_iterations_scaled_to": 2 * outer_ref, "anchor": oracle_anchor(),
                          "sample": (f"each step: 1 outer iteration of the FP64 numpy oracle's "
                                     f"BiCGstab({w['ell']}) recurrence, scaled by 2 x {outer_ref} outer "
                                     f"iterations (both passes of the oracle's double-pass solve; "
@@ -439,12 +490,18 @@ def main():
     b = torch.from_numpy(w["b"]).cuda()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    # reference solution for the error measurement (untimed)
+    # reference solutions for the error measurement (untimed): the library's own
+    # FP64 solve at tol 1e-12 on the whole lattice, and the FP64 oracle's y* at
+    # the sampled sites stored with the tests (when the workload has them)
     yref = ctx.apply_f(b, ell=ell, tol=1e-12, max_outer=4000, precision="f64").y
     yref_norm = torch.linalg.vector_norm(yref).item()
+    samples = oracle_site_samples(args.workload)
 
     def err(y):
         return (torch.linalg.vector_norm(y - yref) / yref_norm).item()
+
+    def err_o(y):
+        return err_vs_oracle(y.cpu().numpy(), samples)
 
     if args.switch_resid < 0:
         args.switch_resid = 0.08 / ell ** 2
@@ -479,7 +536,9 @@ def main():
             r = ctx.apply_f(b, ell=ell, tol=tol, max_outer=4000, check=False, **kw)
             e = err(r.y) if r.stats["status"] == 0 else float("inf")
             pick = (tol, e, r.stats)
-            if e <= TARGET:
+            # the headline must also meet the target against the oracle's samples
+            eo = err_o(r.y) if (name == "pseudo_mixed" and samples is not None) else None
+            if e <= TARGET and (eo is None or eo["rel_2norm"] <= TARGET):
                 break
         chosen[name] = pick
 
@@ -568,13 +627,17 @@ def main():
         except Exception as ex:   # reported, never fatal to the bench line
             other["overlap_pseudo_mixed"] = {"error": f"{type(ex).__name__}: {ex}"}
     other["pseudo_mixed_events"] = {"ms": statistics.mean(inst_ms), "note": "direct launches, hop events on"}
-    other["pseudo_mixed"] = {"ms": ms_step, "tol": tol_h, "rel_err": e_h,
+    head_vs_oracle = err_o(head_res.y)
+    other["pseudo_mixed"] = {"ms": ms_step, "tol": tol_h, "rel_err": e_h, "rel_err_vs_oracle": head_vs_oracle,
+                             "rel_err_reference": "rel_err: the library's FP64 solve at tol 1e-12, whole lattice; "
+                                                  "rel_err_vs_oracle: the FP64 oracle's y* at the stored samples",
                              "outer_iters": head_res.stats["outer_iters"],
                              "stored_outer": head_res.stats["stored_outer"],
                              "switch_outer": head_res.stats["switch_outer"], "meets_1e-8": e_h <= TARGET}
 
     if args.quick:
         print(json.dumps({"mode": "quick", "ms_per_solve": ms_step, "variant": other["pseudo_mixed"],
+                          "rel_err_vs_oracle": head_vs_oracle,
                           "hop_f32_ms": hop32_ms, "hop_f32_dot_ms": hop32d_ms, "hop_f64_ms": hop64_ms,
                           "hop_df_ms": hopdf_ms, "hop_df_dot_ms": hopdfd_ms,
                           "hop_f32_gbs": 384.0 * V / (hop32_ms * 1e-3) / 1e9 if hop32_ms else None,
@@ -600,6 +663,7 @@ def main():
         if i >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
     e2e_err = float(np.linalg.norm(y_pin.numpy() - yref.cpu().numpy()) / yref_norm)
+    e2e_err_o = err_vs_oracle(y_pin.numpy(), samples)
 
     # rooflines of the sweep kernels, each template instance on its own (the
     # plain sweep and the sweep that also forms <rt, out> and runs a seed step
@@ -645,11 +709,19 @@ def main():
     # DRAM traffic per launch from one ncu capture of the same kernels in the
     # timed solve on this lattice (dram__bytes_read.sum + dram__bytes_write.sum;
     # means over 10 + 6 FP32 and 30 + 18 double-float launches)
+    # (constants from that capture, applied only on its lattice; null elsewhere)
+    src = ("ncu capture (dram__bytes_read.sum + dram__bytes_write.sum per launch) of these kernels inside "
+           "the 16^3x32 headline solve, profiles/hop_traffic_16x16x16x32.md; fixed constants, not "
+           "re-measured by this run")
+    for r_ in (roof32, roof32d, roof64, roofdf, roofdfd):
+        r_["traffic_source"] = None
     if V == 16 * 16 * 16 * 32:
         roof32["traffic"] = 37.776e6 + 0.001e6
         roof32d["traffic"] = 50.415e6 + 0.029e6
         roofdf["traffic"] = 102.530e6 + 7.053e6
         roofdfd["traffic"] = 128.135e6 + 10.071e6
+        for r_ in (roof32, roof32d, roofdf, roofdfd):
+            r_["traffic_source"] = src
     roofs = [roof32, roof32d, roof64, roofdf, roofdfd]
     dominant = max(roofs, key=lambda r: r["total_ms"])
 
@@ -670,7 +742,9 @@ def main():
         "roofline_hop_df_dot": roofdfd,
         "stencil_gbs": achieved,
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": int(b_pin.numel() * 16),
-                "d2h_bytes_per_step": int(y_pin.numel() * 16), "rel_err": e2e_err},
+                "d2h_bytes_per_step": int(y_pin.numel() * 16), "rel_err": e2e_err,
+                "rel_err_vs_oracle": e2e_err_o},
+        "rel_err_vs_oracle": head_vs_oracle,
         "fp32_sweep_shape": {"chosen": ["auto", "wide", "narrow"][tune["shape"]],
                              "ms_per_launch_wide_narrow": tune["times_ms"]},
         "gpu_launches": head_launches // max(1, args.steps),

@@ -33,7 +33,7 @@ EXPORTS = (
     "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
     "fa_set_poles", "fa_neuberger_poles", "fa_zolotarev_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
     "fa_apply_f", "fa_apply_sign", "fa_apply_overlap", "fa_apply_sign_deflated", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
-    "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
+    "fa_hop_timing_split", "fa_hop_timing_reset", "fa_fused_timing", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune",
 )
@@ -119,6 +119,7 @@ def load_library(path=LIB_PATH):
         "fa_hop_timing": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_split": (I, [P, I, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_reset": (I, [P]),
+        "fa_fused_timing": (I, [P, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
         "fa_set_hop_shape": (I, [P, I]),
         "fa_get_hop_shape": (I, [P]),
@@ -286,11 +287,11 @@ class Context:
     @staticmethod
     def params(ell=2, tol=1e-10, max_outer=2000, mode="double", precision="f64",
                switch_resid=0.0, timing=False, hop_timing=False, store_gb=0.0, graph=False,
-               reliable_every=0, fixed_iters=False, overlap=True):
+               reliable_every=0, fixed_iters=False, overlap=True, fused=True):
         return SolverParams(int(ell), float(tol), int(max_outer), _MODE[mode], _PREC[precision],
                             float(switch_resid),
                             (1 if timing else 0) | (2 if hop_timing else 0) | (4 if graph else 0)
-                            | (8 if fixed_iters else 0) | (0 if overlap else 16),
+                            | (8 if fixed_iters else 0) | (0 if overlap else 16) | (0 if fused else 32),
                             float(store_gb), int(reliable_every))
 
     def apply_f(self, b, out=None, check=True, **kw):
@@ -397,6 +398,14 @@ class Context:
         with_dot = -1 if dot is None else int(bool(dot))
         _check(self.lib.fa_hop_timing_split(self.h, _PREC[precision], with_dot, ctypes.byref(ms),
                                             ctypes.byref(n)), "fa_hop_timing_split")
+        return ms.value, n.value
+
+    def fused_timing(self):
+        """Mean event-timed ms of the 4l fused FP32 sweeps of one outer iteration
+        (timed as one run) and how many outer iterations were timed."""
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(self.lib.fa_fused_timing(self.h, ctypes.byref(ms), ctypes.byref(n)), "fa_fused_timing")
         return ms.value, n.value
 
     def device_bytes(self):

@@ -487,7 +487,7 @@ int fa_device_bytes(const fa_ctx* c, unsigned long long* field_bytes, unsigned l
     // lattice-sized buffers: links, spinors, stores, staging, reduction partials
     const fa::DevBuf* field[] = {&c->links64, &c->links32, &c->linksdf, &c->io64a, &c->io64b, &c->io32a,
                                  &c->io32b, &c->tmp64, &c->tmp32, &c->partials, &c->r64, &c->u64, &c->rt64,
-                                 &c->r32, &c->u32, &c->rt32, &c->y64, &c->xs64, &c->us64, &c->bhost_dev,
+                                 &c->r32, &c->u32, &c->rt32, &c->r32a, &c->u32a, &c->y64, &c->xs64, &c->us64, &c->bhost_dev,
                                  &c->yhost_dev, &c->gx, &c->gpart, &c->store64, &c->store32, &c->snap64,
                                  &c->snap32, &c->xrel, &c->brel, &c->snapx, &c->defl};
     // scalars: solver state, shifts, records, pass-2 weights, batch descriptors
@@ -522,9 +522,16 @@ int fa_hop_timing(const fa_ctx* c, int precision, double* mean_ms, long long* co
     return fa_hop_timing_split(c, precision, -1, mean_ms, count);
 }
 
+int fa_fused_timing(const fa_ctx* c, double* mean_ms, long long* count) {
+    if (!c || !mean_ms || !count) return FA_EINVAL;
+    *count = c->hop_count[6];
+    *mean_ms = c->hop_count[6] ? c->hop_ms[6] / (double)c->hop_count[6] : 0.0;
+    return FA_OK;
+}
+
 int fa_hop_timing_reset(fa_ctx* c) {
     if (!c) return FA_EINVAL;
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 7; ++k) {
         c->hop_ms[k] = 0.0;
         c->hop_count[k] = 0;
     }

@@ -92,7 +92,7 @@ static int launch_hop_t(const Geom& g, const LP* links, const SP* in, SP* out, d
         else if (!g5in && !g5out && dot) FA_HOPN(false, false, true);
         else return FA_EINVAL;
 #undef FA_HOPN
-        return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA;
+        return launch_status("hop kernel");
       }
     }
     const int nb = nblocks(g.V);
@@ -104,7 +104,7 @@ static int launch_hop_t(const Geom& g, const LP* links, const SP* in, SP* out, d
     else if (!g5in && !g5out && dot) FA_HOP(false, false, true);
     else return FA_EINVAL;
 #undef FA_HOP
-    return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA;
+    return launch_status("hop kernel");
 }
 
 int launch_hop_f64(const Geom& g, const double2* links, const double2* in, double2* out, double diag,
@@ -133,7 +133,7 @@ int launch_hop_df(const Geom& g, const float4* links, const float4* in, float4* 
     else if (!g5in && !g5out && dot) FA_HOPD(false, false, true);
     else return FA_EINVAL;
 #undef FA_HOPD
-    return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA;
+    return launch_status("hop kernel");
 }
 
 int launch_hop_f32(const Geom& g, const float4* links, const float4* in, float4* out, double diag,
@@ -242,7 +242,7 @@ int launch_force(const Geom& g, const double2* links, const double2* a1, const d
     SpinorView<double> va2{const_cast<double2*>(a2), g.V}, vb2{const_cast<double2*>(b2), g.V};
     k_force<<<nblocks(g.V), kThreads, 0, st>>>(g, U, va1, vb1, va2, vb2, (double2*)G_canon, w, ef, eb, t_bc,
                                                 partials);
-    return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA;
+    return launch_status("hop kernel");
 }
 
 // ------------------------------------------------------------------ layout conversions
@@ -317,27 +317,26 @@ __global__ void pack_links_kernel(int V, const double2* __restrict__ canon, doub
 }
 
 static int grid_for(size_t n) { return (int)((n + kThreads - 1) / kThreads); }
-static int last_status() { return cudaGetLastError() == cudaSuccess ? FA_OK : FA_ECUDA; }
 
 int launch_pack_spinor_f64(const Geom& g, const double* canon, double2* out, cudaStream_t st) {
     pack_f64_kernel<<<grid_for((size_t)12 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, out);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 int launch_unpack_spinor_f64(const Geom& g, const double2* in, double* canon, cudaStream_t st) {
     unpack_f64_kernel<<<grid_for((size_t)12 * g.V), kThreads, 0, st>>>(g.V, in, (double2*)canon);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 int launch_pack_spinor_f32(const Geom& g, const double* canon, float4* out, cudaStream_t st) {
     pack_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, out);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 int launch_unpack_spinor_f32(const Geom& g, const float4* in, double* canon, cudaStream_t st) {
     unpack_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, in, (double2*)canon);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 int launch_pack_links(const Geom& g, const double* canon, double2* l64, float4* l32, float4* ldf, cudaStream_t st) {
     pack_links_kernel<<<grid_for((size_t)4 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, l64, l32, ldf);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 
 __global__ void pack_df_kernel(int V, const double2* __restrict__ canon, float4* __restrict__ out) {
@@ -366,19 +365,19 @@ __global__ void convert_df_f32_kernel(int V, const float4* __restrict__ in, floa
 
 int launch_pack_spinor_df(const Geom& g, const double* canon, float4* out, cudaStream_t st) {
     pack_df_kernel<<<grid_for((size_t)12 * g.V), kThreads, 0, st>>>(g.V, (const double2*)canon, out);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 int launch_unpack_spinor_df(const Geom& g, const float4* in, double* canon, cudaStream_t st) {
     unpack_df_kernel<<<grid_for((size_t)12 * g.V), kThreads, 0, st>>>(g.V, in, (double2*)canon);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 int launch_convert_df_to_f32(const Geom& g, const float4* in, float4* out, cudaStream_t st) {
     convert_df_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, in, out);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 int launch_convert_f64_to_f32(const Geom& g, const double2* in, float4* out, cudaStream_t st) {
     convert_f64_f32_kernel<<<grid_for((size_t)6 * g.V), kThreads, 0, st>>>(g.V, in, out);
-    return last_status();
+    return launch_status("layout conversion kernel");
 }
 
 }  // namespace fa

@@ -36,13 +36,18 @@ struct DevBuf {
     template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
-// an instantiated outer iteration, keyed by what its launches depend on
+// An instantiated outer iteration.  (key, L, dev, n, V) select the entry;
+// `sig` holds every value that the captured launches took as a kernel
+// argument and that can change between solves on the same context (buffer
+// addresses, operator scalars, link pointer, launch shape, launch attributes).
+// An entry whose signature differs from the current one is re-captured.
 struct GraphEntry {
     int key, L;
     void* dev;
     int n, V;
     cudaGraphExec_t exec;
     long long kernels;
+    std::vector<unsigned long long> sig;
 };
 
 void set_error(const char* fmt, ...);
@@ -76,6 +81,7 @@ struct fa_ctx {
     fa::DevBuf prec, coef, cs;           // per-shift record, pass-2 weights, sweep output
     fa::DevBuf coef4;                    // pass-2 weights as FP32 pairs (gathers of FP32 / double-float stores)
     fa::DevBuf r64, u64, rt64, r32, u32, rt32;   // seed vectors (l+1 each, contiguous)
+    fa::DevBuf r32a, u32a;               // fused FP32 sweeps: alternate buffers of r_j, u_j (j < l)
     fa::DevBuf y64;                      // accumulated result (FP64 internal)
     fa::DevBuf xs64, us64;               // single-pass shift vectors
     fa::DevBuf bhost_dev, yhost_dev;     // canonical staging for fa_apply_f_host
@@ -91,9 +97,10 @@ struct fa_ctx {
 
     long long launches = 0;
     // hop-kernel timing: index FP64 0, FP32 1, double-float 2; + 3 for the
-    // sweeps that also form <dot_with, out> (and run a scalar step in a solve)
-    double hop_ms[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    long long hop_count[6] = {0, 0, 0, 0, 0, 0};
+    // sweeps that also form <dot_with, out> (and run a scalar step in a solve);
+    // 6: the 4l fused FP32 sweeps of one outer iteration, timed as one run
+    double hop_ms[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    long long hop_count[7] = {0, 0, 0, 0, 0, 0, 0};
     bool hop_timing = false;
     int hop_shape = 0;                   // FP32 sweep launch shape (fa_hop_shape; 0: automatic)
     std::vector<cudaEvent_t> hop_ev;     // start/stop pairs, reused across solves

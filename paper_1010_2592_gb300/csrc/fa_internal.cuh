@@ -387,6 +387,14 @@ struct OpParams {
 };
 
 // ------------------------------------------------------------------ host-side API of the kernels
+// Records "what: <CUDA error>" as the library's last error and returns FA_ECUDA.
+int cuda_fail(cudaError_t e, const char* what);
+// FA_OK after a launch, else the launch error recorded by cuda_fail.
+inline int launch_status(const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FA_OK : cuda_fail(e, what);
+}
+
 // Hop (one D_w sweep): out = scale * G5OUT * (diag*in' - 1/2 sum hops(in')),
 // in' = G5IN ? gamma_5 in : in, time weights from `mu_sign` * mu.
 // When dot_with != nullptr, per-block partials of <dot_with, out> are written

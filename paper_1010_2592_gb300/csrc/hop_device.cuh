@@ -68,8 +68,10 @@ __device__ __forceinline__ void recon_add(cx<R> acc[12], const cx<R> h[6]) {
     for (int c = 0; c < 3; ++c) recon1<MU, S>(acc[c], acc[3 + c], acc[6 + c], acc[9 + c], h[c], h[3 + c]);
 }
 
-template <typename R, bool G5IN>
-__device__ __forceinline__ void load_in(const SpinorView<R>& in, int s, cx<R> p[12]) {
+// `in` is any spinor view with load(site, cx<R>[12]): a stored spinor, or a
+// linear combination of two formed as it is read (the solver's fused sweeps)
+template <typename R, bool G5IN, typename SV>
+__device__ __forceinline__ void load_in(const SV& in, int s, cx<R> p[12]) {
     in.load(s, p);
     if (G5IN) {
 #pragma unroll
@@ -78,8 +80,8 @@ __device__ __forceinline__ void load_in(const SpinorView<R>& in, int s, cx<R> p[
 }
 
 // forward hop from site s to neighbour nb: acc += w (1 - g_MU) U_MU(s) psi(nb)
-template <int MU, bool WEIGHT, bool G5IN, typename R>
-__device__ __forceinline__ void hop_fwd(cx<R> acc[12], const SpinorView<R>& in, const LinkView<R>& U,
+template <int MU, bool WEIGHT, bool G5IN, typename R, typename SV>
+__device__ __forceinline__ void hop_fwd(cx<R> acc[12], const SV& in, const LinkView<R>& U,
                                         int s, int nb, R w) {
     cx<R> p[12], h[6], L[3][3], c[6];
     load_in<R, G5IN>(in, nb, p);
@@ -98,8 +100,8 @@ __device__ __forceinline__ void hop_fwd(cx<R> acc[12], const SpinorView<R>& in, 
 }
 
 // backward hop: acc += w (1 + g_MU) U_MU(nb)^H psi(nb), nb = s - MU
-template <int MU, bool WEIGHT, bool G5IN, typename R>
-__device__ __forceinline__ void hop_bwd(cx<R> acc[12], const SpinorView<R>& in, const LinkView<R>& U,
+template <int MU, bool WEIGHT, bool G5IN, typename R, typename SV>
+__device__ __forceinline__ void hop_bwd(cx<R> acc[12], const SV& in, const LinkView<R>& U,
                                         int nb, R w) {
     cx<R> p[12], h[6], L[3][3], c[6];
     load_in<R, G5IN>(in, nb, p);
@@ -119,9 +121,10 @@ __device__ __forceinline__ void hop_bwd(cx<R> acc[12], const SpinorView<R>& in, 
 
 // out = scale * G5OUT * ((4+m) in'(s) - 1/2 sum hops(in')), in' = G5IN ? g5 in : in;
 // cdiag = scale*(4+m), chop = -scale/2, ef/eb = e^{+-mu}, bc = time-boundary sign.
-template <typename R, bool G5IN, bool G5OUT>
-__device__ __forceinline__ void hop_site(const Geom& g, const LinkView<R>& U, const SpinorView<R>& in, int s,
-                                         R cdiag, R chop, R ef, R eb, R bc, cx<R> p[12]) {
+// PIN: pin receives in'(s), the input at the site itself.
+template <typename R, bool G5IN, bool G5OUT, bool PIN = false, typename SV>
+__device__ __forceinline__ void hop_site(const Geom& g, const LinkView<R>& U, const SV& in, int s,
+                                         R cdiag, R chop, R ef, R eb, R bc, cx<R> p[12], cx<R>* pin = nullptr) {
     const int X = g.X, Y = g.Y, Z = g.Z, T = g.T;
     const int x = s % X;
     const int r1 = s / X;
@@ -144,6 +147,10 @@ __device__ __forceinline__ void hop_site(const Geom& g, const LinkView<R>& U, co
     hop_fwd<3, true, G5IN>(acc, in, U, s, (t == T - 1) ? s - (T - 1) * sT : s + sT, wf);
     hop_bwd<3, true, G5IN>(acc, in, U, (t == 0) ? s + (T - 1) * sT : s - sT, wb);
     load_in<R, G5IN>(in, s, p);
+    if constexpr (PIN) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) pin[k] = p[k];
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
         const bool neg = G5OUT && k >= 6;

@@ -17,6 +17,7 @@
 // overlap on a GPU (other streams, other contexts on the same device) race
 // on it and must be serialised by the caller.  Nothing in it needs clearing
 // between calls: each call writes every element it later reads.
+#include <cmath>
 #include <mutex>
 
 #include "fa_context.h"
@@ -77,15 +78,19 @@ extern "C" int fa_apply_A_noalloc(fa_ctx* c, const double* in, double* out, int 
     if (rc != FA_OK) return rc;
     double2* a = scratch;                                   // packed input, later the packed result
     double2* t = scratch + (size_t)12 * kNoAllocMaxSites;   // g5 D in
-    const bool dg = dagger != 0;
+    // A = c g5 D g5 D; A^H = A(-mu).  The hop kernels are launched directly,
+    // so the call leaves the context's solver state and timing untouched.
+    const double mu = dagger != 0 ? -c->mu : c->mu;
+    const double ef = std::exp(mu), eb = std::exp(-mu), diag = 4.0 + c->mass;
     rc = launch_pack_spinor_f64(c->g, in, a, c->stream);
-    if (rc != FA_OK) return cuda_fail(cudaGetLastError(), "fa_apply_A_noalloc: pack");
-    rc = hop_f64(c, a, t, 1.0, false, true, dg, nullptr, nullptr, nullptr);
-    if (rc != FA_OK) return rc;
-    rc = hop_f64(c, t, a, c->scale_c, false, true, dg, nullptr, nullptr, nullptr);
-    if (rc != FA_OK) return rc;
-    rc = launch_unpack_spinor_f64(c->g, a, out, c->stream);
-    if (rc != FA_OK) return cuda_fail(cudaGetLastError(), "fa_apply_A_noalloc: unpack");
-    c->launches += 2;
+    if (rc == FA_OK)
+        rc = launch_hop_f64(c->g, links64_of(c), a, t, diag, ef, eb, c->t_bc, 1.0, false, true, nullptr, nullptr,
+                            nullptr, c->stream);
+    if (rc == FA_OK)
+        rc = launch_hop_f64(c->g, links64_of(c), t, a, diag, ef, eb, c->t_bc, c->scale_c, false, true, nullptr,
+                            nullptr, nullptr, c->stream);
+    if (rc == FA_OK) rc = launch_unpack_spinor_f64(c->g, a, out, c->stream);
+    if (rc != FA_OK) return rc;   // the launch error is recorded for fa_last_error
+    c->launches += 4;
     return FA_OK;
 }

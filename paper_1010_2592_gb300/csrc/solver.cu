@@ -8,13 +8,14 @@
 // runs in the kernels of solver_kernels.cuh and dslash.cu; the host only
 // enqueues them and polls a done flag.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <algorithm>
 #include <vector>
 #include <type_traits>
 
 #include "fa_context.h"
-#include "solver_kernels.cuh"
+#include "fused_sweep.cuh"
 
 namespace fa {
 
@@ -75,7 +76,6 @@ int hop_f64(fa_ctx* c, const double2* in, double2* out, double scale, bool g5in,
                             c->t_bc, scale, g5in, g5out, dot_with, partials, done, c->stream);
     hop_timing_end(c);
     c->launches++;
-    if (rc == FA_ECUDA) return cuda_fail(cudaGetLastError(), "hop_f64");
     return rc;
 }
 
@@ -87,7 +87,6 @@ int hop_f32(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, b
                             c->t_bc, scale, g5in, g5out, dot_with, partials, done, c->stream, c->hop_shape);
     hop_timing_end(c);
     c->launches++;
-    if (rc == FA_ECUDA) return cuda_fail(cudaGetLastError(), "hop_f32");
     return rc;
 }
 
@@ -99,7 +98,6 @@ int hop_df(fa_ctx* c, const float4* in, float4* out, double scale, bool g5in, bo
                            g5in, g5out, dot_with, partials, done, c->stream);
     hop_timing_end(c);
     c->launches++;
-    if (rc == FA_ECUDA) return cuda_fail(cudaGetLastError(), "hop_df");
     return rc;
 }
 
@@ -185,6 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_lincomb_canon(int n, int k, const 
 struct Layout {
     int L, ns, max_outer, V;
     bool need64, need32, single;
+    bool fused;                // FP32 stretches run the fused sweeps (one system, l <= 4)
     size_t vs64, vs32;         // one spinor in elements of double2 / float4
     int nblk, red_grid, part_slots;
     int vgrid;                 // balanced vector kernels: kVecBlocks per SM
@@ -199,8 +198,11 @@ static int red_grid_for(int V) { return std::min(nblocks(V), 8 * sms()); }
 static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
     const int V = Lo.V, L = Lo.L, ns = c->ns, MO = Lo.max_outer;
     const size_t s64 = (size_t)12 * V * sizeof(double2), s32 = (size_t)6 * V * sizeof(float4);
-    FA_CUDA(c->partials.ensure(std::max((size_t)std::max({Lo.nblk, Lo.red_grid, Lo.vgrid + 1}) * Lo.part_slots,
-                                        (size_t)row_blocks(V)) * sizeof(double2)),
+    // the fused Gram epilogue writes n_gram(l) partials per block of the FP32 sweep
+    const size_t hop_blk = (size_t)std::max(nblocks(V), (V + kHopNarrowThreads - 1) / kHopNarrowThreads) + 1;
+    FA_CUDA(c->partials.ensure(std::max({(size_t)std::max({Lo.nblk, Lo.red_grid, Lo.vgrid + 1}) * Lo.part_slots,
+                                         (size_t)row_blocks(V), hop_blk * (size_t)Lo.part_slots}) *
+                               sizeof(double2)),
             "alloc partials");
     FA_CUDA(c->state.ensure(sizeof(DevState)), "alloc state");
     FA_CUDA(c->shiftbuf.ensure((size_t)kMaxShifts * (2 * sizeof(double) + 2 * sizeof(double2) + 2 * sizeof(int))),
@@ -218,6 +220,10 @@ static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
         FA_CUDA(c->tmp64.ensure(s64), "alloc tmp64");
     }
     if (Lo.need32) {
+        if (Lo.fused) {
+            FA_CUDA(c->r32a.ensure((size_t)L * s32), "alloc r32 alternates");
+            FA_CUDA(c->u32a.ensure((size_t)L * s32), "alloc u32 alternates");
+        }
         FA_CUDA(c->r32.ensure((L + 1) * s32), "alloc r32");
         FA_CUDA(c->u32.ensure((L + 1) * s32), "alloc u32");
         FA_CUDA(c->rt32.ensure(s32), "alloc rt32");
@@ -273,6 +279,8 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     d.u32 = c->u32.as<float4>();
     d.rt32 = c->rt32.as<float4>();
     d.tmp32 = c->tmp32.as<float4>();
+    d.r32a = Lo.fused ? c->r32a.as<float4>() : nullptr;
+    d.u32a = Lo.fused ? c->u32a.as<float4>() : nullptr;
     d.y = c->y64.as<double2>();
     d.xs = Lo.single ? c->xs64.as<double2>() : nullptr;
     d.us = Lo.single ? c->us64.as<double2>() : nullptr;
@@ -302,6 +310,8 @@ struct Batch {
     bool pdl = true;                      // programmatic dependent launch inside an outer iteration
 };
 
+template <int L> static int enqueue_outer_fused(Batch& B, bool pass2, bool reliable);
+
 // Kernel launch, with programmatic stream serialization when `pdl` is set: the
 // kernel may then be placed on the SMs while its predecessor (a kernel) finishes,
 // and it waits in dep_sync() before its first memory access.  Used only for
@@ -327,6 +337,8 @@ static int upload(Batch& B) {
     return FA_OK;
 }
 
+static inline ScalarStep none_step() { return ScalarStep{STEP_NONE, 0}; }
+
 // working precision of a stretch of outer iterations
 enum Rp { RP64 = 0, RP32 = 1, RPDF = 2 };
 template <typename R> constexpr int rp_of() {
@@ -340,6 +352,9 @@ template <typename R> constexpr int rp_of() {
 // Each launch covers the whole batch (grid.y = systems).
 template <typename R, int L>
 static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reliable) {
+    if constexpr (rp_of<R>() == RP32 && L <= 4) {
+        if (B.Lo.fused && !single) return enqueue_outer_fused<L>(B, pass2, reliable);
+    }
     fa_ctx* c = B.c0;
     const int n = B.n, nb = B.Lo.nblk, rg = B.Lo.red_grid, vg = B.Lo.vgrid;
     const int p2 = pass2 ? 1 : 0;
@@ -485,8 +500,153 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
             rc = launch_hop_f64(h0.g, h0.links64, t1, t2, h0.diag, h0.ef, h0.eb, h0.bc, h0.scale, false, true,
                                 nullptr, nullptr, done, st);
         c->launches += 2;
-        if (rc != FA_OK) return cuda_fail(cudaGetLastError(), "reliable update");
+        if (rc != FA_OK) return rc;
         k_reliable<R><<<gv, kThreads, 0, st>>>(ds, t2, p2, conv);
+        FA_LAUNCHED(c, "k_reliable");
+    }
+    if (pass2) {
+        launch(pdl, k_advance, dim3(n), 1, st, ds);
+        FA_LAUNCHED(c, "k_advance");
+    }
+    return FA_OK;
+}
+
+// One FP32 outer iteration of a one-system double-pass solve with the fused
+// sweeps (fused_sweep.cuh): per BiCG sub-step j the four sweeps F1..F4, then the
+// MR kernel; 4l + 1 launches (+ the reliable update, + the pass-2 counter).
+// Buffers: home r_i, u_i (i <= l) in r32 / u32, alternates of r_j, u_j (j < l)
+// in r32a / u32a (see the file comment of fused_sweep.cuh).
+template <int L, int NT, int MB>
+static int enqueue_fused_sweeps(Batch& B, bool pass2, bool pdl_first, bool pdl) {
+    fa_ctx* c = B.c0;
+    const SolverDev& h = B.host[0];
+    const SolverDev* ds = B.dev;
+    cudaStream_t st = c->stream;
+    const int V = h.V;
+    const size_t vs = (size_t)6 * V;
+    auto rh = [&](int i) { return h.r32 + (size_t)i * vs; };
+    auto uh = [&](int i) { return h.u32 + (size_t)i * vs; };
+    auto ra = [&](int i) { return h.r32a + (size_t)i * vs; };
+    auto ua = [&](int i) { return h.u32a + (size_t)i * vs; };
+    const LinkView<float> U{h.links32, V};
+    const float ef = host_cvt<float>(h.ef), eb = host_cvt<float>(h.eb), bc = host_cvt<float>(h.bc);
+    const float cd1 = host_cvt<float>(1.0 * h.diag), ch1 = host_cvt<float>(-0.5 * 1.0);
+    const float cd2 = host_cvt<float>(h.scale * h.diag), ch2 = host_cvt<float>(-0.5 * h.scale);
+    const int nb = (V + NT - 1) / NT;
+    const int p2 = pass2 ? 1 : 0;
+    const ScalarStep none{STEP_NONE, 0};
+    bool first = true;
+    auto pd = [&]() {
+        const bool r = first ? pdl_first : pdl;
+        first = false;
+        return r;
+    };
+    for (int j = 0; j < L; ++j) {
+        // F1: tmp = g5 D (r_j - beta u_j); u_j -> alternate; u_i (i < j) at the own sites
+        FusedHop1 a{};
+        a.g = h.g;
+        a.U = U;
+        a.a = rh(j);
+        a.b = uh(j);
+        a.tmp = h.tmp32;
+        a.upd = ua(j);
+        for (int i = 0; i < j; ++i) {
+            a.cdst[i] = ua(i);
+            a.ca[i] = ra(i);
+            a.cb[i] = ua(i);
+        }
+        a.u0 = ua(0);
+        a.cdiag = cd1;
+        a.chop = ch1;
+        a.ef = ef;
+        a.eb = eb;
+        a.bc = bc;
+        a.j = j;
+        launch(pd(), k_fhop1<L, 0, false, false, NT, MB>, dim3(nb), NT, st, a, ds, p2);
+        FA_LAUNCHED(c, "k_fhop1 (u)");
+        // F2: u_{j+1} = c g5 D tmp, <rt, u_{j+1}>, alpha
+        FusedHop2 b{};
+        b.g = h.g;
+        b.U = U;
+        b.in = h.tmp32;
+        b.out = uh(j + 1);
+        b.rt = h.rt32;
+        b.part = h.part;
+        b.cdiag = cd2;
+        b.chop = ch2;
+        b.ef = ef;
+        b.eb = eb;
+        b.bc = bc;
+        if (pass2) launch(pd(), k_fhop2<L, 0, NT, MB>, dim3(nb), NT, st, b, ds, p2, none);
+        else launch(pd(), k_fhop2<L, 1, NT, MB>, dim3(nb), NT, st, b, ds, p2, ScalarStep{STEP_ALPHA, j});
+        FA_LAUNCHED(c, "k_fhop2 (u)");
+        // F3: tmp = g5 D (r_j - alpha u_{j+1}); r_j -> alternate; r_i (i < j);
+        // occurrences stored (pass 1) or summed into y (pass 2); shift block (pass 1)
+        a.a = rh(j);
+        a.b = uh(j + 1);
+        a.upd = ra(j);
+        for (int i = 0; i < j; ++i) {
+            a.cdst[i] = ra(i);
+            a.ca[i] = ra(i);
+            a.cb[i] = ua(i + 1);
+        }
+        if (pass2) launch(pd(), k_fhop1<L, 1, false, true, NT, MB>, dim3(nb), NT, st, a, ds, p2);
+        else launch(pd(), k_fhop1<L, 1, true, false, NT, MB>, dim3(nb + 1), NT, st, a, ds, p2);
+        FA_LAUNCHED(c, "k_fhop1 (r)");
+        // F4: r_{j+1} = c g5 D tmp; next beta, or the Gram matrix and gamma
+        b.out = rh(j + 1);
+        if (pass2) {
+            launch(pd(), k_fhop2<L, 0, NT, MB>, dim3(nb), NT, st, b, ds, p2, none);
+        } else if (j < L - 1) {
+            launch(pd(), k_fhop2<L, 1, NT, MB>, dim3(nb), NT, st, b, ds, p2, ScalarStep{STEP_BETA, j + 1});
+        } else {
+            for (int i = 0; i < L; ++i) b.gram[i] = ra(i);
+            launch(pd(), k_fhop2<L, 2, NT, MB>, dim3(nb), NT, st, b, ds, p2, none);
+        }
+        FA_LAUNCHED(c, "k_fhop2 (r)");
+    }
+    return FA_OK;
+}
+
+template <int L>
+static int enqueue_outer_fused(Batch& B, bool pass2, bool reliable) {
+    fa_ctx* c = B.c0;
+    const SolverDev& h0 = B.host[0];
+    const SolverDev* ds = B.dev;
+    cudaStream_t st = c->stream;
+    const int n = B.n, vg = B.Lo.vgrid, rg = B.Lo.red_grid;
+    const int p2 = pass2 ? 1 : 0;
+    // the 4l sweeps run back to back; with sweep timing on (direct launches)
+    // one event pair brackets them, so the first sweep follows the event
+    // record in plain stream order and the others keep programmatic launch
+    const bool timing = c->hop_timing && !B.use_graph;
+    if (timing) hop_timing_begin(c, 6);
+    const bool narrow = hop_use_narrow(c->hop_shape, h0.V);
+    int rc;
+    if (narrow) rc = enqueue_fused_sweeps<L, kHopNarrowThreads, kHopNarrowBlocks>(B, pass2, B.pdl && !timing, B.pdl);
+    else rc = enqueue_fused_sweeps<L, kThreads, FA_HOP_MINB>(B, pass2, B.pdl && !timing, B.pdl);
+    if (timing) hop_timing_end(c);
+    FA_TRY(rc);
+    const bool pdl = B.pdl && !timing;
+    const int mg = mr_min_blocks<float, L>() >= kVecBlocks ? vg : rg;
+    const dim3 gm(mg, n), gmx(mg + 1, n);
+    const ScalarStep conv = pass2 ? none_step() : ScalarStep{STEP_CONV, 0};
+    if (pass2) launch(pdl, k_mr<float, L, true, false, false, false, true>, gm, kThreads, st, ds, p2, none_step());
+    else launch(pdl, k_mr<float, L, false, false, true, true, true>, gmx, kThreads, st, ds, p2,
+                reliable ? none_step() : conv);
+    FA_LAUNCHED(c, "k_mr");
+    if (reliable) {
+        double2* t1 = c->io64a.as<double2>();
+        double2* t2 = c->io64b.as<double2>();
+        const int* done = pass2 ? nullptr : &h0.st->done;
+        int r = launch_hop_f64(h0.g, h0.links64, h0.x64, t1, h0.diag, h0.ef, h0.eb, h0.bc, 1.0, false, true,
+                               nullptr, nullptr, done, st);
+        if (r == FA_OK)
+            r = launch_hop_f64(h0.g, h0.links64, t1, t2, h0.diag, h0.ef, h0.eb, h0.bc, h0.scale, false, true,
+                               nullptr, nullptr, done, st);
+        c->launches += 2;
+        if (r != FA_OK) return r;
+        k_reliable<float><<<dim3(vg, n), kThreads, 0, st>>>(ds, t2, p2, conv);
         FA_LAUNCHED(c, "k_reliable");
     }
     if (pass2) {
@@ -514,18 +674,61 @@ static int enqueue_outer_direct(Batch& B, int rp, bool pass2, bool single, bool 
     }
 }
 
+// Everything the launches of one outer iteration take as kernel arguments
+// that is not part of the cache key: for a batch of one the stand-alone hop
+// kernel gets its vectors, links, reduction partials, state and the operator
+// scalars (4+m, e^{+-mu}, boundary sign, c) as parameters, and its launch shape;
+// the reliable update's FP64 hops read the scratch pair io64a/io64b.  A batch
+// reads its systems from the descriptor array, re-uploaded before every solve.
+static std::vector<unsigned long long> graph_signature(const Batch& B) {
+    std::vector<unsigned long long> s;
+    auto p = [&](const void* v) { s.push_back((unsigned long long)(uintptr_t)v); };
+    auto d = [&](double v) {
+        unsigned long long u;
+        std::memcpy(&u, &v, sizeof(u));
+        s.push_back(u);
+    };
+    const fa_ctx* c = B.c0;
+    s.push_back((unsigned long long)B.pdl);
+    s.push_back((unsigned long long)(long long)c->hop_shape);
+    p(c->io64a.p);
+    p(c->io64b.p);
+    if (B.n == 1) {
+        const SolverDev& h = B.host[0];
+        for (const void* v : {(const void*)h.st, (const void*)h.part, (const void*)h.links64,
+                              (const void*)h.links32, (const void*)h.linksdf, (const void*)h.r64,
+                              (const void*)h.u64, (const void*)h.rt64, (const void*)h.tmp64, (const void*)h.r32,
+                              (const void*)h.u32, (const void*)h.rt32, (const void*)h.tmp32, (const void*)h.x64,
+                              (const void*)h.b64, (const void*)h.r32a, (const void*)h.u32a})
+            p(v);
+        d(h.diag);
+        d(h.ef);
+        d(h.eb);
+        d(h.bc);
+        d(h.scale);
+    }
+    return s;
+}
+
 // One outer iteration, replayed from a captured CUDA graph when the batch
-// uses graphs (every argument of every launch is iteration-independent: the
-// kernels read m and their scalars from the device).
+// uses graphs (every launch argument is iteration-independent: the kernels
+// read m and their scalars from the device).  A cached graph whose launch
+// arguments no longer match the context (new mu, mass, scale, gauge field,
+// launch shape or reallocated buffers) is destroyed and captured again.
 static int enqueue_outer_any(Batch& B, int rp, bool pass2, bool single, bool head, bool rel = false) {
     if (!B.use_graph) return enqueue_outer_direct(B, rp, pass2, single, head, rel);
     fa_ctx* c = B.c0;
-    const int key = rp | (pass2 ? 4 : 0) | (single ? 8 : 0) | (head ? 16 : 0) | (rel ? 32 : 0);
+    const int key = rp | (pass2 ? 4 : 0) | (single ? 8 : 0) | (head ? 16 : 0) | (rel ? 32 : 0) |
+                    (B.Lo.fused ? 64 : 0);
+    std::vector<unsigned long long> sig = graph_signature(B);
     GraphEntry* ge = nullptr;
     for (auto& e : c->graphs)
-        if (e.key == key && e.L == B.Lo.L && e.dev == (void*)B.dev && e.n == B.n && e.V == B.Lo.V && e.exec)
-            ge = &e;
-    if (!ge) {
+        if (e.key == key && e.L == B.Lo.L && e.dev == (void*)B.dev && e.n == B.n && e.V == B.Lo.V) ge = &e;
+    if (ge && ge->sig != sig) {
+        if (ge->exec) cudaGraphExecDestroy(ge->exec);
+        ge->exec = nullptr;
+    }
+    if (!ge || !ge->exec) {
         const long long n0 = c->launches;
         cudaGraph_t g = nullptr;
         FA_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -537,9 +740,14 @@ static int enqueue_outer_any(Batch& B, int rp, bool pass2, bool single, bool hea
         e = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         FA_CUDA(e, "instantiate graph");
-        c->graphs.push_back(GraphEntry{key, B.Lo.L, (void*)B.dev, B.n, B.Lo.V, ex, c->launches - n0});
+        if (!ge) {
+            c->graphs.push_back(GraphEntry{key, B.Lo.L, (void*)B.dev, B.n, B.Lo.V, nullptr, 0, {}});
+            ge = &c->graphs.back();
+        }
+        ge->exec = ex;
+        ge->kernels = c->launches - n0;
+        ge->sig = std::move(sig);
         c->launches = n0;
-        ge = &c->graphs.back();
     }
     FA_CUDA(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
     c->launches += ge->kernels;
@@ -681,6 +889,9 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     // by HBM, not by the per-SM imbalance)
     Lo.vgrid = std::min(Lo.nblk, kVecBlocks * sms());
     Lo.part_slots = std::max(n_gram(L), 2);
+    // FP32 stretches of a one-system double-pass solve run the fused sweeps
+    // (flags bit 5 turns them off: the unfused kernels, for comparison)
+    Lo.fused = n == 1 && !single && L <= 4 && prec != FA_F64 && (p->flags & 32) == 0;
     for (auto* c : B.sys) FA_TRY(ensure_workspace(c, Lo));
     FA_CUDA(c0->descbuf.ensure((size_t)n * sizeof(SolverDev)), "alloc descriptors");
     FA_CUDA(c0->flagbuf.ensure((size_t)2 * n * sizeof(int)), "alloc flags");

@@ -28,6 +28,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d["higher_is_better"] is False and d["value"] > 0
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    # the value scales sampled outer iterations to a whole solve, and says so;
+    # the anchor is one whole oracle solve timed end to end
+    assert cb["extrapolated"] is True and cb["per_outer_iteration_ms"] > 0
+    assert cb["anchor"]["extrapolated"] is False and cb["anchor"]["solve_ms"] > 0
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "wilson_4x4x4x8"
 

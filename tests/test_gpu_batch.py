@@ -119,3 +119,51 @@ def test_batch_rejects_mixed_precision_for_several_systems():
     with pytest.raises(fa.FAError) as e:
         fa.apply_f_batched(ctxs[:3], srcs[:3], ell=2, precision="mixed")
     assert e.value.status == fa.FA_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "mixed_df"])
+def test_graph_cache_follows_context_changes(precision):
+    """A graph-replayed solve after a change of mu / mass / scale (fa_set_params),
+    of the gauge field, of the FP32 sweep shape or of l (which can reallocate the
+    seed vectors) equals a solve with direct launches under the new settings: no
+    cached outer iteration replays stale kernel arguments."""
+    import torch
+    w = workload_case("wilson_4x4x4x8")
+    stream = torch.cuda.Stream()
+    ctx = fa.Context(w["dims"], stream)
+    ctx.set_gauge(to_dev(w["U"]))
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], w["c"])
+    ctx.set_poles(w["omega"], w["sigma"])
+    with torch.cuda.stream(stream):
+        b = to_dev(w["b"])
+    stream.synchronize()
+    kw = dict(ell=2, tol=1e-10, mode="pseudo", precision=precision)
+
+    def same(**over):
+        k = dict(kw, **over)
+        g = to_host(ctx.apply_f(b, graph=True, **k).y)
+        d = to_host(ctx.apply_f(b, graph=False, **k).y)
+        stream.synchronize()
+        assert np.array_equal(g, d), over
+        return g
+
+    y0 = same()
+    ctx.set_params(w["mass"], 0.15, w["t_bc"], w["c"])           # new mu
+    y1 = same()
+    assert rel(y1, y0) > 1e-3
+    ctx.set_params(-1.7, 0.15, w["t_bc"], 0.9 * w["c"])           # new mass and scale
+    y2 = same()
+    assert rel(y2, y1) > 1e-3
+    U2 = inputs.su3_exp_gauge(w["dims"], 0.5, 777)
+    ctx.set_gauge(to_dev(U2))                                     # new gauge field
+    y3 = same()
+    assert rel(y3, y2) > 1e-3
+    ctx.set_hop_shape("wide")                                     # FP32 sweep shape
+    same()
+    ctx.set_hop_shape("auto")
+    same(ell=4)                                                   # larger l reallocates
+    same()
+    # back to the first settings: the graphs follow again
+    ctx.set_gauge(to_dev(w["U"]))
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], w["c"])
+    assert np.array_equal(same(), y0)

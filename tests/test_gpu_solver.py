@@ -335,7 +335,7 @@ def test_hop_timing_split_by_kernel():
     w = workload_case(C1)
     ctx = ctx_for(w)
     ctx.hop_timing_reset()
-    ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, mode="pseudo", precision="f32", hop_timing=True)
+    ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, mode="pseudo", precision="f32", hop_timing=True, fused=False)
     ms_all, n_all = ctx.hop_timing("f32")
     ms0, n0 = ctx.hop_timing("f32", dot=False)
     ms1, n1 = ctx.hop_timing("f32", dot=True)
@@ -344,11 +344,59 @@ def test_hop_timing_split_by_kernel():
     assert abs(ms_all * n_all - (ms0 * n0 + ms1 * n1)) <= 1e-9 * ms_all * n_all
     # per BiCG sub-step: two hops of A for u and two for r, one of each pair with
     # the inner product except for the last sub-step's r (its product is in the Gram matrix)
-    r = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, mode="pseudo", precision="f32")
+    r = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, mode="pseudo", precision="f32", fused=False)
     M = r.stats["outer_iters"]
     assert n_all == 8 * M and n1 == 3 * M
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     assert ctx.lib.fa_hop_timing_split(ctx.h, fa.F32, 2, ctypes.byref(ms), ctypes.byref(n)) == fa.FA_EINVAL
+    # fused sweeps: the 4l sweeps of each pass-1 outer iteration timed as one run
+    ctx.hop_timing_reset()
+    r = ctx.apply_f(to_dev(w["b"]), ell=2, tol=1e-10, mode="pseudo", precision="f32", hop_timing=True)
+    ms_f, n_f = ctx.fused_timing()
+    assert n_f == r.stats["outer_iters"] and ms_f > 0
+    assert ctx.hop_timing("f32")[1] == 0
+
+
+@pytest.mark.parametrize("ell", [1, 2, 3, 4])
+@pytest.mark.parametrize("mode", ["double", "pseudo"])
+def test_fused_sweeps_match_unfused(ell, mode):
+    """The fused FP32 sweeps (vector updates folded into the D_w sweeps, Gram
+    matrix in the last sweep's epilogue) against the same solve with the update
+    and Gram kernels of their own: the same recurrence, rounded the same way
+    except for the order of the Gram sums, so both land within FP32 rounding of
+    each other and within the FP32 bound of the oracle; the number of matrix-
+    vector products per outer iteration and the launch count shrink as stated."""
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    b = to_dev(w["b"])
+    y_o, _ = oracle_double(C1, None, ell, 1e-12)
+    kw = dict(ell=ell, tol=1e-10, mode=mode, precision="f32", max_outer=400)
+    rf = ctx.apply_f(b, **kw)
+    ru = ctx.apply_f(b, fused=False, **kw)
+    assert rel(to_host(rf.y), y_o) < tol_for("f32", ell)
+    assert rel(to_host(rf.y), to_host(ru.y)) < 2 * tol_for("f32", ell)
+    assert abs(rf.stats["outer_iters"] - ru.stats["outer_iters"]) <= 2
+    assert rf.stats["n_mv"] == (2 if mode == "pseudo" else 4) * ell * rf.stats["outer_iters"]
+
+
+def test_fused_sweeps_partial_store_and_reliable_updates():
+    """Pass 2 of the fused sweeps (the weighted occurrences summed into y in the
+    first hop of each sub-step): a pseudo-double-pass store that holds only part
+    of the solve, with and without reliable updates, against the oracle and the
+    unfused kernels."""
+    w = workload_case(C1)
+    ctx = ctx_for(w)
+    b = to_dev(w["b"])
+    y_o, _ = oracle_double(C1, None, 2, 1e-12)
+    per32 = 5 * 512 * 96 / 1e9
+    for rel_every in (0, 5):
+        kw = dict(ell=2, tol=1e-10, mode="pseudo", precision="f32", store_gb=6.5 * per32,
+                  reliable_every=rel_every)
+        rf = ctx.apply_f(b, **kw)
+        ru = ctx.apply_f(b, fused=False, **kw)
+        assert 0 < rf.stats["stored_outer"] < rf.stats["outer_iters"]
+        assert rel(to_host(rf.y), y_o) < tol_for("f32", 2)
+        assert rel(to_host(rf.y), to_host(ru.y)) < 2e-6
 
 
 def test_two_pass_memory_is_independent_of_the_number_of_poles():
@@ -373,3 +421,53 @@ def test_two_pass_memory_is_independent_of_the_number_of_poles():
     assert got["single", 4][0] - got["double", 4][0] == 4 * (2 + 2) * spinor64
     for mode in ("double", "pseudo", "single"):
         assert got[mode, 64][1] > got[mode, 4][1]
+
+
+def headline_site_samples():
+    """y* of the 16^3 x 32 workload at every spin-colour component of 48 seeded
+    sites per time slice (FP64 oracle, tol 1e-12; tests/golden/make_golden.py --sites)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "wilson_16x16x16x32_sites.json")
+    g = json.load(open(path))
+    idx = np.asarray(g["site_index_tzyx"])
+    want = np.asarray(g["y_re"]) + 1j * np.asarray(g["y_im"])
+    return g, idx, want
+
+
+def test_headline_configuration_against_oracle_site_samples():
+    """The configuration bench.py times as its headline: 16^3 x 32, l 2, 20 poles,
+    pseudo-double-pass, double-float head until every live shift residual is
+    below 0.08/l^2 |b|, FP32 tail, tol 1e-9, CUDA-graph replay, on a capturable
+    stream.  Compared entry by entry with the oracle's y* at 18,432 sampled
+    entries (all 12 components of 48 sites in every time slice, t = 0 and T-1
+    included): relative 2-norm of the difference <= 1e-8 (the target of the
+    16^3 x 32 configuration), and max |dy| / max |y*| <= 1e-8."""
+    import torch
+    g, idx, want = headline_site_samples()
+    w = inputs.make_workload("wilson_16x16x16x32")
+    stream = torch.cuda.Stream()
+    ctx = fa.Context(w["dims"], stream)
+    ctx.set_gauge(to_dev(w["U"]))
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], g["scale_c"])
+    ctx.set_poles(*fa.neuberger_poles(w["ns"]))
+    with torch.cuda.stream(stream):
+        b = to_dev(w["b"])
+    stream.synchronize()
+    kw = dict(ell=2, tol=1e-9, max_outer=4000, mode="pseudo", precision="mixed_df", switch_resid=0.08 / 4,
+              graph=True)
+    for _ in range(2):       # the second solve replays the captured graphs
+        r = ctx.apply_f(b, **kw)
+        stream.synchronize()
+        y = to_host(r.y)[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]].reshape(len(idx), 12)
+        d = y - want
+        rel2 = np.linalg.norm(d) / np.linalg.norm(want)
+        rmax = np.abs(d).max() / np.abs(want).max()
+        assert rel2 <= 1e-8, rel2
+        assert rmax <= 1e-8, rmax
+        assert r.stats["switch_outer"] > 0 and r.stats["stored_outer"] == r.stats["outer_iters"]
+    # the error spreads over the lattice: no time slice (the antiperiodic
+    # boundary slices included) is far off the overall figure
+    T = w["dims"][3]
+    per_t = [np.linalg.norm(d[idx[:, 0] == t]) / np.linalg.norm(want[idx[:, 0] == t]) for t in range(T)]
+    assert max(per_t) <= 3e-8, per_t
