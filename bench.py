@@ -65,6 +65,9 @@ def parse():
                    help="precision of the head of the headline solve: double-float or FP64")
     p.add_argument("--store-gb", type=float, default=0.0,
                    help="pseudo-double-pass store budget (0: the library default)")
+    p.add_argument("--no-gram-epilogue", action="store_true",
+                   help="FP32 stretches with the MR Gram matrix in a kernel of its own (by default the last "
+                        "D_w sweep of each outer iteration forms it in its epilogue)")
     p.add_argument("--ns-sweep", action="store_true",
                    help="runtime against the number of poles at a fixed number of BiCG steps "
                         "(M l = 64) for the single-pass, double-pass and pseudo-double-pass forms")
@@ -507,7 +510,7 @@ def main():
         args.switch_resid = 0.08 / ell ** 2
     variants = {
         "pseudo_mixed": dict(mode="pseudo", precision=args.head, switch_resid=args.switch_resid, graph=True,
-                             store_gb=args.store_gb),
+                             store_gb=args.store_gb, gram_epilogue=not args.no_gram_epilogue),
         "pseudo_mixed_fp64head": dict(mode="pseudo", precision="mixed", switch_resid=args.switch_resid, graph=True,
                                       store_gb=args.store_gb),
         "double_mixed": dict(mode="double", precision="mixed", switch_resid=args.switch_resid),
@@ -640,6 +643,8 @@ def main():
                           "rel_err_vs_oracle": head_vs_oracle,
                           "hop_f32_ms": hop32_ms, "hop_f32_dot_ms": hop32d_ms, "hop_f64_ms": hop64_ms,
                           "hop_df_ms": hopdf_ms, "hop_df_dot_ms": hopdfd_ms,
+                          "hop_f32_gram_ms": ctx.hop_timing("f32", dot="gram")[0],
+                          "gram_epilogue": not args.no_gram_epilogue,
                           "hop_f32_gbs": 384.0 * V / (hop32_ms * 1e-3) / 1e9 if hop32_ms else None,
                           "launches_per_solve": head_launches // max(1, args.steps), "clocks": clk}),
               flush=True)

@@ -191,21 +191,34 @@ class _ShiftScalars:
         c = [sum(gam[j] * ms ** (j - 1 - k) for j in range(k + 1, ell + 1)) for k in range(ell)]
         return ps, c
 
-    def converge(self, m, r0):
+    def converge(self, m, r0, last=False):
+        """Freeze the shifts whose residual |r_0| / |zeta_s| is below tol |b|; with
+        `last` (the final outer iteration of a fixed-cost run) freeze all."""
         rn = np.linalg.norm(r0)
         for s in np.flatnonzero(self.active):
-            if rn / abs(self.zeta[s]) <= self.tol * self.bnorm:
+            if last or rn / abs(self.zeta[s]) <= self.tol * self.bnorm:
                 self.active[s] = False
                 self.iters[s] = m + 1
         return bool(self.active.any())
 
 
+def _stopper(sh, fixed_outer):
+    """end_outer hook: the convergence test, and for a fixed-cost run the
+    freezing of every remaining shift after outer iteration fixed_outer."""
+    if fixed_outer is None:
+        return sh.converge
+    return lambda m, r0: sh.converge(m, r0, last=m + 1 >= fixed_outer)
+
+
 def multishift_single(A, b, sigma, ell, tol, max_outer=10000, round_vec=None, stats=None,
-                      observer=None):
+                      observer=None, fixed_outer=None):
     """Single-pass multi-shift BiCGstab(l): returns the list of x_s.
 
     observer(m, r_0, xs, zeta, active), if given, is called after every outer
     iteration before the convergence test (used to check invariants).
+    fixed_outer = M: a fixed-cost run (the setting of Sec. 3, Fig. 2): at most M
+    outer iterations; shifts still active after the M-th are frozen there
+    instead of raising.
     """
     st = stats if stats is not None else Stats()
     sh = _ShiftScalars(sigma, tol, np.linalg.norm(b))
@@ -233,12 +246,15 @@ def multishift_single(A, b, sigma, ell, tol, max_outer=10000, round_vec=None, st
             sh.zeta[s] *= ps
             sh.zeta_p[s] *= ps
 
+    stop = _stopper(sh, fixed_outer)
+
     def end_outer(m, r0):
         if observer is not None:
             observer(m, r0, xs, sh.zeta.copy(), sh.active.copy())
-        return sh.converge(m, r0)
+        return stop(m, r0)
 
-    seed_recurrence(A, b, ell, max_outer, substep, mr, end_outer, round_vec=round_vec, stats=st)
+    n = max_outer if fixed_outer is None else fixed_outer
+    seed_recurrence(A, b, ell, n, substep, mr, end_outer, round_vec=round_vec, stats=st)
     st.iters_per_shift = sh.iters.copy()
     if sh.active.any():
         raise RuntimeError("multishift_single: not converged within max_outer")
@@ -250,10 +266,13 @@ def _occurrences_per_outer(ell):
 
 
 def multishift_double(A, b, sigma, omega, ell, tol, max_outer=10000, round_vec=None,
-                      stats=None, return_coefficients=False):
-    """Double-pass multi-shift BiCGstab(l): returns y = sum_s omega_s x_s."""
+                      stats=None, return_coefficients=False, fixed_outer=None):
+    """Double-pass multi-shift BiCGstab(l): returns y = sum_s omega_s x_s.
+    fixed_outer: a fixed-cost run, as in multishift_single."""
     st = stats if stats is not None else Stats()
     sh = _ShiftScalars(sigma, tol, np.linalg.norm(b))
+    if fixed_outer is not None:
+        max_outer = fixed_outer
     ns = len(sh.sigma)
     cap = max_outer * _occurrences_per_outer(ell)
     CX = np.zeros((ns, cap), dtype=np.complex128)            # x_s  = sum_i CX[s, i] v^(i)
@@ -292,7 +311,7 @@ def multishift_double(A, b, sigma, omega, ell, tol, max_outer=10000, round_vec=N
             sh.zeta[s] *= ps
             sh.zeta_p[s] *= ps
 
-    _, rec = seed_recurrence(A, b, ell, max_outer, substep, mr, sh.converge,
+    _, rec = seed_recurrence(A, b, ell, max_outer, substep, mr, _stopper(sh, fixed_outer),
                              round_vec=round_vec, stats=st)
     st.iters_per_shift = sh.iters.copy()
     if sh.active.any():

@@ -33,7 +33,7 @@ EXPORTS = (
     "fa_create", "fa_destroy", "fa_set_gauge", "fa_set_params", "fa_estimate_scale",
     "fa_set_poles", "fa_neuberger_poles", "fa_zolotarev_poles", "fa_apply_dw", "fa_apply_A", "fa_solve_multishift",
     "fa_apply_f", "fa_apply_sign", "fa_apply_overlap", "fa_apply_sign_deflated", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
-    "fa_hop_timing_split", "fa_hop_timing_reset", "fa_fused_timing", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
+    "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune",
 )
@@ -57,7 +57,8 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int), ("tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("switch_resid", ctypes.c_double), ("flags", ctypes.c_int),
-                ("store_gb", ctypes.c_double), ("reliable_every", ctypes.c_int)]
+                ("store_gb", ctypes.c_double), ("reliable_every", ctypes.c_int),
+                ("shift_chunk", ctypes.c_int)]
 
 
 class SolverStats(ctypes.Structure):
@@ -119,7 +120,6 @@ def load_library(path=LIB_PATH):
         "fa_hop_timing": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_split": (I, [P, I, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_reset": (I, [P]),
-        "fa_fused_timing": (I, [P, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_device_bytes": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
         "fa_set_hop_shape": (I, [P, I]),
         "fa_get_hop_shape": (I, [P]),
@@ -287,12 +287,12 @@ class Context:
     @staticmethod
     def params(ell=2, tol=1e-10, max_outer=2000, mode="double", precision="f64",
                switch_resid=0.0, timing=False, hop_timing=False, store_gb=0.0, graph=False,
-               reliable_every=0, fixed_iters=False, overlap=True, fused=True):
+               reliable_every=0, fixed_iters=False, overlap=True, gram_epilogue=True, shift_chunk=0):
         return SolverParams(int(ell), float(tol), int(max_outer), _MODE[mode], _PREC[precision],
                             float(switch_resid),
                             (1 if timing else 0) | (2 if hop_timing else 0) | (4 if graph else 0)
-                            | (8 if fixed_iters else 0) | (0 if overlap else 16) | (0 if fused else 32),
-                            float(store_gb), int(reliable_every))
+                            | (8 if fixed_iters else 0) | (0 if overlap else 16) | (0 if gram_epilogue else 32),
+                            float(store_gb), int(reliable_every), int(shift_chunk))
 
     def apply_f(self, b, out=None, check=True, **kw):
         b = _spinor_check(b, self.spinor_shape, "b")
@@ -369,15 +369,17 @@ class Context:
                                             ctypes.byref(st)), "fa_solve_multishift")
         return Result(xs, st.as_dict())
 
-    def grad(self, b, eta, ell=2, tol=1e-12, max_outer=4000, want_db=True):
-        """(L, dL/dU, dL/dmu, dL/db, stats) for L = Re <eta, f(A) b> (single-pass FP64 solves)."""
+    def grad(self, b, eta, ell=2, tol=1e-12, max_outer=4000, want_db=True, shift_chunk=0):
+        """(L, dL/dU, dL/dmu, dL/db, stats) for L = Re <eta, f(A) b> (single-pass FP64
+        solves; shift_chunk > 0: that many poles at a time)."""
         torch = _torch()
         b = _spinor_check(b, self.spinor_shape, "b")
         eta = _spinor_check(eta, self.spinor_shape, "eta")
         gU = torch.empty(self.gauge_shape, dtype=torch.complex128, device="cuda")
         gb = self.empty_spinor() if want_db else None
         dmu, L = ctypes.c_double(), ctypes.c_double()
-        p = self.params(ell=ell, tol=tol, max_outer=max_outer, mode="single", precision="f64")
+        p = self.params(ell=ell, tol=tol, max_outer=max_outer, mode="single", precision="f64",
+                        shift_chunk=shift_chunk)
         st = SolverStats()
         _check(self.lib.fa_grad(self.h, b.data_ptr(), eta.data_ptr(), gU.data_ptr(), ctypes.byref(dmu),
                                 ctypes.byref(L), gb.data_ptr() if want_db else None, ctypes.byref(p),
@@ -392,20 +394,13 @@ class Context:
 
     def hop_timing(self, precision="f32", dot=None):
         """Mean event-timed ms per sweep and the count; dot: None (all sweeps),
-        False (plain sweeps), True (sweeps that also form an inner product)."""
+        False (plain sweeps), True (sweeps that also form an inner product),
+        "gram" (the FP32 sweep with the Gram-matrix epilogue)."""
         ms = ctypes.c_double()
         n = ctypes.c_longlong()
-        with_dot = -1 if dot is None else int(bool(dot))
+        with_dot = -1 if dot is None else (2 if dot == "gram" else int(bool(dot)))
         _check(self.lib.fa_hop_timing_split(self.h, _PREC[precision], with_dot, ctypes.byref(ms),
                                             ctypes.byref(n)), "fa_hop_timing_split")
-        return ms.value, n.value
-
-    def fused_timing(self):
-        """Mean event-timed ms of the 4l fused FP32 sweeps of one outer iteration
-        (timed as one run) and how many outer iterations were timed."""
-        ms = ctypes.c_double()
-        n = ctypes.c_longlong()
-        _check(self.lib.fa_fused_timing(self.h, ctypes.byref(ms), ctypes.byref(n)), "fa_fused_timing")
         return ms.value, n.value
 
     def device_bytes(self):

@@ -487,7 +487,7 @@ int fa_device_bytes(const fa_ctx* c, unsigned long long* field_bytes, unsigned l
     // lattice-sized buffers: links, spinors, stores, staging, reduction partials
     const fa::DevBuf* field[] = {&c->links64, &c->links32, &c->linksdf, &c->io64a, &c->io64b, &c->io32a,
                                  &c->io32b, &c->tmp64, &c->tmp32, &c->partials, &c->r64, &c->u64, &c->rt64,
-                                 &c->r32, &c->u32, &c->rt32, &c->r32a, &c->u32a, &c->y64, &c->xs64, &c->us64, &c->bhost_dev,
+                                 &c->r32, &c->u32, &c->rt32, &c->y64, &c->xs64, &c->us64, &c->bhost_dev,
                                  &c->yhost_dev, &c->gx, &c->gpart, &c->store64, &c->store32, &c->snap64,
                                  &c->snap32, &c->xrel, &c->brel, &c->snapx, &c->defl};
     // scalars: solver state, shifts, records, pass-2 weights, batch descriptors
@@ -503,15 +503,18 @@ int fa_device_bytes(const fa_ctx* c, unsigned long long* field_bytes, unsigned l
 
 int fa_hop_timing_split(const fa_ctx* c, int precision, int with_dot, double* mean_ms, long long* count) {
     if (!c || !mean_ms || !count || (precision != FA_F64 && precision != FA_F32 && precision != FA_DF) ||
-        with_dot < -1 || with_dot > 1)
+        with_dot < -1 || with_dot > 2 || (with_dot == 2 && precision != FA_F32))
         return FA_EINVAL;
     const int k = precision == FA_F64 ? 0 : (precision == FA_F32 ? 1 : 2);
     double ms = 0.0;
     long long n = 0;
-    for (int d = 0; d < 2; ++d) {
+    // index of each selector: plain k, with the inner product k + 3, FP32 Gram sweep 6
+    for (int d = 0; d < 3; ++d) {
         if (with_dot >= 0 && d != with_dot) continue;
-        ms += c->hop_ms[k + 3 * d];
-        n += c->hop_count[k + 3 * d];
+        if (d == 2 && precision != FA_F32) continue;
+        const int idx = d == 2 ? 6 : k + 3 * d;
+        ms += c->hop_ms[idx];
+        n += c->hop_count[idx];
     }
     *count = n;
     *mean_ms = n ? ms / (double)n : 0.0;
@@ -520,13 +523,6 @@ int fa_hop_timing_split(const fa_ctx* c, int precision, int with_dot, double* me
 
 int fa_hop_timing(const fa_ctx* c, int precision, double* mean_ms, long long* count) {
     return fa_hop_timing_split(c, precision, -1, mean_ms, count);
-}
-
-int fa_fused_timing(const fa_ctx* c, double* mean_ms, long long* count) {
-    if (!c || !mean_ms || !count) return FA_EINVAL;
-    *count = c->hop_count[6];
-    *mean_ms = c->hop_count[6] ? c->hop_ms[6] / (double)c->hop_count[6] : 0.0;
-    return FA_OK;
 }
 
 int fa_hop_timing_reset(fa_ctx* c) {

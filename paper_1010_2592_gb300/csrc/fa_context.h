@@ -81,7 +81,6 @@ struct fa_ctx {
     fa::DevBuf prec, coef, cs;           // per-shift record, pass-2 weights, sweep output
     fa::DevBuf coef4;                    // pass-2 weights as FP32 pairs (gathers of FP32 / double-float stores)
     fa::DevBuf r64, u64, rt64, r32, u32, rt32;   // seed vectors (l+1 each, contiguous)
-    fa::DevBuf r32a, u32a;               // fused FP32 sweeps: alternate buffers of r_j, u_j (j < l)
     fa::DevBuf y64;                      // accumulated result (FP64 internal)
     fa::DevBuf xs64, us64;               // single-pass shift vectors
     fa::DevBuf bhost_dev, yhost_dev;     // canonical staging for fa_apply_f_host
@@ -98,7 +97,7 @@ struct fa_ctx {
     long long launches = 0;
     // hop-kernel timing: index FP64 0, FP32 1, double-float 2; + 3 for the
     // sweeps that also form <dot_with, out> (and run a scalar step in a solve);
-    // 6: the 4l fused FP32 sweeps of one outer iteration, timed as one run
+    // 6: the FP32 sweep with the Gram-matrix epilogue (the last of an outer iteration)
     double hop_ms[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     long long hop_count[7] = {0, 0, 0, 0, 0, 0, 0};
     bool hop_timing = false;

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_lincomb_canon(int n, int k, const 
 struct Layout {
     int L, ns, max_outer, V;
     bool need64, need32, single;
-    bool fused;                // FP32 stretches run the fused sweeps (one system, l <= 4)
+    bool gram_hop;             // FP32 pass 1: the Gram matrix in the last sweep's epilogue (one system, l <= 4)
     size_t vs64, vs32;         // one spinor in elements of double2 / float4
     int nblk, red_grid, part_slots;
     int vgrid;                 // balanced vector kernels: kVecBlocks per SM
@@ -198,7 +198,7 @@ static int red_grid_for(int V) { return std::min(nblocks(V), 8 * sms()); }
 static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
     const int V = Lo.V, L = Lo.L, ns = c->ns, MO = Lo.max_outer;
     const size_t s64 = (size_t)12 * V * sizeof(double2), s32 = (size_t)6 * V * sizeof(float4);
-    // the fused Gram epilogue writes n_gram(l) partials per block of the FP32 sweep
+    // the Gram epilogue of the FP32 sweep writes n_gram(l) partials per block
     const size_t hop_blk = (size_t)std::max(nblocks(V), (V + kHopNarrowThreads - 1) / kHopNarrowThreads) + 1;
     FA_CUDA(c->partials.ensure(std::max({(size_t)std::max({Lo.nblk, Lo.red_grid, Lo.vgrid + 1}) * Lo.part_slots,
                                          (size_t)row_blocks(V), hop_blk * (size_t)Lo.part_slots}) *
@@ -220,10 +220,6 @@ static int ensure_workspace(fa_ctx* c, const Layout& Lo) {
         FA_CUDA(c->tmp64.ensure(s64), "alloc tmp64");
     }
     if (Lo.need32) {
-        if (Lo.fused) {
-            FA_CUDA(c->r32a.ensure((size_t)L * s32), "alloc r32 alternates");
-            FA_CUDA(c->u32a.ensure((size_t)L * s32), "alloc u32 alternates");
-        }
         FA_CUDA(c->r32.ensure((L + 1) * s32), "alloc r32");
         FA_CUDA(c->u32.ensure((L + 1) * s32), "alloc u32");
         FA_CUDA(c->rt32.ensure(s32), "alloc rt32");
@@ -279,8 +275,6 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     d.u32 = c->u32.as<float4>();
     d.rt32 = c->rt32.as<float4>();
     d.tmp32 = c->tmp32.as<float4>();
-    d.r32a = Lo.fused ? c->r32a.as<float4>() : nullptr;
-    d.u32a = Lo.fused ? c->u32a.as<float4>() : nullptr;
     d.y = c->y64.as<double2>();
     d.xs = Lo.single ? c->xs64.as<double2>() : nullptr;
     d.us = Lo.single ? c->us64.as<double2>() : nullptr;
@@ -310,7 +304,6 @@ struct Batch {
     bool pdl = true;                      // programmatic dependent launch inside an outer iteration
 };
 
-template <int L> static int enqueue_outer_fused(Batch& B, bool pass2, bool reliable);
 
 // Kernel launch, with programmatic stream serialization when `pdl` is set: the
 // kernel may then be placed on the SMs while its predecessor (a kernel) finishes,
@@ -352,9 +345,6 @@ template <typename R> constexpr int rp_of() {
 // Each launch covers the whole batch (grid.y = systems).
 template <typename R, int L>
 static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reliable) {
-    if constexpr (rp_of<R>() == RP32 && L <= 4) {
-        if (B.Lo.fused && !single) return enqueue_outer_fused<L>(B, pass2, reliable);
-    }
     fa_ctx* c = B.c0;
     const int n = B.n, nb = B.Lo.nblk, rg = B.Lo.red_grid, vg = B.Lo.vgrid;
     const int p2 = pass2 ? 1 : 0;
@@ -449,6 +439,35 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
         FA_LAUNCHED(c, "k_hop_sys");
         return FA_OK;
     };
+    // FP32 pass 1 of a one-system double-pass solve: the last sweep forms the
+    // Gram matrix (fused_sweep.cuh) instead of a kernel of its own
+    const bool gram_hop = rp_of<R>() == RP32 && L <= 4 && B.Lo.gram_hop && n == 1 && !pass2 && !single;
+    auto gram_sweep = [&]() -> int {
+        if constexpr (rp_of<R>() == RP32 && L <= 4) {
+            GramHop a{};
+            a.g = h0.g;
+            a.U = LinkView<float>{h0.links32, h0.V};
+            a.in = h0.tmp32;
+            a.out = h0.r32 + (size_t)L * 6 * h0.V;
+            a.part = h0.part;
+            for (int i = 0; i < L; ++i) a.r[i] = h0.r32 + (size_t)i * 6 * h0.V;
+            a.cdiag = host_cvt<float>(h0.scale * h0.diag);
+            a.chop = host_cvt<float>(-0.5 * h0.scale);
+            a.ef = host_cvt<float>(h0.ef);
+            a.eb = host_cvt<float>(h0.eb);
+            a.bc = host_cvt<float>(h0.bc);
+            if (timing) hop_timing_begin(c, 6);
+            if (hop_use_narrow(c->hop_shape, h0.V)) {
+                constexpr int NT = kHopNarrowThreads, MB = kHopNarrowBlocks;
+                launch(pdl, k_hop_gram<L, NT, MB>, dim3((h0.V + NT - 1) / NT), NT, st, a, ds);
+            } else {
+                launch(pdl, k_hop_gram<L, kThreads, FA_HOP_MINB>, dim3(nblocks(h0.V)), kThreads, st, a, ds);
+            }
+            if (timing) hop_timing_end(c);
+            FA_LAUNCHED(c, "k_hop_gram");
+        }
+        return FA_OK;
+    };
     // Pass 1: the seed parts of the scalar steps run in the last block of the
     // reduction that precedes them (alpha after <rt, u_{j+1}>, the next beta
     // after <rt, r_{j+1}>, the MR coefficients after the Gram matrix,
@@ -471,9 +490,13 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
         FA_LAUNCHED(c, "k_update_r");
         FA_TRY(hop(1, j, 2, 0, 0, false, none));                                   // tmp = g5 D r_j
         const bool next_beta = !pass2 && j < L - 1;
-        FA_TRY(hop(2, 0, 1, j + 1, 1, next_beta, next_beta ? ScalarStep{STEP_BETA, j + 1} : none));   // r_{j+1}
+        if (gram_hop && j == L - 1) {
+            FA_TRY(gram_sweep());   // r_l and, in the epilogue, the Gram matrix and gamma
+        } else {
+            FA_TRY(hop(2, 0, 1, j + 1, 1, next_beta, next_beta ? ScalarStep{STEP_BETA, j + 1} : none));   // r_{j+1}
+        }
     }
-    if (!pass2) {
+    if (!pass2 && !gram_hop) {
         launch(pdl, k_gram<R, L>, gg, kThreads, st, ds, single ? 1 : 0);
         FA_LAUNCHED(c, "k_gram");
     }
@@ -502,151 +525,6 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
         c->launches += 2;
         if (rc != FA_OK) return rc;
         k_reliable<R><<<gv, kThreads, 0, st>>>(ds, t2, p2, conv);
-        FA_LAUNCHED(c, "k_reliable");
-    }
-    if (pass2) {
-        launch(pdl, k_advance, dim3(n), 1, st, ds);
-        FA_LAUNCHED(c, "k_advance");
-    }
-    return FA_OK;
-}
-
-// One FP32 outer iteration of a one-system double-pass solve with the fused
-// sweeps (fused_sweep.cuh): per BiCG sub-step j the four sweeps F1..F4, then the
-// MR kernel; 4l + 1 launches (+ the reliable update, + the pass-2 counter).
-// Buffers: home r_i, u_i (i <= l) in r32 / u32, alternates of r_j, u_j (j < l)
-// in r32a / u32a (see the file comment of fused_sweep.cuh).
-template <int L, int NT, int MB>
-static int enqueue_fused_sweeps(Batch& B, bool pass2, bool pdl_first, bool pdl) {
-    fa_ctx* c = B.c0;
-    const SolverDev& h = B.host[0];
-    const SolverDev* ds = B.dev;
-    cudaStream_t st = c->stream;
-    const int V = h.V;
-    const size_t vs = (size_t)6 * V;
-    auto rh = [&](int i) { return h.r32 + (size_t)i * vs; };
-    auto uh = [&](int i) { return h.u32 + (size_t)i * vs; };
-    auto ra = [&](int i) { return h.r32a + (size_t)i * vs; };
-    auto ua = [&](int i) { return h.u32a + (size_t)i * vs; };
-    const LinkView<float> U{h.links32, V};
-    const float ef = host_cvt<float>(h.ef), eb = host_cvt<float>(h.eb), bc = host_cvt<float>(h.bc);
-    const float cd1 = host_cvt<float>(1.0 * h.diag), ch1 = host_cvt<float>(-0.5 * 1.0);
-    const float cd2 = host_cvt<float>(h.scale * h.diag), ch2 = host_cvt<float>(-0.5 * h.scale);
-    const int nb = (V + NT - 1) / NT;
-    const int p2 = pass2 ? 1 : 0;
-    const ScalarStep none{STEP_NONE, 0};
-    bool first = true;
-    auto pd = [&]() {
-        const bool r = first ? pdl_first : pdl;
-        first = false;
-        return r;
-    };
-    for (int j = 0; j < L; ++j) {
-        // F1: tmp = g5 D (r_j - beta u_j); u_j -> alternate; u_i (i < j) at the own sites
-        FusedHop1 a{};
-        a.g = h.g;
-        a.U = U;
-        a.a = rh(j);
-        a.b = uh(j);
-        a.tmp = h.tmp32;
-        a.upd = ua(j);
-        for (int i = 0; i < j; ++i) {
-            a.cdst[i] = ua(i);
-            a.ca[i] = ra(i);
-            a.cb[i] = ua(i);
-        }
-        a.u0 = ua(0);
-        a.cdiag = cd1;
-        a.chop = ch1;
-        a.ef = ef;
-        a.eb = eb;
-        a.bc = bc;
-        a.j = j;
-        launch(pd(), k_fhop1<L, 0, false, false, NT, MB>, dim3(nb), NT, st, a, ds, p2);
-        FA_LAUNCHED(c, "k_fhop1 (u)");
-        // F2: u_{j+1} = c g5 D tmp, <rt, u_{j+1}>, alpha
-        FusedHop2 b{};
-        b.g = h.g;
-        b.U = U;
-        b.in = h.tmp32;
-        b.out = uh(j + 1);
-        b.rt = h.rt32;
-        b.part = h.part;
-        b.cdiag = cd2;
-        b.chop = ch2;
-        b.ef = ef;
-        b.eb = eb;
-        b.bc = bc;
-        if (pass2) launch(pd(), k_fhop2<L, 0, NT, MB>, dim3(nb), NT, st, b, ds, p2, none);
-        else launch(pd(), k_fhop2<L, 1, NT, MB>, dim3(nb), NT, st, b, ds, p2, ScalarStep{STEP_ALPHA, j});
-        FA_LAUNCHED(c, "k_fhop2 (u)");
-        // F3: tmp = g5 D (r_j - alpha u_{j+1}); r_j -> alternate; r_i (i < j);
-        // occurrences stored (pass 1) or summed into y (pass 2); shift block (pass 1)
-        a.a = rh(j);
-        a.b = uh(j + 1);
-        a.upd = ra(j);
-        for (int i = 0; i < j; ++i) {
-            a.cdst[i] = ra(i);
-            a.ca[i] = ra(i);
-            a.cb[i] = ua(i + 1);
-        }
-        if (pass2) launch(pd(), k_fhop1<L, 1, false, true, NT, MB>, dim3(nb), NT, st, a, ds, p2);
-        else launch(pd(), k_fhop1<L, 1, true, false, NT, MB>, dim3(nb + 1), NT, st, a, ds, p2);
-        FA_LAUNCHED(c, "k_fhop1 (r)");
-        // F4: r_{j+1} = c g5 D tmp; next beta, or the Gram matrix and gamma
-        b.out = rh(j + 1);
-        if (pass2) {
-            launch(pd(), k_fhop2<L, 0, NT, MB>, dim3(nb), NT, st, b, ds, p2, none);
-        } else if (j < L - 1) {
-            launch(pd(), k_fhop2<L, 1, NT, MB>, dim3(nb), NT, st, b, ds, p2, ScalarStep{STEP_BETA, j + 1});
-        } else {
-            for (int i = 0; i < L; ++i) b.gram[i] = ra(i);
-            launch(pd(), k_fhop2<L, 2, NT, MB>, dim3(nb), NT, st, b, ds, p2, none);
-        }
-        FA_LAUNCHED(c, "k_fhop2 (r)");
-    }
-    return FA_OK;
-}
-
-template <int L>
-static int enqueue_outer_fused(Batch& B, bool pass2, bool reliable) {
-    fa_ctx* c = B.c0;
-    const SolverDev& h0 = B.host[0];
-    const SolverDev* ds = B.dev;
-    cudaStream_t st = c->stream;
-    const int n = B.n, vg = B.Lo.vgrid, rg = B.Lo.red_grid;
-    const int p2 = pass2 ? 1 : 0;
-    // the 4l sweeps run back to back; with sweep timing on (direct launches)
-    // one event pair brackets them, so the first sweep follows the event
-    // record in plain stream order and the others keep programmatic launch
-    const bool timing = c->hop_timing && !B.use_graph;
-    if (timing) hop_timing_begin(c, 6);
-    const bool narrow = hop_use_narrow(c->hop_shape, h0.V);
-    int rc;
-    if (narrow) rc = enqueue_fused_sweeps<L, kHopNarrowThreads, kHopNarrowBlocks>(B, pass2, B.pdl && !timing, B.pdl);
-    else rc = enqueue_fused_sweeps<L, kThreads, FA_HOP_MINB>(B, pass2, B.pdl && !timing, B.pdl);
-    if (timing) hop_timing_end(c);
-    FA_TRY(rc);
-    const bool pdl = B.pdl && !timing;
-    const int mg = mr_min_blocks<float, L>() >= kVecBlocks ? vg : rg;
-    const dim3 gm(mg, n), gmx(mg + 1, n);
-    const ScalarStep conv = pass2 ? none_step() : ScalarStep{STEP_CONV, 0};
-    if (pass2) launch(pdl, k_mr<float, L, true, false, false, false, true>, gm, kThreads, st, ds, p2, none_step());
-    else launch(pdl, k_mr<float, L, false, false, true, true, true>, gmx, kThreads, st, ds, p2,
-                reliable ? none_step() : conv);
-    FA_LAUNCHED(c, "k_mr");
-    if (reliable) {
-        double2* t1 = c->io64a.as<double2>();
-        double2* t2 = c->io64b.as<double2>();
-        const int* done = pass2 ? nullptr : &h0.st->done;
-        int r = launch_hop_f64(h0.g, h0.links64, h0.x64, t1, h0.diag, h0.ef, h0.eb, h0.bc, 1.0, false, true,
-                               nullptr, nullptr, done, st);
-        if (r == FA_OK)
-            r = launch_hop_f64(h0.g, h0.links64, t1, t2, h0.diag, h0.ef, h0.eb, h0.bc, h0.scale, false, true,
-                               nullptr, nullptr, done, st);
-        c->launches += 2;
-        if (r != FA_OK) return r;
-        k_reliable<float><<<dim3(vg, n), kThreads, 0, st>>>(ds, t2, p2, conv);
         FA_LAUNCHED(c, "k_reliable");
     }
     if (pass2) {
@@ -699,7 +577,7 @@ static std::vector<unsigned long long> graph_signature(const Batch& B) {
                               (const void*)h.links32, (const void*)h.linksdf, (const void*)h.r64,
                               (const void*)h.u64, (const void*)h.rt64, (const void*)h.tmp64, (const void*)h.r32,
                               (const void*)h.u32, (const void*)h.rt32, (const void*)h.tmp32, (const void*)h.x64,
-                              (const void*)h.b64, (const void*)h.r32a, (const void*)h.u32a})
+                              (const void*)h.b64})
             p(v);
         d(h.diag);
         d(h.ef);
@@ -719,7 +597,7 @@ static int enqueue_outer_any(Batch& B, int rp, bool pass2, bool single, bool hea
     if (!B.use_graph) return enqueue_outer_direct(B, rp, pass2, single, head, rel);
     fa_ctx* c = B.c0;
     const int key = rp | (pass2 ? 4 : 0) | (single ? 8 : 0) | (head ? 16 : 0) | (rel ? 32 : 0) |
-                    (B.Lo.fused ? 64 : 0);
+                    (B.Lo.gram_hop ? 64 : 0);
     std::vector<unsigned long long> sig = graph_signature(B);
     GraphEntry* ge = nullptr;
     for (auto& e : c->graphs)
@@ -889,9 +767,9 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     // by HBM, not by the per-SM imbalance)
     Lo.vgrid = std::min(Lo.nblk, kVecBlocks * sms());
     Lo.part_slots = std::max(n_gram(L), 2);
-    // FP32 stretches of a one-system double-pass solve run the fused sweeps
-    // (flags bit 5 turns them off: the unfused kernels, for comparison)
-    Lo.fused = n == 1 && !single && L <= 4 && prec != FA_F64 && (p->flags & 32) == 0;
+    // FP32 stretches of a one-system double-pass solve form the MR Gram matrix in
+    // the epilogue of their last sweep (flags bit 5: the Gram kernel instead)
+    Lo.gram_hop = n == 1 && !single && L <= 4 && prec != FA_F64 && (p->flags & 32) == 0;
     for (auto* c : B.sys) FA_TRY(ensure_workspace(c, Lo));
     FA_CUDA(c0->descbuf.ensure((size_t)n * sizeof(SolverDev)), "alloc descriptors");
     FA_CUDA(c0->flagbuf.ensure((size_t)2 * n * sizeof(int)), "alloc flags");
@@ -906,7 +784,9 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     B.flags = c0->flagbuf.as<int>();
     // graphs need a capturable stream (not the legacy default stream)
     B.use_graph = (p->flags & 4) != 0 && c0->stream != nullptr && c0->stream != cudaStreamLegacy;
-    B.pdl = (p->flags & 16) == 0;
+    // programmatic dependent launch for direct launches only: under CUDA-graph
+    // replay it measured slower (16^3 x 32 headline: 15.00 against 14.62 ms)
+    B.pdl = (p->flags & 16) == 0 && !B.use_graph;
     for (auto* c : B.sys) B.host.push_back(make_dev(c, Lo));
     for (auto& h : B.host) h.fixed_iters = (p->flags & 8) ? 1 : 0;
     cudaStream_t st = c0->stream;
@@ -1296,64 +1176,107 @@ int grad(fa_ctx* c, const double* b, const double* eta, double* dLdU, double* dL
     fa_solver_params ps = *p;
     ps.mode = FA_SINGLE;
     ps.precision = FA_F64;
-    fa_solver_stats st1{}, st2{};
-    FA_TRY(solve(c, b, nullptr, nullptr, &ps, &st1));
     const int V = c->g.V, ns = c->ns;
+    const int chunk = (p->shift_chunk > 0 && p->shift_chunk < ns) ? p->shift_chunk : ns;
     const size_t vs = (size_t)12 * V;
     const size_t sb = vs * sizeof(double2);
     cudaStream_t st = c->stream;
-    FA_CUDA(c->gx.ensure(ns * sb), "alloc gradient");
-    FA_CUDA(cudaMemcpyAsync(c->gx.p, c->xs64.p, ns * sb, cudaMemcpyDeviceToDevice, st), "save x_s");
-    const double mu0 = c->mu;
-    c->mu = -mu0;
-    const int rc2 = solve(c, eta, nullptr, nullptr, &ps, &st2);
-    c->mu = mu0;
-    FA_TRY(rc2);
     const int nb = nblocks(V), rg = red_grid_for(V);
+    FA_CUDA(c->gx.ensure((size_t)chunk * sb), "alloc gradient");
     FA_CUDA(c->io64a.ensure(sb), "alloc");
     FA_CUDA(c->io64b.ensure(sb), "alloc");
-    FA_CUDA(c->gpart.ensure(((size_t)ns * nb + 2 * (size_t)rg) * sizeof(double2)), "alloc");
+    FA_CUDA(c->tmp64.ensure(sb), "alloc");
+    // mu-derivative partials of one chunk (summed on the host chunk by chunk, in
+    // shift order) and the partials of <eta, y>
+    FA_CUDA(c->gpart.ensure(((size_t)chunk * nb + 2 * (size_t)rg) * sizeof(double2)), "alloc");
+    FA_CUDA(c->defl.ensure(2 * sb), "alloc");             // y and dL/db accumulators
+    double2* yacc = c->defl.as<double2>();
+    double2* bacc = yacc + vs;
     FA_CUDA(cudaMemsetAsync(dLdU, 0, (size_t)V * 72 * sizeof(double), st), "zero dL/dU");
+    FA_CUDA(cudaMemsetAsync(yacc, 0, 2 * sb, st), "zero accumulators");
     double2* gxs = c->gx.as<double2>();
-    double2* lam = c->xs64.as<double2>();
     double2* t1 = c->io64a.as<double2>();
     double2* t2 = c->io64b.as<double2>();
     double2* part = c->gpart.as<double2>();
-    for (int s = 0; s < ns; ++s) {
-        const double2* xs = gxs + s * vs;
-        const double2* ls = lam + s * vs;
-        FA_TRY(hop_f64(c, xs, t1, 1.0, false, true, false, nullptr, nullptr, nullptr));   // g5 D x
-        FA_TRY(hop_f64(c, ls, t2, 1.0, false, false, true, nullptr, nullptr, nullptr));   // D(-mu) lambda
-        FA_TRY(launch_force(c->g, links64_of(c), ls, t1, t2, xs, dLdU, -c->scale_c * c->omega[s],
-                            std::exp(c->mu), std::exp(-c->mu), c->t_bc, part + (size_t)s * nb, st));
+    // the poles of the whole expansion; each chunk solves with a slice of them
+    std::vector<double> om_all(c->omega, c->omega + ns), sg_all(c->sigma, c->sigma + ns);
+    const double mu0 = c->mu;
+    fa_solver_stats st1{}, st2{}, acc{};
+    int rc = FA_OK;
+    double dmu = 0.0;
+    std::vector<double2> hmu((size_t)chunk * nb);
+    for (int s0 = 0; s0 < ns && rc == FA_OK; s0 += chunk) {
+        const int k = std::min(chunk, ns - s0);
+        c->ns = k;
+        for (int i = 0; i < k; ++i) {
+            c->omega[i] = om_all[s0 + i];
+            c->sigma[i] = sg_all[s0 + i];
+        }
+        rc = solve(c, b, nullptr, nullptr, &ps, &st1);
+        if (rc != FA_OK) break;
+        rc = ok(cudaMemcpyAsync(gxs, c->xs64.p, (size_t)k * sb, cudaMemcpyDeviceToDevice, st), "save x_s");
+        if (rc != FA_OK) break;
+        c->mu = -mu0;
+        rc = solve(c, eta, nullptr, nullptr, &ps, &st2);
+        c->mu = mu0;
+        if (rc != FA_OK) break;
+        const double2* lam = c->xs64.as<double2>();
+        for (int i = 0; i < k && rc == FA_OK; ++i) {
+            const double2* xs = gxs + i * vs;
+            const double2* ls = lam + i * vs;
+            rc = hop_f64(c, xs, t1, 1.0, false, true, false, nullptr, nullptr, nullptr);   // g5 D x
+            if (rc == FA_OK) rc = hop_f64(c, ls, t2, 1.0, false, false, true, nullptr, nullptr, nullptr);   // D(-mu) lambda
+            if (rc == FA_OK)
+                rc = launch_force(c->g, links64_of(c), ls, t1, t2, xs, dLdU, -c->scale_c * om_all[s0 + i],
+                                  std::exp(c->mu), std::exp(-c->mu), c->t_bc, part + (size_t)i * nb, st);
+            c->launches++;
+        }
+        if (rc != FA_OK) break;
+        // y += sum_chunk omega x; dL/db += sum_chunk omega lambda (the pole weights of the
+        // chunk were uploaded by its solves: shift buffer, after sigma)
+        const double* om_dev = reinterpret_cast<const double*>(c->shiftbuf.as<char>() + kMaxShifts * sizeof(double));
+        k_combine<<<(12 * V + kThreads - 1) / kThreads, kThreads, 0, st>>>(V, k, om_dev, gxs, vs, yacc, 1);
         c->launches++;
+        if (dLdb) {
+            k_combine<<<(12 * V + kThreads - 1) / kThreads, kThreads, 0, st>>>(V, k, om_dev, lam, vs, bacc, 1);
+            c->launches++;
+        }
+        rc = ok(cudaGetLastError(), "k_combine");
+        if (rc == FA_OK)
+            rc = ok(cudaMemcpyAsync(hmu.data(), part, (size_t)k * nb * sizeof(double2), cudaMemcpyDeviceToHost, st),
+                    "read partials");
+        if (rc == FA_OK) rc = ok(cudaStreamSynchronize(st), "sync gradient chunk");
+        for (size_t q = 0; rc == FA_OK && q < (size_t)k * nb; ++q) dmu += hmu[q].x;
+        acc.n_mv += st1.n_mv + st2.n_mv;
+        acc.n_dot += st1.n_dot + st2.n_dot;
+        acc.outer_iters += st1.outer_iters + st2.outer_iters;
+        if (s0 == 0) acc.status = st1.status;
     }
-    // y = sum omega x, L = Re <eta, y>; dL/db = sum omega lambda
-    // the pole weights omega were uploaded by the solves (shift buffer, after sigma)
-    const double* om_dev = reinterpret_cast<const double*>(c->shiftbuf.as<char>() + kMaxShifts * sizeof(double));
-    k_combine<<<(12 * V + kThreads - 1) / kThreads, kThreads, 0, st>>>(V, ns, om_dev, gxs, vs, c->y64.as<double2>());
-    FA_LAUNCHED(c, "k_combine");
+    c->ns = ns;
+    for (int i = 0; i < ns; ++i) {
+        c->omega[i] = om_all[i];
+        c->sigma[i] = sg_all[i];
+    }
+    c->mu = mu0;
+    FA_TRY(rc);
+    // L = Re <eta, y>
     FA_TRY(launch_pack_spinor_f64(c->g, eta, t1, st));
-    k_dot2<double><<<rg, kThreads, 0, st>>>(V, t1, c->y64.as<double2>(), part + (size_t)ns * nb);
+    k_dot2<double><<<rg, kThreads, 0, st>>>(V, t1, yacc, part);
     FA_LAUNCHED(c, "k_dot2");
-    if (dLdb) {
-        k_combine<<<(12 * V + kThreads - 1) / kThreads, kThreads, 0, st>>>(V, ns, om_dev, lam, vs, t2);
-        FA_LAUNCHED(c, "k_combine");
-        FA_TRY(launch_unpack_spinor_f64(c->g, t2, dLdb, st));
-    }
-    std::vector<double2> h((size_t)ns * nb + 2 * (size_t)rg);
+    if (dLdb) FA_TRY(launch_unpack_spinor_f64(c->g, bacc, dLdb, st));
+    std::vector<double2> h((size_t)rg);
     FA_CUDA(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, st), "read partials");
     FA_CUDA(cudaStreamSynchronize(st), "sync gradient");
-    double dmu = 0.0, lre = 0.0;
-    for (size_t k = 0; k < (size_t)ns * nb; ++k) dmu += h[k].x;
-    for (int k = 0; k < rg; ++k) lre += h[(size_t)ns * nb + k].x;
+    double lre = 0.0;
+    for (int k = 0; k < rg; ++k) lre += h[k].x;
     *dLdmu = dmu;
     *L = lre;
     if (stats) {
         *stats = st1;
-        stats->n_mv += st2.n_mv;
-        stats->n_dot += st2.n_dot;
-        stats->outer_iters = st1.outer_iters + st2.outer_iters;
+        stats->n_mv = acc.n_mv;
+        stats->n_dot = acc.n_dot;
+        stats->outer_iters = acc.outer_iters;
+        stats->status = acc.status;
         stats->n_launch = c->launches;
     }
     return FA_OK;

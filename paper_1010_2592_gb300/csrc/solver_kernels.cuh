@@ -80,8 +80,6 @@ struct SolverDev {
     // seed vectors: r_0..r_l and u_0..u_l contiguous, the shadow vector, scratch
     double2 *r64, *u64, *rt64, *tmp64;
     float4 *r32, *u32, *rt32, *tmp32;
-    // fused FP32 sweeps: alternate buffers of r_0..r_{l-1}, u_0..u_{l-1} (l each, contiguous)
-    float4 *r32a, *u32a;
     double2* y;            // FP64 [12][V] result
     double2* xs;           // single-pass x_s   [ns][12][V]
     double2* us;           // single-pass u^s_i [ns][l+1][12][V]
@@ -936,9 +934,7 @@ k_gram(const SolverDev* __restrict__ ds, int shifts) {
 template <typename R, int L> constexpr int mr_min_blocks() {
     return (!std::is_same<R, double>::value && L <= 3) ? 4 : 1;
 }
-// ALT (fused FP32 sweeps): r_j and u_j, j < l, are read from their alternate
-// buffers (where the fused sweeps left them); r_0, u_0 are written home.
-template <typename R, int L, bool ACC, bool SHIFTS, bool DOT, bool XS = false, bool ALT = false>
+template <typename R, int L, bool ACC, bool SHIFTS, bool DOT, bool XS = false>
 __global__ void __launch_bounds__(kThreads, mr_min_blocks<R, L>())
 k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
     dep_sync();
@@ -956,9 +952,6 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
     typename Ch<R>::T* u = Vec<R>::u(d);
     const typename Ch<R>::T* rt = Vec<R>::rt(d);
     const size_t vs = vstride<R>(d);
-    // where r_i, u_i (i < l) are read from
-    const typename Ch<R>::T* rin = ALT ? reinterpret_cast<const typename Ch<R>::T*>(d.r32a) : r;
-    const typename Ch<R>::T* uin = ALT ? reinterpret_cast<const typename Ch<R>::T*>(d.u32a) : u;
     double2* y = d.y;
     double2* xs = d.xs;
     double2* us = d.us;
@@ -978,7 +971,7 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
         for (int q = 0; q < Ch<R>::N; ++q) {
             Ch<R> rv[L + 1];
 #pragma unroll
-            for (int i = 0; i <= L; ++i) rv[i] = Ch<R>::ld((i < L ? rin : r) + i * vs, q, d.V, s);
+            for (int i = 0; i <= L; ++i) rv[i] = Ch<R>::ld(r + i * vs, q, d.V, s);
             if (store != nullptr) {
 #pragma unroll
                 for (int k = 0; k < L; ++k) rv[k].stv(store + slot_mr(L, k) * vs, q, d.V, s);
@@ -1027,10 +1020,10 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
                 for (int j = 1; j <= L; ++j) acc_x<R>(d.x64, q, d.V, s, d.rec_gamma[m * (L + 1) + j], rv[j - 1]);
             }
             Ch<R> r0 = rv[0];
-            Ch<R> u0 = Ch<R>::ld(uin, q, d.V, s);
+            Ch<R> u0 = Ch<R>::ld(u, q, d.V, s);
 #pragma unroll
             for (int j = 1; j <= L; ++j) {
-                Ch<R> uj = Ch<R>::ld((j < L ? uin : u) + j * vs, q, d.V, s);
+                Ch<R> uj = Ch<R>::ld(u + j * vs, q, d.V, s);
 #pragma unroll
                 for (int w = 0; w < Ch<R>::W; ++w) {
                     r0.c[w] = cfma(ng[j], rv[j].c[w], r0.c[w]);
@@ -1457,11 +1450,16 @@ __global__ void k_combine_sys(const SolverDev* __restrict__ ds) {
     d.y[idx] = make_double2(a, b);
 }
 
-// single-pass result y = sum_s omega_s x_s (FP64 [12][V])
-__global__ void k_combine(int V, int ns, const double* omega, const double2* xs, size_t svs, double2* y) {
+// single-pass result y = sum_s omega_s x_s (FP64 [12][V]); accumulate: y += that sum
+__global__ void k_combine(int V, int ns, const double* omega, const double2* xs, size_t svs, double2* y,
+                          int accumulate = 0) {
     const int idx = blockIdx.x * kThreads + threadIdx.x;
     if (idx >= 12 * V) return;
     double a = 0.0, b = 0.0;
+    if (accumulate) {
+        a = y[idx].x;
+        b = y[idx].y;
+    }
     for (int sh = 0; sh < ns; ++sh) {
         const double2 v = xs[sh * svs + idx];
         a = __fma_rn(omega[sh], v.x, a);

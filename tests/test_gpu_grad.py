@@ -90,3 +90,30 @@ def test_autograd_function_matches_fa_grad():
     assert rel(to_host(U.grad), to_host(gU)) < 1e-12
     assert abs(mu.grad.item() - dmu) < 1e-12 * abs(dmu)
     assert rel(to_host(b.grad), to_host(gb)) < 1e-12
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 4])
+def test_chunked_gradient_equals_whole_and_bounds_memory(chunk):
+    """shift_chunk = k: the poles are solved k at a time.  Every x_s and lambda_s
+    comes from the same seed recurrence and the sums over s run in the same
+    order, so L, dL/dU, dL/dmu and dL/db equal the all-poles result bit for bit;
+    the lattice-sized device memory no longer grows with N_s (a fresh context
+    with twice the poles holds the same field bytes)."""
+    w = workload_case("wilson_4x4x4x8")
+    eta = to_dev(inputs.gaussian_spinor(w["dims"], w["seeds"]["eta"]))
+    b = to_dev(w["b"])
+    ctx = make_context(w["dims"], w["U"], w["mass"], w["mu"], w["c"], w["t_bc"], w["omega"], w["sigma"])
+    L0, g0, m0, b0, _ = ctx.grad(b, eta, ell=2, tol=1e-11)
+    ctx = make_context(w["dims"], w["U"], w["mass"], w["mu"], w["c"], w["t_bc"], w["omega"], w["sigma"])
+    L1, g1, m1, b1, st = ctx.grad(b, eta, ell=2, tol=1e-11, shift_chunk=chunk)
+    assert L1 == L0 and m1 == m0
+    assert np.array_equal(to_host(g1), to_host(g0))
+    assert np.array_equal(to_host(b1), to_host(b0))
+    assert st["status"] == 0
+    fields = []
+    for ns in (8, 16):
+        om, sg = fa.neuberger_poles(ns)
+        c2 = make_context(w["dims"], w["U"], w["mass"], w["mu"], w["c"], w["t_bc"], om, sg)
+        c2.grad(b, eta, ell=2, tol=1e-10, shift_chunk=4)
+        fields.append(c2.device_bytes()[0])
+    assert fields[0] == fields[1]

@@ -264,6 +264,34 @@ def test_single_equals_double_pass(ell):
     assert rel(y2, y1) < 1e-13
 
 
+@pytest.mark.parametrize("ell", [1, 2, 4])
+def test_fixed_cost_mode(ell):
+    """fixed_outer = M (the fixed-cost runs of Sec. 3, Fig. 2): the shift
+    recurrences truncated after M outer iterations.  Pins: a pole at sigma = 0
+    reproduces the seed recurrence's own iterate after M outer iterations (the
+    shifted system is then the seed system); the double-pass resolution of the
+    truncated recurrence equals the single-pass shift vectors; a fixed M past
+    the natural stop changes nothing."""
+    w = inputs.make_workload("wilson_4x4x4x8")
+    op = dirac.Operator(w["U"], w["mass"], w["mu"])
+    c = scale.power_scale(op.A, w["v0"], 100)
+    op = dirac.Operator(w["U"], w["mass"], w["mu"], c)
+    M = 5
+    x_seed, _ = ms.seed_recurrence(op.A, w["b"], ell, M)
+    st = ms.Stats()
+    xs = ms.multishift_single(op.A, w["b"], [0.0, 0.3], ell, 1e-300, fixed_outer=M, stats=st)
+    assert st.n_outer == M and list(st.iters_per_shift) == [M, M]
+    assert rel(xs[0], x_seed) < 1e-12
+    om, sg = poles.neuberger_poles(w["ns"])
+    xs = ms.multishift_single(op.A, w["b"], sg, ell, 1e-10, fixed_outer=M)
+    y2 = ms.multishift_double(op.A, w["b"], sg, om, ell, 1e-10, fixed_outer=M)
+    assert rel(y2, ms.pfe_from_shifts(xs, om)) < 1e-13
+    st = ms.Stats()
+    y_free = ms.multishift_double(op.A, w["b"], sg, om, ell, 1e-10, stats=st)
+    y_long = ms.multishift_double(op.A, w["b"], sg, om, ell, 1e-10, fixed_outer=st.n_outer + 5)
+    assert np.array_equal(y_long, y_free)
+
+
 def test_operation_counts_match_cost_table():
     """Sec. 3 table: #Mv = 2Ml (1-pass), 4Ml (2-pass); #dot = Ml(0.5l+3.5)
     (+1 residual norm per outer iteration for the convergence test)."""
