@@ -51,10 +51,12 @@ def parse():
     p.add_argument("--impl", default="fapath", choices=["fapath", "reference"])
     p.add_argument("--workload", default="wilson_16x16x16x32")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-large", action="store_true", help="skip the 32^3 x 64 variant of the default line")
+    p.add_argument("--no-batched", action="store_true", help="skip the 72-system batched variant of the default line")
     p.add_argument("--switch-resid", type=float, default=-1.0,
                    help="head/tail switch threshold of the mixed forms; < 0: 0.08/l^2 (on 16^3 x 32, "
                         "l = 2 the fastest threshold whose error floor stays below half of 1e-8); "
-                        "0: the library default 0.04/l^2")
+                        "0: the library default min(0.04/l^2, 0.4/l^6)")
     p.add_argument("--quick", action="store_true",
                    help="headline solve only at tol 1e-9 (no comparisons, e2e or CPU baseline)")
     p.add_argument("--hop-only", action="store_true",
@@ -380,16 +382,16 @@ def run_ns_sweep(args):
     ctx.close()
 
 
-def run_batched(args):
+def batched_measure(steps, warmup, ells=None, one_at_a_time=True, name="wilson_batched_72"):
     """72 systems: 12 spin-colour point sources on each of 6 lattices of three
     shapes (2 x 8^4, 2 x 12^3 x 24, 2 x 16^3 x 32), mu_k ~ U[0, 0.2], 16 Neuberger
     poles, FP32 bulk, pseudo-double-pass.  One step = one fa_apply_f_batched
-    call over all 72 systems (systems of a shape share every launch); compared
-    with the same 72 solves one at a time."""
+    call over all 72 systems; compared with the same 72 solves one at a time,
+    and the first source of every lattice against an FP64 solve."""
     import torch
     import inputs
     import paper_1010_2592_gb300 as fa
-    w = inputs.make_batched_workload(args.workload)
+    w = inputs.make_batched_workload(name)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctxs, srcs, owners = [], [], []
@@ -410,44 +412,137 @@ def run_batched(args):
         owners.append(owner)
     torch.cuda.synchronize()
     free, _ = torch.cuda.mem_get_info()
-    out = {"mode": "batched", "workload": args.workload, "systems": len(ctxs), "ns": w["ns"],
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {"workload": name, "systems": len(ctxs), "ns": w["ns"],
            "lattices": ["x".join(map(str, l["dims"])) for l in w["lattice_systems"]],
-           "mu": [round(l["mu"], 4) for l in w["lattice_systems"]], "precision": "f32", "form": "pseudo"}
-    for ell in w["ell"]:
-        kw = dict(ell=ell, tol=w["tol"], max_outer=4000, mode="pseudo", precision="f32",
+           "mu": [round(l["mu"], 4) for l in w["lattice_systems"]], "form": "pseudo",
+           "launches": "one launch per kernel for all 72 systems (work tables); FP32 sweeps by lattice group",
+           "l2": "flushed before every timed step (512 MB write)"}
+    tune = fa.autotune_batched(ctxs, reps=5)   # multi-RHS sweep shape for this batch (untimed)
+    out["mrhs_shape"] = {"rhs_per_block": tune["rhs_per_block"], "min_blocks": tune["min_blocks"]}
+    # FP32 bulk at l = 2 and l = 4; at l = 4 the FP32-only form stays above 1e-6
+    # (power-basis cancellation), so the same batch also runs with a double-float head
+    runs = [(ell, "f32") for ell in (ells or w["ell"])] + [(4, "mixed_df")]
+    for ell, precision in runs:
+        kw = dict(ell=ell, tol=w["tol"], max_outer=4000, mode="pseudo", precision=precision,
                   store_gb=0.4 * free / 1e9, graph=True)
         ys, st = fa.apply_f_batched(ctxs, srcs, **kw)          # warm-up (also instantiates graphs)
-        for _ in range(max(0, args.warmup - 1)):
+        for _ in range(max(0, warmup - 1)):
             fa.apply_f_batched(ctxs, srcs, **kw)
         times = []
-        for _ in range(args.steps):
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ys, st = fa.apply_f_batched(ctxs, srcs, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        row = {"ms_batched": statistics.mean(times), "systems_per_s": len(ctxs) / (statistics.mean(times) * 1e-3),
+               "outer_iters_max": max(x["outer_iters"] for x in st),
+               "outer_iters_min": min(x["outer_iters"] for x in st)}
+        if one_at_a_time:
+            # the same 72 solves, one at a time, each with its share of the store budget
+            kw1 = dict(kw, store_gb=kw["store_gb"] / len(ctxs))
+            for ctx, b in zip(ctxs[:3], srcs[:3]):
+                ctx.apply_f(b, **kw1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ys, st = fa.apply_f_batched(ctxs, srcs, **kw)
+            for ctx, b in zip(ctxs, srcs):
+                ctx.apply_f(b, **kw1)
             torch.cuda.synchronize()
-            times.append((time.perf_counter() - t0) * 1e3)
-        # the same 72 solves, one at a time, each with its share of the store budget
-        kw1 = dict(kw, store_gb=kw["store_gb"] / len(ctxs))
-        for ctx, b in zip(ctxs[:3], srcs[:3]):
-            ctx.apply_f(b, **kw1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for ctx, b in zip(ctxs, srcs):
-            ctx.apply_f(b, **kw1)
-        torch.cuda.synchronize()
-        one = (time.perf_counter() - t0) * 1e3
+            one = (time.perf_counter() - t0) * 1e3
+            row.update(ms_one_at_a_time=one, speedup=one / statistics.mean(times))
         # accuracy of the FP32 bulk against an FP64 solve, first source of every lattice
         errs = []
         for k in range(0, len(ctxs), 12):
             r64 = ctxs[k].apply_f(srcs[k], ell=ell, tol=1e-12, max_outer=4000, mode="double", precision="f64")
             errs.append(float((torch.linalg.vector_norm(ys[k] - r64.y) / torch.linalg.vector_norm(r64.y)).item()))
-        out[f"ell{ell}"] = {"ms_batched": statistics.mean(times), "ms_one_at_a_time": one,
-                             "speedup": one / statistics.mean(times),
-                             "systems_per_s": len(ctxs) / (statistics.mean(times) * 1e-3),
-                             "outer_iters_max": max(x["outer_iters"] for x in st),
-                             "outer_iters_min": min(x["outer_iters"] for x in st),
-                             "rel_err_vs_f64_per_lattice": errs}
-    print(json.dumps(out), flush=True)
+        row["rel_err_vs_f64_per_lattice"] = errs
+        row["precision"] = precision
+        out[f"ell{ell}" + ("" if precision == "f32" else "_" + precision)] = row
+    for c_ in ctxs:
+        c_.close()
+    return out
+
+
+def run_batched(args):
+    print(json.dumps(dict(mode="batched", **batched_measure(args.steps, args.warmup))), flush=True)
+
+
+def large_measure(steps, warmup, name="wilson_32x32x32x64"):
+    """The 32^3 x 64 workload (l 4, 32 poles): pseudo-double-pass with a
+    double-float head and FP32 tail, at the loosest tolerance of TOLS whose
+    result meets 1e-8 against an FP64 double-pass solve at tol 1e-12 (the FP64
+    oracle would take hours here); L2 flushed before every timed step; the FP32
+    sweep's event-timed bandwidth inside the instrumented repeat."""
+    import torch
+    import inputs
+    import paper_1010_2592_gb300 as fa
+    w = inputs.make_workload(name)
+    dims, ell = w["dims"], w["ell"]
+    V = int(np.prod(dims))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = fa.Context(dims, stream)
+    ctx.set_gauge(torch.from_numpy(w["U"]).cuda())
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], 1.0)
+    c = ctx.estimate_scale(torch.from_numpy(w["v0"]).cuda(), 100)
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], c)
+    ctx.set_poles(*fa.neuberger_poles(w["ns"]))
+    b = torch.from_numpy(w["b"]).cuda()
+    ns = w["ns"]
+    del w
+    free, _ = torch.cuda.mem_get_info()
+    ref = ctx.apply_f(b, ell=ell, tol=1e-12, max_outer=4000, mode="double", precision="f64")
+    yref, yn = ref.y, torch.linalg.vector_norm(ref.y).item()
+    kw = dict(ell=ell, max_outer=4000, mode="pseudo", precision="mixed_df", switch_resid=0.0,
+              graph=True, store_gb=0.5 * free / 1e9)
+    pick = None
+    for tol in TOLS:
+        r = ctx.apply_f(b, tol=tol, check=False, **kw)
+        e = (torch.linalg.vector_norm(r.y - yref) / yn).item() if r.stats["status"] == 0 else float("inf")
+        pick = (tol, e, r.stats)
+        if e <= TARGET:
+            break
+    tol, e, st = pick
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        ctx.apply_f(b, tol=tol, **kw)
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.apply_f(b, tol=tol, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ctx.hop_timing_reset()
+    ctx.apply_f(b, tol=tol, hop_timing=True, **dict(kw, graph=False))
+    hop_ms, hop_n = ctx.hop_timing("f32", dot=False)
+    peak, _ = measured_hbm_peak()
+    gbs = 384.0 * V / (hop_ms * 1e-3) / 1e9 if hop_ms else None
+    out = {"workload": name, "lattice": "x".join(map(str, dims)), "ell": ell, "ns": ns,
+           "ms": statistics.mean(times), "tol": tol, "rel_err_vs_f64": e, "meets_1e-8": e <= TARGET,
+           "reference": "the library's FP64 double-pass solve at tol 1e-12", "outer_iters": st["outer_iters"],
+           "switch_outer": st["switch_outer"], "stored_outer": st["stored_outer"],
+           "hop_f32_plain": {"mean_launch_ms": hop_ms, "launches": hop_n, "gbs": gbs,
+                             "frac_of_measured_hbm": gbs / peak if gbs else None,
+                             "bytes_per_launch": 384.0 * V},
+           "l2": "flushed before every timed step (512 MB write)"}
+    ctx.close()
+    return out
+
+
+def measured_hbm_peak():
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -684,11 +779,7 @@ def main():
     #   bound by FP32 issue; 11,650 thread instructions per site, the ncu
     #   instruction count of one plain 16^3 x 32 launch (smsp__inst_executed x 32
     #   / V), against 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3 T instructions/s.
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak, peak_src = 6800.0, "fallback"
-    if os.path.exists(peaks_path):
-        with open(peaks_path) as f:
-            peak, peak_src = float(json.load(f)["hbm_gbs"]), "measured"
+    peak, peak_src = measured_hbm_peak()
     over = "the instrumented repeat of the timed steps (direct launches, CUDA events around each sweep launch)"
 
     def roof(kernel, bound, per_launch, ms, n, unit, pk, pk_src, what, scale):
@@ -756,6 +847,18 @@ def main():
         "gpu_launches_total_timed": head_launches,
         "clocks": clk,
     }
+    # the other configurations of the workload family, measured in the same run:
+    # the 32^3 x 64 lattice (l 4, 32 poles) and the 72-system batch
+    if not args.no_large:
+        try:
+            line["variants"]["large_32x32x32x64"] = large_measure(max(1, min(args.steps, 2)), 1)
+        except Exception as ex:   # reported, never fatal to the bench line
+            line["variants"]["large_32x32x32x64"] = {"error": f"{type(ex).__name__}: {ex}"}
+    if not args.no_batched:
+        try:
+            line["variants"]["batched_72"] = batched_measure(max(1, min(args.steps, 2)), 1, one_at_a_time=False)
+        except Exception as ex:
+            line["variants"]["batched_72"] = {"error": f"{type(ex).__name__}: {ex}"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the oracle's own outer-iteration count at the headline's tolerance
         outer_ref, ref_tol = golden_outer_iters(args.workload, tol_h)

@@ -35,7 +35,7 @@ EXPORTS = (
     "fa_apply_f", "fa_apply_sign", "fa_apply_overlap", "fa_apply_sign_deflated", "fa_apply_f_host", "fa_sync", "fa_launch_count", "fa_hop_timing",
     "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
-    "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune",
+    "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune", "fa_autotune_batched",
 )
 
 # FP32 sweep launch shapes (fa_hop_shape)
@@ -124,6 +124,7 @@ def load_library(path=LIB_PATH):
         "fa_set_hop_shape": (I, [P, I]),
         "fa_get_hop_shape": (I, [P]),
         "fa_autotune": (I, [P, I, ctypes.POINTER(D)]),
+        "fa_autotune_batched": (I, [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), I]),
         "fa_status_string": (ctypes.c_char_p, [I]),
         "fa_last_error": (ctypes.c_char_p, []),
         "fa_version": (ctypes.c_char_p, []),
@@ -177,6 +178,22 @@ def apply_f_batched(contexts, sources, check=True, **kw):
     if check:
         _check(rc, "fa_apply_f_batched")
     return ys, [s.as_dict() for s in st]
+
+
+def autotune_batched(contexts, reps=10):
+    """Pick the launch shape of the batched multi-RHS FP32 sweep for this batch
+    (fa_autotune_batched): right-hand sides per block and blocks per SM, kept in
+    contexts[0].  Returns {"rhs_per_block", "min_blocks", "times_ms"}."""
+    lib = load_library()
+    n = len(contexts)
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in contexts])
+    rpb, mb = ctypes.c_int(), ctypes.c_int()
+    times = (ctypes.c_double * 14)()
+    _check(lib.fa_autotune_batched(hs, n, int(reps), ctypes.byref(rpb), ctypes.byref(mb), times, 14),
+           "fa_autotune_batched")
+    grid = [(r, m) for r in (1, 2, 3, 4, 6, 12, 16) for m in (7, 4)]
+    return {"rhs_per_block": rpb.value, "min_blocks": mb.value,
+            "times_ms": {f"{r}x{m}": float(t) for (r, m), t in zip(grid, times)}}
 
 
 def _torch():

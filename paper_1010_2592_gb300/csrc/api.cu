@@ -416,41 +416,24 @@ int fa_apply_sign_deflated(fa_ctx* c, const double* b, double* out, int k, const
 int fa_apply_f_batched(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y,
                        const fa_solver_params* p, fa_solver_stats* stats) {
     if (!ctxs || !b || !y || !p || n < 1 || n > 4096) return FA_EINVAL;
-    // group the systems by lattice shape; each group shares every launch
-    std::vector<int> done(n, 0);
-    int rc_all = FA_OK;
-    for (int i = 0; i < n; ++i) {
-        if (done[i]) continue;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i] || !b[i] || !y[i]) return FA_EINVAL;
+    // every system in one solve: each kernel launch serves all of them, whatever
+    // their lattice shapes (work tables), and the FP32 sweeps read a lattice's
+    // links once per tile for all the sources that share its gauge field
+    std::vector<fa_solver_stats> st(n);
+    const int rc = solve_batch(ctxs, n, b, y, nullptr, p, st.data());
+    if (stats)
+        for (int i = 0; i < n; ++i) stats[i] = st[i];
+    return rc;
+}
+
+int fa_autotune_batched(fa_ctx* const* ctxs, int n, int reps, int* rhs_per_block, int* min_blocks, double* times_ms,
+                        int ntimes) {
+    if (!ctxs || n < 1 || n > 4096 || reps < 1 || !rhs_per_block || !min_blocks) return FA_EINVAL;
+    for (int i = 0; i < n; ++i)
         if (!ctxs[i]) return FA_EINVAL;
-        std::vector<int> idx;
-        for (int k = i; k < n; ++k) {
-            if (!ctxs[k]) return FA_EINVAL;
-            const Geom& a = ctxs[i]->g;
-            const Geom& g = ctxs[k]->g;
-            if (!done[k] && a.X == g.X && a.Y == g.Y && a.Z == g.Z && a.T == g.T) {
-                idx.push_back(k);
-                done[k] = 1;
-            }
-        }
-        std::vector<fa_ctx*> cs;
-        std::vector<const double*> bs;
-        std::vector<double*> ys;
-        for (int k : idx) {
-            cs.push_back(ctxs[k]);
-            bs.push_back(b[k]);
-            ys.push_back(y[k]);
-        }
-        std::vector<fa_solver_stats> st(idx.size());
-        // an explicit store budget covers the whole call: each group gets its share
-        fa_solver_params pg = *p;
-        if (pg.store_gb > 0.0) pg.store_gb = p->store_gb * (double)idx.size() / (double)n;
-        const int rc = solve_batch(cs.data(), (int)cs.size(), bs.data(), ys.data(), nullptr, &pg, st.data());
-        if (stats)
-            for (size_t j = 0; j < idx.size(); ++j) stats[idx[j]] = st[j];
-        if (rc != FA_OK && rc_all == FA_OK) rc_all = rc;
-        if (rc == FA_EINVAL || rc == FA_ECUDA || rc == FA_ESTATE || rc == FA_ENOMEM) return rc;
-    }
-    return rc_all;
+    return autotune_batch(ctxs, n, reps, rhs_per_block, min_blocks, times_ms, ntimes);
 }
 
 int fa_apply_f_host(fa_ctx* c, const double* b_host, double* y_host, const fa_solver_params* p,

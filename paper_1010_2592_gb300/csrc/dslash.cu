@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kRowThreads, rows_min_blocks<DOT>())
 hop_rows_kernel(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb,
                 R bc, SpinorView<R> dotv, double2* partials, const int* done) {
     if (done != nullptr && *done) return;
-    cx<R> dres[1] = {hop_rows_body<R, G5IN, G5OUT, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv)};
+    cx<R> dres[1] = {hop_rows_body<R, G5IN, G5OUT, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv, blockIdx.x)};
     if (DOT) block_reduce_store<1, R, kRowThreads>(dres, partials, 0, blockIdx.x);
 }
 

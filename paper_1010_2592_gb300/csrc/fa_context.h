@@ -88,6 +88,8 @@ struct fa_ctx {
     fa::DevBuf store64, store32;         // pseudo-double-pass occurrence stores
     fa::DevBuf snap64, snap32;           // seed state at the first unstored outer iteration
     fa::DevBuf descbuf, flagbuf;         // batch descriptors and done flags (first context of a batch)
+    fa::DevBuf tabbuf;                   // batch work tables and lattice groups (first context of a batch)
+    int mrhs_rpb = 0, mrhs_mb = 0;       // multi-RHS FP32 sweep shape of batches led by this context (0: default)
     fa::DevBuf xrel, brel, snapx;        // reliable updates: seed solution, packed source, snapshot
     fa::DevBuf defl;                     // deflated sign: partial sums, coefficients, projected source
     std::vector<fa::GraphEntry> graphs;  // captured outer iterations
@@ -131,6 +133,8 @@ int solve(fa_ctx* c, const double* b_canon, double* y_canon, double* const* xs_c
 int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y_canon,
                 double* const* xs_canon, const fa_solver_params* p, fa_solver_stats* stats);
 int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out);
+int autotune_batch(fa_ctx* const* ctxs, int n, int reps, int* rhs_per_block, int* min_blocks, double* times_ms,
+                   int ntimes);
 int apply_sign(fa_ctx* c, const double* b, double* out, const fa_solver_params* p, fa_solver_stats* stats,
                bool overlap);
 int apply_sign_deflated(fa_ctx* c, const double* b, double* out, int k, const double* lambda, const double* R,

@@ -74,7 +74,7 @@ k_hop_gram(GramHop A, const SolverDev* __restrict__ ds) {
         }
     }
     block_reduce_store<NG, float, NT>(red, A.part, gridDim.x, blockIdx.x);
-    if (last_block(d.st)) sc_mr_seed<L, true>(d, gridDim.x);
+    if (last_block(d.st, gridDim.x)) sc_mr_seed<L, true>(d, gridDim.x);
 }
 
 }  // namespace fa

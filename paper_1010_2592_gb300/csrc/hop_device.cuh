@@ -264,8 +264,9 @@ __device__ __forceinline__ void recon1_c(dcs acc[4], dcs h0, dcs h1) {
 constexpr int kRowSites = 64;
 constexpr int kRowThreads = 3 * kRowSites;
 __device__ __forceinline__ int row_of_thread() { return (int)(threadIdx.x >> 6); }
-__device__ __forceinline__ int site_of_thread() {
-    return (int)blockIdx.x * kRowSites + (int)(threadIdx.x & (kRowSites - 1));
+// site of the thread in block bx of the sweep
+__device__ __forceinline__ int site_of_thread(int bx) {
+    return bx * kRowSites + (int)(threadIdx.x & (kRowSites - 1));
 }
 inline int row_blocks(int V) { return (V + kRowSites - 1) / kRowSites; }
 
@@ -391,8 +392,8 @@ __device__ __forceinline__ void hop_site_row_sh(const Geom& g, const LinkView<df
 template <typename R, bool G5IN, bool G5OUT, bool DOT>
 __device__ __forceinline__ cx<R> hop_rows_body(const Geom& g, const LinkView<R>& U, const SpinorView<R>& in,
                                                const SpinorView<R>& out, R cdiag, R chop, R ef, R eb, R bc,
-                                               const SpinorView<R>& dotv) {
-    const int a = row_of_thread(), s = site_of_thread();
+                                               const SpinorView<R>& dotv, int bx) {
+    const int a = row_of_thread(), s = site_of_thread(bx);
     cx<R> dres = czero<R>();
     cx<R> o[4];
     hop_site_row_sh<G5IN, G5OUT>(g, U, in, s, a, s < g.V, cdiag, chop, ef, eb, bc, o);

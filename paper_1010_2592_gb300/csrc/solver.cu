@@ -252,6 +252,13 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     d.eb = std::exp(-c->mu);
     d.bc = c->t_bc;
     d.scale = c->scale_c;
+    d.fdiag1 = host_cvt<float>(1.0 * d.diag);
+    d.fhop1 = host_cvt<float>(-0.5 * 1.0);
+    d.fdiag2 = host_cvt<float>(d.scale * d.diag);
+    d.fhop2 = host_cvt<float>(-0.5 * d.scale);
+    d.fef = host_cvt<float>(d.ef);
+    d.feb = host_cvt<float>(d.eb);
+    d.fbc = host_cvt<float>(d.bc);
     char* sb = c->shiftbuf.as<char>();
     d.sigma = reinterpret_cast<const double*>(sb);
     d.omega = reinterpret_cast<const double*>(sb + kMaxShifts * sizeof(double));
@@ -291,14 +298,30 @@ static SolverDev make_dev(fa_ctx* c, const Layout& Lo) {
     return d;
 }
 
-// A batch: systems of one lattice shape whose kernels share each launch.
+// Work tables of a batch launch (see `where` in solver_kernels.cuh): per kernel
+// kind, one entry (system, block, vector blocks, tickets) per block of the launch.
+enum TabKind { TB_VEC = 0, TB_VECX, TB_RG, TB_RGX, TB_HOP, TB_ROWS, TB_KINDS };
+
+// A batch: systems whose kernels share each launch.  One system, or systems of
+// one lattice shape without work tables (grid.y = systems), or systems of any
+// shapes with work tables (grid.x = the table).
 struct Batch {
     fa_ctx* c0 = nullptr;                 // owner of the stream and the descriptor array
     std::vector<fa_ctx*> sys;
     std::vector<SolverDev> host;          // host copy of the descriptors
     SolverDev* dev = nullptr;             // device array
     int* flags = nullptr;                 // device done flags
-    Layout Lo{};
+    Layout Lo{};                          // layout of system 0 (all systems without tables)
+    std::vector<Layout> lo;               // layout of each system
+    bool tables = false;                  // launches follow the work tables
+    const int4* tab[TB_KINDS] = {};       // device tables
+    int tab_n[TB_KINDS] = {};             // their lengths (blocks of the launch)
+    const GroupDev* groups = nullptr;     // systems sharing a gauge field (multi-RHS FP32 sweep)
+    const int4* items = nullptr;          // (group, tile, first, end) per block of that sweep
+    int n_items = 0;
+    int rhs_per_block = 1;
+    int mrhs_min_blocks = kHopNarrowBlocks;
+    std::vector<char> tab_host;           // staging of the tables (alive until the solve's final sync)
     int n = 0;
     bool use_graph = false;
     bool pdl = true;                      // programmatic dependent launch inside an outer iteration
@@ -354,10 +377,24 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     // sites for 256 threads, a second pass for one thread of every block).
     // k_gram / k_mr use vg where their register budget gives kVecBlocks
     // resident blocks per SM, else the reduction grid.
-    const dim3 gs(nb, n), gv(vg, n), gvx(vg + 1, n);
-    const dim3 gg(gram_min_blocks<R, L>() >= kVecBlocks ? vg : rg, n);
-    const int mg = mr_min_blocks<R, L>() >= kVecBlocks ? vg : rg;
-    const dim3 gm(mg, n), gmx(mg + 1, n);
+    dim3 gs(nb, n), gv(vg, n), gvx(vg + 1, n);
+    const bool gram_vec = gram_min_blocks<R, L>() >= kVecBlocks, mr_vec = mr_min_blocks<R, L>() >= kVecBlocks;
+    dim3 gg(gram_vec ? vg : rg, n);
+    const int mg = mr_vec ? vg : rg;
+    dim3 gm(mg, n), gmx(mg + 1, n);
+    // work tables (systems of different lattice shapes in one launch)
+    const int4 *tv = nullptr, *tvx = nullptr, *tg = nullptr, *tm = nullptr, *tmx = nullptr;
+    if (B.tables) {
+        auto T = [&](int k, dim3& g, const int4*& t) {
+            g = dim3(B.tab_n[k]);
+            t = B.tab[k];
+        };
+        T(TB_VEC, gv, tv);
+        T(TB_VECX, gvx, tvx);
+        T(gram_vec ? TB_VEC : TB_RG, gg, tg);
+        T(mr_vec ? TB_VEC : TB_RG, gm, tm);
+        T(mr_vec ? TB_VECX : TB_RGX, gmx, tmx);
+    }
     const SolverDev* ds = B.dev;
     cudaStream_t st = c->stream;
     constexpr int kind = rp_of<R>() == RP64 ? 0 : (rp_of<R>() == RP32 ? 1 : 2);
@@ -427,13 +464,48 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
             FA_LAUNCHED(c, "k_hop1");
             return FA_OK;
         }
+        if constexpr (rp_of<R>() == RP32) {
+            if (B.items != nullptr) {
+                // the sources of one lattice share each tile's links
+                const dim3 gi(B.n_items);
+                const ScalarStep e = dot ? step : none;
+                if (B.mrhs_min_blocks == 4) {
+                    if (dot) launch(pdl, k_hop_mrhs<true, 4>, gi, kHopNarrowThreads, st, ds, B.groups, B.items, in_sel,
+                                    in_j, out_sel, out_j, second, p2, e);
+                    else launch(pdl, k_hop_mrhs<false, 4>, gi, kHopNarrowThreads, st, ds, B.groups, B.items, in_sel,
+                                in_j, out_sel, out_j, second, p2, e);
+                } else {
+                    if (dot) launch(pdl, k_hop_mrhs<true, kHopNarrowBlocks>, gi, kHopNarrowThreads, st, ds, B.groups,
+                                    B.items, in_sel, in_j, out_sel, out_j, second, p2, e);
+                    else launch(pdl, k_hop_mrhs<false, kHopNarrowBlocks>, gi, kHopNarrowThreads, st, ds, B.groups,
+                                B.items, in_sel, in_j, out_sel, out_j, second, p2, e);
+                }
+                if (timing) hop_timing_end(c);
+                FA_LAUNCHED(c, "k_hop_mrhs");
+                return FA_OK;
+            }
+        }
         if constexpr (rp_of<R>() == RPDF) {
-            const dim3 gw(row_blocks(h0.V), n);
-            if (dot) launch(pdl, k_hop_sys_rows<R, true>, gw, kRowThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, step);
-            else launch(pdl, k_hop_sys_rows<R, false>, gw, kRowThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, none);
+            dim3 gw(row_blocks(h0.V), n);
+            const int4* tw = nullptr;
+            if (B.tables) {
+                gw = dim3(B.tab_n[TB_ROWS]);
+                tw = B.tab[TB_ROWS];
+            }
+            if (dot) launch(pdl, k_hop_sys_rows<R, true>, gw, kRowThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2,
+                            step, tw);
+            else launch(pdl, k_hop_sys_rows<R, false>, gw, kRowThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2,
+                        none, tw);
         } else {
-            if (dot) launch(pdl, k_hop_sys<R, true>, gs, kThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, step);
-            else launch(pdl, k_hop_sys<R, false>, gs, kThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, none);
+            const int4* th = nullptr;
+            if (B.tables) {
+                gs = dim3(B.tab_n[TB_HOP]);
+                th = B.tab[TB_HOP];
+            }
+            if (dot) launch(pdl, k_hop_sys<R, true>, gs, kThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, step,
+                            th);
+            else launch(pdl, k_hop_sys<R, false>, gs, kThreads, st, ds, in_sel, in_j, out_sel, out_j, second, p2, none,
+                        th);
         }
         if (timing) hop_timing_end(c);
         FA_LAUNCHED(c, "k_hop_sys");
@@ -474,18 +546,18 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
     // convergence after |r_0|^2); the shift parts in block 0 of the next
     // vector kernel (double-pass forms) or with the seed part (single pass).
     for (int j = 0; j < L; ++j) {
-        launch(j > 0 && pdl, k_update_u<R>, gv, kThreads, st, ds, j, p2);
+        launch(j > 0 && pdl, k_update_u<R>, gv, kThreads, st, ds, j, p2, tv);
         FA_LAUNCHED(c, "k_update_u");
         FA_TRY(hop(0, j, 2, 0, 0, false, none));                                   // tmp = g5 D u_j
         const ScalarStep alpha{single ? STEP_ALPHA_ALL : STEP_ALPHA, j};
         FA_TRY(hop(2, 0, 0, j + 1, 1, !pass2, pass2 ? none : alpha));              // u_{j+1}
         if (pass2) {
-            launch(pdl, k_update_r<R, true, false>, gv, kThreads, st, ds, j, p2);
+            launch(pdl, k_update_r<R, true, false>, gv, kThreads, st, ds, j, p2, tv);
         } else if (single) {
-            if constexpr (rp_of<R>() == RP64) launch(pdl, k_update_r<R, false, true>, gv, kThreads, st, ds, j, p2);
+            if constexpr (rp_of<R>() == RP64) launch(pdl, k_update_r<R, false, true>, gv, kThreads, st, ds, j, p2, tv);
         } else {
             // block 0: shift part of sub-step j beside the vector blocks
-            launch(pdl, k_update_r<R, false, false, true>, gvx, kThreads, st, ds, j, p2);
+            launch(pdl, k_update_r<R, false, false, true>, gvx, kThreads, st, ds, j, p2, tvx);
         }
         FA_LAUNCHED(c, "k_update_r");
         FA_TRY(hop(1, j, 2, 0, 0, false, none));                                   // tmp = g5 D r_j
@@ -497,18 +569,18 @@ static int enqueue_outer(Batch& B, bool pass2, bool single, bool head, bool reli
         }
     }
     if (!pass2 && !gram_hop) {
-        launch(pdl, k_gram<R, L>, gg, kThreads, st, ds, single ? 1 : 0);
+        launch(pdl, k_gram<R, L>, gg, kThreads, st, ds, single ? 1 : 0, tg);
         FA_LAUNCHED(c, "k_gram");
     }
     const ScalarStep conv = pass2 ? none : ScalarStep{STEP_CONV, head ? 1 : 0};
     if (pass2) {
-        launch(pdl, k_mr<R, L, true, false, false>, gm, kThreads, st, ds, p2, none);
+        launch(pdl, k_mr<R, L, true, false, false>, gm, kThreads, st, ds, p2, none, tm);
     } else if (single) {
         if constexpr (rp_of<R>() == RP64)
-            launch(pdl, k_mr<R, L, false, true, true>, gm, kThreads, st, ds, p2, reliable ? none : conv);
+            launch(pdl, k_mr<R, L, false, true, true>, gm, kThreads, st, ds, p2, reliable ? none : conv, tm);
     } else {
         // block 0: shift part of the MR step beside the vector blocks
-        launch(pdl, k_mr<R, L, false, false, true, true>, gmx, kThreads, st, ds, p2, reliable ? none : conv);
+        launch(pdl, k_mr<R, L, false, false, true, true>, gmx, kThreads, st, ds, p2, reliable ? none : conv, tmx);
     }
     FA_LAUNCHED(c, "k_mr");
     if (reliable) {
@@ -569,6 +641,11 @@ static std::vector<unsigned long long> graph_signature(const Batch& B) {
     const fa_ctx* c = B.c0;
     s.push_back((unsigned long long)B.pdl);
     s.push_back((unsigned long long)(long long)c->hop_shape);
+    // batches: the tables' addresses and lengths set the launches' grids
+    p(c->tabbuf.p);
+    for (int k = 0; k < TB_KINDS; ++k) s.push_back((unsigned long long)B.tab_n[k]);
+    s.push_back((unsigned long long)B.n_items);
+    s.push_back((unsigned long long)B.mrhs_min_blocks);
     p(c->io64a.p);
     p(c->io64b.p);
     if (B.n == 1) {
@@ -654,7 +731,7 @@ static int launch_sweep(Batch& B) {
 static int load_source(Batch& B, int i, const double* b, int rp) {
     fa_ctx* c = B.sys[i];
     cudaStream_t st = B.c0->stream;
-    const int V = B.Lo.V;
+    const int V = B.lo[i].V;
     if (rp != RP32) {
         if (rp == RP64) FA_TRY(launch_pack_spinor_f64(c->g, b, c->r64.as<double2>(), st));
         else FA_TRY(launch_pack_spinor_df(c->g, b, c->r64.as<float4>(), st));
@@ -689,7 +766,7 @@ static int switch_to_f32(Batch& B, int i, int from) {
 // r_0, u_0, rt of system i <-> its snapshot buffer
 static int snapshot(Batch& B, int i, bool f64, bool restore) {
     fa_ctx* c = B.sys[i];
-    const size_t sb = f64 ? B.Lo.vs64 * sizeof(double2) : B.Lo.vs32 * sizeof(float4);
+    const size_t sb = f64 ? B.lo[i].vs64 * sizeof(double2) : B.lo[i].vs32 * sizeof(float4);
     char* snap = f64 ? c->snap64.as<char>() : c->snap32.as<char>();
     void* v[3] = {f64 ? c->r64.p : c->r32.p, f64 ? c->u64.p : c->u32.p, f64 ? c->rt64.p : c->rt32.p};
     for (int k = 0; k < 3; ++k) {
@@ -698,7 +775,7 @@ static int snapshot(Batch& B, int i, bool f64, bool restore) {
         FA_CUDA(cudaMemcpyAsync(dst, src, sb, cudaMemcpyDeviceToDevice, B.c0->stream), "snapshot");
     }
     if (B.host[i].x64) {   // reliable updates: the seed solution belongs to the state
-        const size_t xb = B.Lo.vs64 * sizeof(double2);
+        const size_t xb = B.lo[i].vs64 * sizeof(double2);
         void* dst = restore ? (void*)B.host[i].x64 : c->snapx.p;
         const void* src = restore ? c->snapx.p : (const void*)B.host[i].x64;
         FA_CUDA(cudaMemcpyAsync(dst, src, xb, cudaMemcpyDeviceToDevice, B.c0->stream), "snapshot x");
@@ -715,7 +792,93 @@ static int read_states(Batch& B, std::vector<DevState>& hs) {
     return FA_OK;
 }
 
-// ------------------------------------------------------------------ the solve (a batch of n systems)
+// Work tables and lattice groups of a batch of several systems, in one device
+// buffer of the first context.  Shift blocks come first in their tables (they
+// run the per-shift FP64 recurrences, the longest blocks of a launch).
+static int build_tables(Batch& B) {
+    fa_ctx* c0 = B.c0;
+    const int n = B.n;
+    std::vector<int4> t[TB_KINDS];
+    auto blocks = [&](std::vector<int4>& v, int i, int nb, bool xs) {
+        for (int b = 0; b < nb; ++b) v.push_back(make_int4(i, b, nb, nb + (xs ? 1 : 0)));
+    };
+    for (int i = 0; i < n; ++i) {
+        t[TB_VECX].push_back(make_int4(i, -1, B.lo[i].vgrid, B.lo[i].vgrid + 1));
+        t[TB_RGX].push_back(make_int4(i, -1, B.lo[i].red_grid, B.lo[i].red_grid + 1));
+    }
+    for (int i = 0; i < n; ++i) {
+        const Layout& lo = B.lo[i];
+        blocks(t[TB_VEC], i, lo.vgrid, false);
+        blocks(t[TB_VECX], i, lo.vgrid, true);
+        blocks(t[TB_RG], i, lo.red_grid, false);
+        blocks(t[TB_RGX], i, lo.red_grid, true);
+        blocks(t[TB_HOP], i, lo.nblk, false);
+        blocks(t[TB_ROWS], i, row_blocks(lo.V), false);
+    }
+    // lattice groups for the FP32 multi-RHS sweep: systems sharing the packed
+    // links and the lattice shape, at most kMaxRhs per group
+    std::vector<GroupDev> groups;
+    std::vector<const void*> gkey;
+    std::vector<int4> items;
+    if (B.Lo.need32) {
+        for (int i = 0; i < n; ++i) {
+            const void* key = B.host[i].links32;
+            int gi = -1;
+            for (size_t g = 0; g < groups.size(); ++g)
+                if (gkey[g] == key && groups[g].nsys < kMaxRhs && B.host[groups[g].sys[0]].V == B.host[i].V &&
+                    B.host[groups[g].sys[0]].g.X == B.host[i].g.X && B.host[groups[g].sys[0]].g.Y == B.host[i].g.Y &&
+                    B.host[groups[g].sys[0]].g.Z == B.host[i].g.Z)
+                    gi = (int)g;
+            if (gi < 0) {
+                GroupDev gd{};
+                gd.nsys = 0;
+                gd.ntile = (B.host[i].V + kHopNarrowThreads - 1) / kHopNarrowThreads;
+                groups.push_back(gd);
+                gkey.push_back(key);
+                gi = (int)groups.size() - 1;
+            }
+            groups[gi].sys[groups[gi].nsys++] = i;
+        }
+        const int rpb = c0->mrhs_rpb > 0 ? c0->mrhs_rpb : kMaxRhs;
+        for (size_t g = 0; g < groups.size(); ++g)
+            for (int tile = 0; tile < groups[g].ntile; ++tile)
+                for (int r0 = 0; r0 < groups[g].nsys; r0 += rpb)
+                    items.push_back(make_int4((int)g, tile, r0, std::min(r0 + rpb, groups[g].nsys)));
+        B.rhs_per_block = rpb;
+        B.mrhs_min_blocks = c0->mrhs_mb == 4 ? 4 : kHopNarrowBlocks;
+    }
+    size_t off[TB_KINDS + 2], bytes = 0;
+    for (int k = 0; k < TB_KINDS; ++k) {
+        off[k] = bytes;
+        bytes += t[k].size() * sizeof(int4);
+    }
+    off[TB_KINDS] = bytes;
+    bytes += items.size() * sizeof(int4);
+    off[TB_KINDS + 1] = bytes;
+    bytes += groups.size() * sizeof(GroupDev);
+    FA_CUDA(c0->tabbuf.ensure(std::max<size_t>(bytes, 16)), "alloc work tables");
+    B.tab_host.assign(bytes, 0);
+    for (int k = 0; k < TB_KINDS; ++k)
+        if (!t[k].empty()) std::memcpy(B.tab_host.data() + off[k], t[k].data(), t[k].size() * sizeof(int4));
+    if (!items.empty()) std::memcpy(B.tab_host.data() + off[TB_KINDS], items.data(), items.size() * sizeof(int4));
+    if (!groups.empty())
+        std::memcpy(B.tab_host.data() + off[TB_KINDS + 1], groups.data(), groups.size() * sizeof(GroupDev));
+    char* base = c0->tabbuf.as<char>();
+    FA_CUDA(cudaMemcpyAsync(base, B.tab_host.data(), bytes, cudaMemcpyHostToDevice, c0->stream), "upload work tables");
+    B.tables = true;
+    for (int k = 0; k < TB_KINDS; ++k) {
+        B.tab[k] = reinterpret_cast<const int4*>(base + off[k]);
+        B.tab_n[k] = (int)t[k].size();
+    }
+    if (!items.empty()) {
+        B.items = reinterpret_cast<const int4*>(base + off[TB_KINDS]);
+        B.n_items = (int)items.size();
+        B.groups = reinterpret_cast<const GroupDev*>(base + off[TB_KINDS + 1]);
+    }
+    return FA_OK;
+}
+
+// ------------------------------------------------------------------ the solve (a batch of n systems)// ------------------------------------------------------------------ the solve (a batch of n systems)
 int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y_canon, double* const* xs_canon,
                 const fa_solver_params* p, fa_solver_stats* stats) {
     if (n < 1 || !ctxs || !b || !p) return FA_EINVAL;
@@ -724,8 +887,12 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         fa_ctx* c = ctxs[i];
         if (!c || !b[i]) return FA_EINVAL;
         if (!c->have_gauge || !c->have_params || !c->have_poles) return FA_ESTATE;
-        if (c->g.X != c0->g.X || c->g.Y != c0->g.Y || c->g.Z != c0->g.Z || c->g.T != c0->g.T) return FA_EINVAL;
         if (c->device != c0->device) return FA_EINVAL;
+    }
+    bool same_shape = true;
+    for (int i = 0; i < n; ++i) {
+        const Geom& g = ctxs[i]->g;
+        same_shape = same_shape && g.X == c0->g.X && g.Y == c0->g.Y && g.Z == c0->g.Z && g.T == c0->g.T;
     }
     const int L = p->ell;
     if (!(L == 1 || L == 2 || L == 3 || L == 4 || L == 8)) return FA_EINVAL;
@@ -738,39 +905,49 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     if (single && prec != FA_F64) return FA_EINVAL;
     const bool mixed = prec == FA_MIXED || prec == FA_MIXED_DF;
     const int head_rp = prec == FA_MIXED_DF ? RPDF : RP64;   // working precision of the head
-    if (mixed && n != 1) return FA_EINVAL;   // per-system switch points: one system at a time
     const int rel_every = p->reliable_every;
     if (rel_every < 0 || (rel_every > 0 && n != 1)) return FA_EINVAL;
-    // FA_MIXED: switch_resid <= 0 selects the default 0.04 / l^2 (the FP32
-    // error of the power-basis recurrence grows with l)
-    const double switch_resid = (p->switch_resid > 0.0) ? p->switch_resid : 0.04 / ((double)L * L);
+    // FA_MIXED: switch_resid <= 0 selects the default min(0.04 / l^2, 0.4 / l^6):
+    // the FP32 error of the power-basis recurrence grows steeply with l (FP32-only
+    // solves on 4^3 x 8: 9.1e-8 at l = 2, 1.7e-6 to 3.8e-6 at l = 4), and at l = 4
+    // a threshold of 6.25e-4 left one of nine point sources at 2.4e-8 while 1e-4
+    // kept all of them below 4.3e-10
+    const double Ld = (double)L, L2 = Ld * Ld;
+    const double switch_resid = (p->switch_resid > 0.0) ? p->switch_resid : std::min(0.04 / L2, 0.4 / (L2 * L2 * L2));
     if (mixed && !(switch_resid < 1.0)) return FA_EINVAL;
 
     Batch B;
     B.c0 = c0;
     B.n = n;
     B.sys.assign(ctxs, ctxs + n);
-    Layout& Lo = B.Lo;
-    Lo.L = L;
-    Lo.max_outer = p->max_outer;
-    Lo.V = c0->g.V;
-    Lo.single = single;
-    Lo.need64 = prec != FA_F32;
-    Lo.need32 = prec != FA_F64;
-    Lo.vs64 = (size_t)12 * Lo.V;
-    Lo.vs32 = (size_t)6 * Lo.V;
-    Lo.nblk = nblocks(Lo.V);
-    Lo.red_grid = red_grid_for(Lo.V);
-    // at most one wave of kVecBlocks blocks per SM, one site per thread where
-    // the lattice is smaller (a wave of exactly kVecBlocks per SM with fewer
-    // sites per block measured 3-5% slower on 16^3 x 32: the kernels are bound
-    // by HBM, not by the per-SM imbalance)
-    Lo.vgrid = std::min(Lo.nblk, kVecBlocks * sms());
-    Lo.part_slots = std::max(n_gram(L), 2);
-    // FP32 stretches of a one-system double-pass solve form the MR Gram matrix in
-    // the epilogue of their last sweep (flags bit 5: the Gram kernel instead)
-    Lo.gram_hop = n == 1 && !single && L <= 4 && prec != FA_F64 && (p->flags & 32) == 0;
-    for (auto* c : B.sys) FA_TRY(ensure_workspace(c, Lo));
+    // the layout of each system (its lattice size decides its grids)
+    auto layout_of = [&](const fa_ctx* c) {
+        Layout Lo{};
+        Lo.L = L;
+        Lo.max_outer = p->max_outer;
+        Lo.V = c->g.V;
+        Lo.single = single;
+        Lo.need64 = prec != FA_F32;
+        Lo.need32 = prec != FA_F64;
+        Lo.vs64 = (size_t)12 * Lo.V;
+        Lo.vs32 = (size_t)6 * Lo.V;
+        Lo.nblk = nblocks(Lo.V);
+        Lo.red_grid = red_grid_for(Lo.V);
+        // at most one wave of kVecBlocks blocks per SM, one site per thread where
+        // the lattice is smaller (a wave of exactly kVecBlocks per SM with fewer
+        // sites per block measured 3-5% slower on 16^3 x 32: the kernels are bound
+        // by HBM, not by the per-SM imbalance)
+        Lo.vgrid = std::min(Lo.nblk, kVecBlocks * sms());
+        Lo.part_slots = std::max(n_gram(L), 2);
+        // FP32 stretches of a one-system double-pass solve form the MR Gram matrix in
+        // the epilogue of their last sweep (flags bit 5: the Gram kernel instead)
+        Lo.gram_hop = n == 1 && !single && L <= 4 && prec != FA_F64 && (p->flags & 32) == 0;
+        return Lo;
+    };
+    for (auto* c : B.sys) B.lo.push_back(layout_of(c));
+    B.Lo = B.lo[0];
+    const Layout& Lo = B.Lo;
+    for (int i = 0; i < n; ++i) FA_TRY(ensure_workspace(B.sys[i], B.lo[i]));
     FA_CUDA(c0->descbuf.ensure((size_t)n * sizeof(SolverDev)), "alloc descriptors");
     FA_CUDA(c0->flagbuf.ensure((size_t)2 * n * sizeof(int)), "alloc flags");
     if (c0->pinned_bytes < 2 * n * sizeof(int) + 64) {
@@ -787,8 +964,14 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     // programmatic dependent launch for direct launches only: under CUDA-graph
     // replay it measured slower (16^3 x 32 headline: 15.00 against 14.62 ms)
     B.pdl = (p->flags & 16) == 0 && !B.use_graph;
-    for (auto* c : B.sys) B.host.push_back(make_dev(c, Lo));
+    for (int i = 0; i < n; ++i) B.host.push_back(make_dev(B.sys[i], B.lo[i]));
     for (auto& h : B.host) h.fixed_iters = (p->flags & 8) ? 1 : 0;
+    // Several systems: every launch serves all of them through work tables (any
+    // mix of lattice shapes); FP32 sweeps go by lattice groups (systems that
+    // share one gauge field and shape) so that a block's right-hand sides read
+    // its tile's links once.
+    if (n > 1) FA_TRY(build_tables(B));
+    (void)same_shape;
     cudaStream_t st = c0->stream;
     const bool timing = (p->flags & 1) != 0;
     c0->hop_timing = (p->flags & 2) != 0;
@@ -801,8 +984,14 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     // occurrences of a contiguous prefix [0, K) of outer iterations, as many as the
     // budget holds (FP64 slots while in FP64, FP32 slots after the switch)
     const int NC = nc_slots(L);
-    const size_t s64 = Lo.vs64 * sizeof(double2), s32 = Lo.vs32 * sizeof(float4);
-    const size_t per64 = (size_t)NC * s64, per32 = (size_t)NC * s32;
+    const size_t s64 = Lo.vs64 * sizeof(double2);   // system 0 (reliable updates: one system)
+    // one stored outer iteration of every system (FP64 / FP32 slots): the budget
+    // holds the same number of outer iterations for all systems of a batch
+    double per64t = 0.0, per32t = 0.0;
+    for (int i = 0; i < n; ++i) {
+        per64t += (double)NC * (double)(B.lo[i].vs64 * sizeof(double2));
+        per32t += (double)NC * (double)(B.lo[i].vs32 * sizeof(float4));
+    }
     long long cap64 = 0, cap32 = 0;
     if (pseudo) {
         size_t fb = 0, tb = 0;
@@ -810,23 +999,24 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         double held = 0.0;
         for (auto* c : B.sys) held += (double)c->store64.bytes + (double)c->store32.bytes;
         double budget = p->store_gb > 0.0 ? p->store_gb * 1e9 : std::min(0.25 * ((double)fb + held), 16e9);
-        budget = std::min(budget, 0.9 * ((double)fb + held)) / n;     // per system
+        budget = std::min(budget, 0.9 * ((double)fb + held));     // all systems together
         if (prec == FA_F64) {
-            cap64 = (long long)std::min<double>(Lo.max_outer, budget / per64);
+            cap64 = (long long)std::min<double>(Lo.max_outer, budget / per64t);
         } else if (prec == FA_F32) {
-            cap32 = (long long)std::min<double>(Lo.max_outer, budget / per32);
+            cap32 = (long long)std::min<double>(Lo.max_outer, budget / per32t);
         } else {
-            cap64 = (long long)std::min<double>(std::min(Lo.max_outer, 64), 0.4 * budget / per64);
-            cap32 = (long long)std::min<double>(Lo.max_outer, (budget - (double)cap64 * per64) / per32);
+            cap64 = (long long)std::min<double>(std::min(Lo.max_outer, 64), 0.4 * budget / per64t);
+            cap32 = (long long)std::min<double>(Lo.max_outer, (budget - (double)cap64 * per64t) / per32t);
         }
         cap64 = std::max(0LL, cap64);
         cap32 = std::max(0LL, cap32);
         for (int i = 0; i < n; ++i) {
             fa_ctx* c = B.sys[i];
-            if (cap64 > 0) FA_CUDA(c->store64.ensure((size_t)cap64 * per64), "alloc occurrence store");
-            if (cap32 > 0) FA_CUDA(c->store32.ensure((size_t)cap32 * per32), "alloc occurrence store");
-            if (Lo.need64) FA_CUDA(c->snap64.ensure(3 * s64), "alloc snapshot");
-            if (Lo.need32) FA_CUDA(c->snap32.ensure(3 * s32), "alloc snapshot");
+            const size_t s64i = B.lo[i].vs64 * sizeof(double2), s32i = B.lo[i].vs32 * sizeof(float4);
+            if (cap64 > 0) FA_CUDA(c->store64.ensure((size_t)cap64 * NC * s64i), "alloc occurrence store");
+            if (cap32 > 0) FA_CUDA(c->store32.ensure((size_t)cap32 * NC * s32i), "alloc occurrence store");
+            if (Lo.need64) FA_CUDA(c->snap64.ensure(3 * s64i), "alloc snapshot");
+            if (Lo.need32) FA_CUDA(c->snap32.ensure(3 * s32i), "alloc snapshot");
             B.host[i].store64 = c->store64.as<char>();
             B.host[i].store32 = c->store32.as<char>();
             B.host[i].cap64 = (int)cap64;
@@ -872,10 +1062,11 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         const SolverDev& d = B.host[i];
         FA_CUDA(cudaMemcpyAsync((void*)d.sigma, c->sigma, c->ns * sizeof(double), cudaMemcpyHostToDevice, st), "poles");
         FA_CUDA(cudaMemcpyAsync((void*)d.omega, c->omega, c->ns * sizeof(double), cudaMemcpyHostToDevice, st), "poles");
-        FA_CUDA(cudaMemsetAsync(d.y, 0, (size_t)12 * Lo.V * sizeof(double2), st), "zero y");
+        FA_CUDA(cudaMemsetAsync(d.y, 0, (size_t)12 * B.lo[i].V * sizeof(double2), st), "zero y");
         if (single) {
-            FA_CUDA(cudaMemsetAsync(d.xs, 0, (size_t)c->ns * 12 * Lo.V * sizeof(double2), st), "zero xs");
-            FA_CUDA(cudaMemsetAsync(d.us, 0, (size_t)c->ns * (L + 1) * 12 * Lo.V * sizeof(double2), st), "zero us");
+            const size_t vb = (size_t)12 * B.lo[i].V * sizeof(double2);
+            FA_CUDA(cudaMemsetAsync(d.xs, 0, (size_t)c->ns * vb, st), "zero xs");
+            FA_CUDA(cudaMemsetAsync(d.us, 0, (size_t)c->ns * (L + 1) * vb, st), "zero us");
         }
     }
     if (timing) cudaEventRecord(ev[0], st);
@@ -884,34 +1075,50 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     int rp = prec == FA_F32 ? RP32 : (prec == FA_F64 ? RP64 : head_rp);
     bool head = mixed;
     for (int i = 0; i < n; ++i) FA_TRY(load_source(B, i, b[i], rp));
-    const dim3 gr(Lo.vgrid, n);
+    dim3 gr(Lo.vgrid, n);
+    const int4* tr = nullptr;
+    if (B.tables) {
+        gr = dim3(B.tab_n[TB_VEC]);
+        tr = B.tab[TB_VEC];
+    }
     for (int i = 0; i < n; ++i)
         FA_CUDA(cudaMemsetAsync(B.host[i].st, 0, sizeof(DevState), st), "clear state");
     const double theta = mixed ? switch_resid : 0.0;
-    if (rp == RP64) k_dot2_sys<double><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta);
-    else if (rp == RPDF) k_dot2_sys<df><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta);
-    else k_dot2_sys<float><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta);
+    if (rp == RP64) k_dot2_sys<double><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta, tr);
+    else if (rp == RPDF) k_dot2_sys<df><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta, tr);
+    else k_dot2_sys<float><<<gr, kThreads, 0, st>>>(B.dev, p->tol, theta, tr);
     FA_LAUNCHED(c0, "k_dot2_sys");
 
     std::vector<DevState> hs(n);
     int switch_outer = -1;
     int enq = 0;
     bool all_done = false;
-    // head of FA_MIXED / FA_MIXED_DF (one system): one outer iteration at a time until the switch
+    // head of FA_MIXED / FA_MIXED_DF: one outer iteration at a time until every
+    // system (that has not finished) asks for the switch; a batch switches at one
+    // outer iteration (a system that asked earlier runs its head longer, which
+    // only makes its result more accurate)
     while (head && enq < Lo.max_outer) {
         FA_TRY(before_outer(enq, rp));
         c0->hop_outer = enq;
         FA_TRY(enqueue_outer_any(B, rp, false, single, true, reliable_at(enq)));
         ++enq;
         FA_TRY(read_states(B, hs));
-        if (hs[0].done) { all_done = true; break; }
-        if (hs[0].switch_req) {
-            FA_TRY(switch_to_f32(B, 0, rp));
-            switch_outer = hs[0].m;
+        bool every_done = true, every_switch = true;
+        for (int i = 0; i < n; ++i) {
+            every_done = every_done && hs[i].done;
+            every_switch = every_switch && (hs[i].done || hs[i].switch_req);
+        }
+        if (every_done) { all_done = true; break; }
+        if (every_switch) {
+            for (int i = 0; i < n; ++i) FA_TRY(switch_to_f32(B, i, rp));
+            switch_outer = enq;
             m0_32 = switch_outer;
             // the stored prefix must stay contiguous: no FP32 slots if the head outran its slots
-            B.host[0].m0_32 = m0_32;
-            if (K >= 0) B.host[0].cap32 = 0, cap32 = 0;
+            if (K >= 0) cap32 = 0;
+            for (int i = 0; i < n; ++i) {
+                B.host[i].m0_32 = m0_32;
+                if (K >= 0) B.host[i].cap32 = 0;
+            }
             FA_TRY(upload(B));
             head = false;
             rp = RP32;
@@ -972,16 +1179,23 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         k_coef_reduce<<<dim3((M * NC + 255) / 256, n), 256, 0, st>>>(B.dev);
         FA_LAUNCHED(c0, "k_coef_reduce");
         if (timing) cudaEventRecord(ev[2], st);
+        // the largest lattice of the batch sets the grids (blocks beyond a smaller
+        // system's sites return at once)
+        int max_nblk = 0, max_V = 0;
+        for (int i = 0; i < n; ++i) {
+            max_nblk = std::max(max_nblk, B.lo[i].nblk);
+            max_V = std::max(max_V, B.lo[i].V);
+        }
         if (pseudo && Kst > 0) {
             // one thread per site and chunk: 12 chunks per site (FP64, double-float), 6 (FP32)
             if (cap64 > 0) {
-                const dim3 gw(Lo.nblk * 12, n);
+                const dim3 gw(max_nblk * 12, n);
                 if (prec == FA_MIXED_DF) k_gather<df><<<gw, kThreads, 0, st>>>(B.dev);
                 else k_gather<double><<<gw, kThreads, 0, st>>>(B.dev);
                 FA_LAUNCHED(c0, "k_gather (head store)");
             }
             if (cap32 > 0 && m0_32 >= 0) {
-                k_gather<float><<<dim3(Lo.nblk * 6, n), kThreads, 0, st>>>(B.dev);
+                k_gather<float><<<dim3(max_nblk * 6, n), kThreads, 0, st>>>(B.dev);
                 FA_LAUNCHED(c0, "k_gather<float>");
             }
         }
@@ -1003,7 +1217,7 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
             FA_LAUNCHED(c0, "k_set_m");
             for (int m = mstart; m < M; ++m) {
                 if (p2 != RP32 && mixed && m == switch_outer) {
-                    FA_TRY(switch_to_f32(B, 0, p2));
+                    for (int i = 0; i < n; ++i) FA_TRY(switch_to_f32(B, i, p2));
                     p2 = RP32;
                 }
                 FA_TRY(enqueue_outer_any(B, p2, true, false, false, reliable_at(m)));
@@ -1018,7 +1232,9 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     } else if (rc_all == FA_OK && single) {
         if (timing) { cudaEventRecord(ev[2], st); cudaEventRecord(ev[3], st); }
         if (y_canon) {
-            k_combine_sys<<<dim3((12 * Lo.V + kThreads - 1) / kThreads, n), kThreads, 0, st>>>(B.dev);
+            int max_V = 0;
+            for (int i = 0; i < n; ++i) max_V = std::max(max_V, B.lo[i].V);
+            k_combine_sys<<<dim3((12 * max_V + kThreads - 1) / kThreads, n), kThreads, 0, st>>>(B.dev);
             FA_LAUNCHED(c0, "k_combine_sys");
             for (int i = 0; i < n; ++i) {
                 FA_TRY(launch_unpack_spinor_f64(B.sys[i]->g, B.host[i].y, y_canon[i], st));
@@ -1074,6 +1290,109 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
 int solve(fa_ctx* c, const double* b, double* y_canon, double* const* xs_canon, const fa_solver_params* p,
           fa_solver_stats* stats) {
     return solve_batch(&c, 1, &b, y_canon ? &y_canon : nullptr, xs_canon, p, stats);
+}
+
+// ------------------------------------------------------------------ batched sweep autotuner
+// Times the multi-RHS FP32 sweep of a batch (r_0 -> tmp, the first hop of A)
+// for each right-hand-side count per block and residency; keeps the fastest in
+// ctxs[0].  The sweep's results do not depend on the choice.
+int autotune_batch(fa_ctx* const* ctxs, int n, int reps, int* rpb_out, int* mb_out, double* times, int ntimes) {
+    fa_ctx* c0 = ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]->have_gauge || !ctxs[i]->have_params || !ctxs[i]->have_poles) return FA_ESTATE;
+        if (ctxs[i]->device != c0->device) return FA_EINVAL;
+    }
+    Batch B;
+    B.c0 = c0;
+    B.n = n;
+    B.sys.assign(ctxs, ctxs + n);
+    for (int i = 0; i < n; ++i) {
+        Layout lo{};
+        lo.L = 1;
+        lo.max_outer = 1;
+        lo.V = ctxs[i]->g.V;
+        lo.need32 = true;
+        lo.vs64 = (size_t)12 * lo.V;
+        lo.vs32 = (size_t)6 * lo.V;
+        lo.nblk = nblocks(lo.V);
+        lo.red_grid = red_grid_for(lo.V);
+        lo.vgrid = std::min(lo.nblk, kVecBlocks * sms());
+        lo.part_slots = 2;
+        B.lo.push_back(lo);
+        FA_TRY(ensure_workspace(ctxs[i], lo));
+    }
+    B.Lo = B.lo[0];
+    cudaStream_t st = c0->stream;
+    FA_CUDA(c0->descbuf.ensure((size_t)n * sizeof(SolverDev)), "alloc descriptors");
+    B.dev = c0->descbuf.as<SolverDev>();
+    for (int i = 0; i < n; ++i) {
+        B.host.push_back(make_dev(ctxs[i], B.lo[i]));
+        FA_CUDA(cudaMemsetAsync(B.host[i].st, 0, sizeof(DevState), st), "clear state");
+        FA_CUDA(cudaMemsetAsync(ctxs[i]->r32.p, 0, B.lo[i].vs32 * sizeof(float4), st), "clear r");
+    }
+    FA_TRY(upload(B));
+    const int rpbs[] = {1, 2, 3, 4, 6, 12, kMaxRhs};
+    const int mbs[] = {kHopNarrowBlocks, 4};
+    constexpr int NR = sizeof(rpbs) / sizeof(rpbs[0]), NM = sizeof(mbs) / sizeof(mbs[0]);
+    double best[NR][NM];
+    for (auto& row : best)
+        for (auto& v : row) v = 1e30;
+    const int saved_rpb = c0->mrhs_rpb, saved_mb = c0->mrhs_mb;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FA_CUDA(cudaEventCreate(&e0), "event");
+    FA_CUDA(cudaEventCreate(&e1), "event");
+    int rc = FA_OK;
+    const ScalarStep none{STEP_NONE, 0};
+    for (int round = 0; round < 3 && rc == FA_OK; ++round)
+        for (int a = 0; a < NR && rc == FA_OK; ++a)
+            for (int m = 0; m < NM && rc == FA_OK; ++m) {
+                c0->mrhs_rpb = rpbs[a];
+                c0->mrhs_mb = mbs[m];
+                B.items = nullptr;
+                rc = build_tables(B);
+                if (rc != FA_OK) break;
+                auto go = [&](int k) {
+                    for (int i = 0; i < k; ++i) {
+                        if (B.mrhs_min_blocks == 4)
+                            k_hop_mrhs<false, 4><<<B.n_items, kHopNarrowThreads, 0, st>>>(B.dev, B.groups, B.items, 1,
+                                                                                          0, 2, 0, 0, 0, none);
+                        else
+                            k_hop_mrhs<false, kHopNarrowBlocks><<<B.n_items, kHopNarrowThreads, 0, st>>>(
+                                B.dev, B.groups, B.items, 1, 0, 2, 0, 0, 0, none);
+                    }
+                };
+                go(3);
+                cudaEventRecord(e0, st);
+                go(reps);
+                cudaEventRecord(e1, st);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                if (e != cudaSuccess) { rc = cuda_fail(e, "fa_autotune_batched"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best[a][m] = std::min(best[a][m], (double)ms / reps);
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FA_OK) {
+        c0->mrhs_rpb = saved_rpb;
+        c0->mrhs_mb = saved_mb;
+        return rc;
+    }
+    int ba = NR - 1, bm = 0;
+    for (int a = 0; a < NR; ++a)
+        for (int m = 0; m < NM; ++m)
+            if (best[a][m] < best[ba][bm]) ba = a, bm = m;
+    c0->mrhs_rpb = rpbs[ba];
+    c0->mrhs_mb = mbs[bm];
+    *rpb_out = rpbs[ba];
+    *mb_out = mbs[bm];
+    if (times)
+        for (int a = 0, k = 0; a < NR; ++a)
+            for (int m = 0; m < NM; ++m, ++k)
+                if (k < ntimes) times[k] = best[a][m];
+    FA_CUDA(cudaStreamSynchronize(st), "sync");
+    return FA_OK;
 }
 
 // ------------------------------------------------------------------ sign function, overlap operator

@@ -64,6 +64,9 @@ struct SolverDev {
     const float4* links32;
     const float4* linksdf;            // double-float links [4][9][V]
     double diag, ef, eb, bc, scale;   // 4+m, e^{+mu}, e^{-mu}, time-boundary sign, c
+    // the same operator scalars rounded to FP32 (multi-RHS sweep): 4+m and -1/2 for the
+    // first hop of A, c (4+m) and -c/2 for the second, e^{+-mu}, the boundary sign
+    float fdiag1, fhop1, fdiag2, fhop2, fef, feb, fbc;
     const double* sigma;   // [ns]
     const double* omega;   // [ns]
     double2* zeta;         // [ns]
@@ -125,6 +128,25 @@ template <> struct Vec<float> {
     __device__ static T* tmp(const SolverDev& d) { return d.tmp32; }
     __device__ static LinkView<float> links(const SolverDev& d) { return {d.links32, d.V}; }
 };
+
+// Position of a block in a launch that serves one or several systems.  Without
+// a work table: system blockIdx.y, block blockIdx.x of gridDim.x (every system of
+// the launch has the same lattice shape).  With a table (systems of different
+// lattice shapes in one launch): tab[blockIdx.x] = (system, block within the
+// system, vector blocks of the system, blocks of the system in this launch =
+// the tickets of its reductions).  XS kernels: block -1 is the system's shift
+// block (block 0 of the launch without a table).
+struct Where {
+    int sys, bx, nbx, ntk;
+};
+template <bool XS>
+__device__ __forceinline__ Where where(const int4* tab) {
+    if (tab != nullptr) {
+        const int4 t = tab[blockIdx.x];
+        return {t.x, t.y, t.z, t.w};
+    }
+    return {(int)blockIdx.y, (int)blockIdx.x - (XS ? 1 : 0), (int)gridDim.x - (XS ? 1 : 0), (int)gridDim.x};
+}
 
 // pass 1: the system has finished (converged, failed or max_outer);
 // pass 2: the system has replayed all its outer iterations.
@@ -252,7 +274,7 @@ __device__ __forceinline__ void acc_x(double2* x, int q, int V, int s, double2 a
 // sub-partition's FP64 pipe for tens of cycles, a division for hundreds), so
 // the steps use fused multiply-adds, one real division per complex inverse,
 // and reuse inverses between the per-shift scalars.
-__device__ __forceinline__ bool last_block(DevState* S) {
+__device__ __forceinline__ bool last_block(DevState* S, int ntickets) {
     __shared__ int is_last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -262,7 +284,7 @@ __device__ __forceinline__ bool last_block(DevState* S) {
         // read the partials after the barrier, from L2)
         __threadfence();
         const unsigned t = atomicAdd(&S->ticket, 1u);
-        is_last = t == gridDim.x - 1u;
+        is_last = t == (unsigned)ntickets - 1u;
         if (is_last) {
             S->ticket = 0u;   // every block of this launch has taken its ticket
             __threadfence();
@@ -719,9 +741,10 @@ struct ScalarStep {
     int arg;
 };
 
+// nblk: partials of the reduction; ntickets: blocks of the system in this launch
 template <bool DFP>
-__device__ __forceinline__ void run_step(const SolverDev& d, ScalarStep e, int nblk) {
-    if (e.kind == STEP_NONE || !last_block(d.st)) return;
+__device__ __forceinline__ void run_step(const SolverDev& d, ScalarStep e, int nblk, int ntickets) {
+    if (e.kind == STEP_NONE || !last_block(d.st, ntickets)) return;
     if (e.kind == STEP_BETA) {
         sc_beta<DFP>(d, e.arg, nblk);
     } else if (e.kind == STEP_ALPHA || e.kind == STEP_ALPHA_ALL) {
@@ -750,12 +773,13 @@ __device__ __forceinline__ void site_range(int V, unsigned bx, unsigned nbx, int
 // u_i <- r_i - beta u_i, i = 0..j (r, u: l+1 spinors each, contiguous, stride vs)
 template <typename R>
 __global__ void __launch_bounds__(kThreads, kVecBlocks)
-k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
+k_update_u(const SolverDev* __restrict__ ds, int j, int pass2, const int4* tab) {
     dep_sync();
-    const SolverDev& d = ds[blockIdx.y];
+    const Where w = where<false>(tab);
+    const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
     int s0, s1;
-    site_range(d.V, blockIdx.x, gridDim.x, s0, s1);
+    site_range(d.V, w.bx, w.nbx, s0, s1);
     const typename Ch<R>::T* r = Vec<R>::r(d);
     typename Ch<R>::T* u = Vec<R>::u(d);
     const size_t vs = vstride<R>(d);
@@ -784,16 +808,17 @@ k_update_u(const SolverDev* __restrict__ ds, int j, int pass2) {
 // j (sc_alpha_shifts) beside the vector blocks 1..nblk.
 template <typename R, bool ACC, bool SHIFTS, bool XS = false>
 __global__ void __launch_bounds__(kThreads, kVecBlocks)
-k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
+k_update_r(const SolverDev* __restrict__ ds, int j, int pass2, const int4* tab) {
     dep_sync();
-    const SolverDev& d = ds[blockIdx.y];
+    const Where w = where<XS>(tab);
+    const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
-    if (XS && blockIdx.x == 0) {
+    if (XS && w.bx < 0) {
         sc_alpha_shifts(d, j);
         return;
     }
     int s0, s1;
-    site_range(d.V, blockIdx.x - (XS ? 1u : 0u), gridDim.x - (XS ? 1u : 0u), s0, s1);
+    site_range(d.V, w.bx, w.nbx, s0, s1);
     const int m = d.st->m;
     typename Ch<R>::T* r = Vec<R>::r(d);
     const typename Ch<R>::T* u = Vec<R>::u(d);
@@ -880,9 +905,10 @@ k_update_r(const SolverDev* __restrict__ ds, int j, int pass2) {
 template <typename R, int L> constexpr int gram_min_blocks() { return L <= 2 ? 4 : 1; }
 template <typename R, int L>
 __global__ void __launch_bounds__(kThreads, gram_min_blocks<R, L>())
-k_gram(const SolverDev* __restrict__ ds, int shifts) {
+k_gram(const SolverDev* __restrict__ ds, int shifts, const int4* tab) {
     dep_sync();
-    const SolverDev& d = ds[blockIdx.y];
+    const Where w = where<false>(tab);
+    const SolverDev& d = ds[w.sys];
     if (sys_idle(d, 0)) return;
     const typename Ch<R>::T* r = Vec<R>::r(d);
     const size_t vs = vstride<R>(d);
@@ -892,7 +918,7 @@ k_gram(const SolverDev* __restrict__ ds, int shifts) {
 #pragma unroll
     for (int k = 0; k < NG; ++k) acc[k] = czero<R>();
     int s0, s1;
-    site_range(d.V, blockIdx.x, gridDim.x, s0, s1);
+    site_range(d.V, w.bx, w.nbx, s0, s1);
     for (int s = s0 + threadIdx.x; s < s1; s += kThreads) {
 #pragma unroll
         for (int q = 0; q < Ch<R>::N; ++q) {
@@ -910,9 +936,9 @@ k_gram(const SolverDev* __restrict__ ds, int shifts) {
                 }
         }
     }
-    block_reduce_store<NG, R>(acc, partials, gridDim.x);
-    if (last_block(d.st)) {
-        sc_mr_seed<L, dfp_of<R>()>(d, gridDim.x);
+    block_reduce_store<NG, R>(acc, partials, w.nbx, w.bx);
+    if (last_block(d.st, w.ntk)) {
+        sc_mr_seed<L, dfp_of<R>()>(d, w.nbx);
         if (shifts) {
             __syncthreads();
             sc_mr_shifts<L>(d);
@@ -936,15 +962,16 @@ template <typename R, int L> constexpr int mr_min_blocks() {
 }
 template <typename R, int L, bool ACC, bool SHIFTS, bool DOT, bool XS = false>
 __global__ void __launch_bounds__(kThreads, mr_min_blocks<R, L>())
-k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
+k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step, const int4* tab) {
     dep_sync();
-    const SolverDev& d = ds[blockIdx.y];
+    const Where w = where<XS>(tab);
+    const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
-    const unsigned bx = blockIdx.x - (XS ? 1u : 0u), nbx = gridDim.x - (XS ? 1u : 0u);
-    if (XS && blockIdx.x == 0) {
+    const int bx = w.bx, nbx = w.nbx;
+    if (XS && bx < 0) {
         sc_mr_shifts<L>(d);
         __threadfence();   // the new zeta of every thread before the ticket
-        run_step<dfp_of<R>()>(d, step, nbx);
+        run_step<dfp_of<R>()>(d, step, nbx, w.ntk);
         return;
     }
     const int m = d.st->m;
@@ -1045,17 +1072,17 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step) {
     }
     if (DOT) {
         block_reduce_store<2, R>(dots, partials, nbx, bx);
-        run_step<dfp_of<R>()>(d, step, nbx);
+        run_step<dfp_of<R>()>(d, step, nbx, w.ntk);
     }
 }
 
 // <rt, r0> (slot 0) and |r0|^2 (slot 1), grid-stride (start of a solve)
 template <typename R>
 __device__ __forceinline__ void k_dot2_body(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0,
-                                            double2* partials) {
+                                            double2* partials, int bx, int nbx) {
     cx<R> dots[2] = {czero<R>(), czero<R>()};
     int s0, s1;
-    site_range(V, blockIdx.x, gridDim.x, s0, s1);
+    site_range(V, bx, nbx, s0, s1);
     for (int s = s0 + threadIdx.x; s < s1; s += kThreads) {
 #pragma unroll
         for (int q = 0; q < Ch<R>::N; ++q) {
@@ -1068,21 +1095,23 @@ __device__ __forceinline__ void k_dot2_body(int V, const typename Ch<R>::T* rt, 
             }
         }
     }
-    block_reduce_store<2, R>(dots, partials, gridDim.x);
+    block_reduce_store<2, R>(dots, partials, nbx, bx);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_dot2(int V, const typename Ch<R>::T* rt, const typename Ch<R>::T* r0, double2* partials) {
-    k_dot2_body<R>(V, rt, r0, partials);
+    k_dot2_body<R>(V, rt, r0, partials, blockIdx.x, gridDim.x);
 }
 
 // start of pass 1: <rt, r0>, |r0|^2 and, in the last block, the initial state
 template <typename R>
-__global__ void __launch_bounds__(kThreads, kVecBlocks) k_dot2_sys(const SolverDev* __restrict__ ds, double tol, double theta) {
-    const SolverDev& d = ds[blockIdx.y];
-    k_dot2_body<R>(d.V, Vec<R>::rt(d), Vec<R>::r(d), d.part);
-    if (last_block(d.st)) sc_init<dfp_of<R>()>(d, gridDim.x, tol, theta);
+__global__ void __launch_bounds__(kThreads, kVecBlocks)
+k_dot2_sys(const SolverDev* __restrict__ ds, double tol, double theta, const int4* tab) {
+    const Where w = where<false>(tab);
+    const SolverDev& d = ds[w.sys];
+    k_dot2_body<R>(d.V, Vec<R>::rt(d), Vec<R>::r(d), d.part, w.bx, w.nbx);
+    if (last_block(d.st, w.ntk)) sc_init<dfp_of<R>()>(d, w.nbx, tol, theta);
 }
 
 // A application inside the solver: out = scale * g5 D in on the system's own
@@ -1098,11 +1127,12 @@ __device__ __forceinline__ typename Ch<R>::T* select_vec(const SolverDev& d, int
 template <typename R, bool DOT>
 __global__ void __launch_bounds__(kThreads, hop_min_blocks<R>())
 k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
-          ScalarStep step) {
+          ScalarStep step, const int4* tab) {
     dep_sync();
-    const SolverDev& d = ds[blockIdx.y];
+    const Where w = where<false>(tab);
+    const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
-    const int s = blockIdx.x * kThreads + threadIdx.x;
+    const int s = w.bx * kThreads + threadIdx.x;
     cx<R> dres[1] = {czero<R>()};
     if (s < d.V) {
         const double sc = second ? d.scale : 1.0;
@@ -1123,8 +1153,63 @@ k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, i
         }
     }
     if (DOT) {
-        block_reduce_store<1, R>(dres, d.part, 0);
-        run_step<dfp_of<R>()>(d, step, gridDim.x);
+        block_reduce_store<1, R>(dres, d.part, 0, w.bx);
+        run_step<dfp_of<R>()>(d, step, w.nbx, w.ntk);
+    }
+}
+
+// Systems that share one gauge field and lattice (the sources of one lattice in
+// a batch): the multi-RHS sweep applies D_w to all of them tile by tile.
+constexpr int kMaxRhs = 16;
+struct GroupDev {
+    int nsys;
+    int ntile;             // tiles of kHopNarrowThreads sites
+    int sys[kMaxRhs];      // descriptor index of each system
+};
+
+// FP32 sweep of a batch, several right-hand sides per block.  items[blockIdx.x]
+// = (group, tile, first, end): the block applies the sweep to the systems
+// first..end-1 of the group on the tile's sites, one after the other, so the
+// tile's links (and the neighbours' backward links) come from HBM once and
+// from L1 for the other right-hand sides.  Each system's arithmetic, its
+// per-tile partials of <rt, out> and its scalar step are those of the
+// one-system sweep of the same launch shape (128-thread blocks), so a batched
+// solve equals the one-at-a-time solve bit for bit.
+template <bool DOT, int MB>
+__global__ void __launch_bounds__(kHopNarrowThreads, MB)
+k_hop_mrhs(const SolverDev* __restrict__ ds, const GroupDev* __restrict__ groups, const int4* __restrict__ items,
+           int in_sel, int in_j, int out_sel, int out_j, int second, int pass2, ScalarStep step) {
+    constexpr int NT = kHopNarrowThreads;
+    dep_sync();
+    const int4 it = items[blockIdx.x];
+    const GroupDev& G = groups[it.x];
+    const int tile = it.y;
+    for (int r = it.z; r < it.w; ++r) {
+        const SolverDev& d = ds[G.sys[r]];
+        if (sys_idle(d, pass2)) continue;   // the same for every thread of the block
+        const int s = tile * NT + (int)threadIdx.x;
+        cx<float> dres[1] = {czero<float>()};
+        if (s < d.V) {
+            const SpinorView<float> in{select_vec<float>(d, in_sel, in_j), d.V};
+            const SpinorView<float> out{select_vec<float>(d, out_sel, out_j), d.V};
+            cx<float> p[12];
+            hop_site<float, false, true>(d.g, LinkView<float>{d.links32, d.V}, in, s, second ? d.fdiag2 : d.fdiag1,
+                                         second ? d.fhop2 : d.fhop1, d.fef, d.feb, d.fbc, p);
+            out.store(s, p);
+            if (DOT) {
+                const SpinorView<float> rt{d.rt32, d.V};
+                cx<float> q[12];
+                rt.load(s, q);
+                cx<float> a = czero<float>();
+#pragma unroll
+                for (int k = 0; k < 12; ++k) a = cjfma(q[k], p[k], a);
+                dres[0] = a;
+            }
+        }
+        if (DOT) {
+            block_reduce_store<1, float, NT>(dres, d.part, 0, tile);
+            run_step<true>(d, step, G.ntile, G.ntile);
+        }
     }
 }
 
@@ -1132,9 +1217,10 @@ k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, i
 template <typename R, bool DOT>
 __global__ void __launch_bounds__(kRowThreads, rows_sys_min_blocks<DOT>())
 k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
-               ScalarStep step) {
+               ScalarStep step, const int4* tab) {
     dep_sync();
-    const SolverDev& d = ds[blockIdx.y];
+    const Where w = where<false>(tab);
+    const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
     const double sc = second ? d.scale : 1.0;
     const Geom g = d.g;
@@ -1142,10 +1228,11 @@ k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_s
     const SpinorView<R> rt{Vec<R>::rt(d), d.V};
     cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, Vec<R>::links(d), in, out,
                                                         fromdbl<R>(sc * d.diag), fromdbl<R>(-0.5 * sc),
-                                                        fromdbl<R>(d.ef), fromdbl<R>(d.eb), fromdbl<R>(d.bc), rt)};
+                                                        fromdbl<R>(d.ef), fromdbl<R>(d.eb), fromdbl<R>(d.bc), rt,
+                                                        w.bx)};
     if (DOT) {
-        block_reduce_store<1, R, kRowThreads>(dres, d.part, 0, blockIdx.x);
-        run_step<dfp_of<R>()>(d, step, gridDim.x);
+        block_reduce_store<1, R, kRowThreads>(dres, d.part, 0, w.bx);
+        run_step<dfp_of<R>()>(d, step, w.nbx, w.ntk);
     }
 }
 
@@ -1160,10 +1247,10 @@ k_hop1_rows(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag,
             ScalarStep step) {
     dep_sync();
     if (done != nullptr && *done) return;
-    cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv)};
+    cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv, blockIdx.x)};
     if (DOT) {
         block_reduce_store<1, R, kRowThreads>(dres, partials, 0, blockIdx.x);
-        run_step<dfp_of<R>()>(ds[0], step, gridDim.x);
+        run_step<dfp_of<R>()>(ds[0], step, gridDim.x, gridDim.x);
     }
 }
 
@@ -1190,7 +1277,7 @@ k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R ch
     }
     if (DOT) {
         block_reduce_store<1, R, NT>(dres, partials, 0, blockIdx.x);
-        run_step<dfp_of<R>()>(ds[0], step, gridDim.x);
+        run_step<dfp_of<R>()>(ds[0], step, gridDim.x, gridDim.x);
     }
 }
 
@@ -1201,7 +1288,7 @@ k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R ch
 template <typename R>
 __global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_reliable(const SolverDev* __restrict__ ds, const double2* ax, int pass2, ScalarStep step) {
-    const SolverDev& d = ds[blockIdx.y];
+    const SolverDev& d = ds[blockIdx.y];   // one system (reliable updates are not batched)
     if (sys_idle(d, pass2)) return;
     typename Ch<R>::T* r0 = Vec<R>::r(d);
     const typename Ch<R>::T* rt = Vec<R>::rt(d);
@@ -1229,7 +1316,7 @@ k_reliable(const SolverDev* __restrict__ ds, const double2* ax, int pass2, Scala
         }
     }
     block_reduce_store<2, R>(dots, d.part, gridDim.x);
-    run_step<dfp_of<R>()>(d, step, gridDim.x);
+    run_step<dfp_of<R>()>(d, step, gridDim.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------ pseudo-double-pass gather

@@ -33,6 +33,16 @@ def lattice_systems(dims, gauge_seed, mu, sources, stream=None, poles=10):
     return ctxs, [to_dev(s) for s in sources], (U, c, om, sg)
 
 
+def _batch_systems():
+    d1, d2 = (4, 4, 4, 8), (3, 3, 3, 6)
+    return [(301, d1, 0.05, inputs.point_source(d1, 0, 0)), (302, d2, 0.12, inputs.gaussian_spinor(d2, 11)),
+            (301, d1, 0.05, inputs.point_source(d1, 2, 1)), (303, d1, 0.18, inputs.gaussian_spinor(d1, 12)),
+            (302, d2, 0.12, inputs.point_source(d2, 3, 2)), (301, d1, 0.05, inputs.gaussian_spinor(d1, 9))]
+
+
+SYSTEMS = _batch_systems()   # (gauge seed, dims, mu, source) of build_batch's systems, in its order
+
+
 def build_batch(stream=None):
     d1, d2 = (4, 4, 4, 8), (3, 3, 3, 6)
     srcs1 = [inputs.point_source(d1, 0, 0), inputs.point_source(d1, 2, 1), inputs.gaussian_spinor(d1, 9)]
@@ -50,11 +60,18 @@ def build_batch(stream=None):
 @pytest.mark.parametrize("mode,precision", [("double", "f64"), ("pseudo", "f64"), ("single", "f64"),
                                             ("double", "f32"), ("pseudo", "f32")])
 def test_batched_equals_one_at_a_time(mode, precision):
+    """Systems of two lattice shapes in one batched solve (one launch per kernel
+    for all of them; the FP32 sweep over lattice groups, several right-hand
+    sides per block) against each system solved alone with the same sweep shape
+    (128-thread FP32 sweeps, the Gram matrix in a kernel of its own): equal bit
+    for bit."""
     ctxs, srcs, _ = build_batch()
     kw = dict(ell=2, tol=1e-10, mode=mode, precision=precision)
     ys, stats = fa.apply_f_batched(ctxs, srcs, **kw)
     for i, (ctx, b) in enumerate(zip(ctxs, srcs)):
-        r = ctx.apply_f(b, **kw)
+        ctx.set_hop_shape("narrow")
+        r = ctx.apply_f(b, gram_epilogue=False, **kw)
+        ctx.set_hop_shape("auto")
         assert np.array_equal(to_host(ys[i]), to_host(r.y)), i
         assert stats[i]["outer_iters"] == r.stats["outer_iters"]
         assert stats[i]["iters_per_shift"] == r.stats["iters_per_shift"]
@@ -114,11 +131,20 @@ def test_batched_graph_mode():
         assert np.array_equal(to_host(a), to_host(b))
 
 
-def test_batch_rejects_mixed_precision_for_several_systems():
-    ctxs, srcs, _ = build_batch()
-    with pytest.raises(fa.FAError) as e:
-        fa.apply_f_batched(ctxs[:3], srcs[:3], ell=2, precision="mixed")
-    assert e.value.status == fa.FA_EINVAL
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
+def test_batched_precise_head_against_oracle(precision):
+    """FA_MIXED / FA_MIXED_DF for a batch: the head runs until every system asks
+    for the switch; every system then meets the 1e-8 bound against the oracle."""
+    from oracle import msbicgstab as ms
+    ctxs, srcs, (a, bgrp, cgrp) = build_batch()
+    ys, st = fa.apply_f_batched(ctxs, srcs, ell=2, tol=1e-10, mode="pseudo", precision=precision)
+    assert len({x["switch_outer"] for x in st}) == 1 and st[0]["switch_outer"] > 0
+    for i, (gauge_seed, dims, mu, src) in enumerate(SYSTEMS):
+        U = inputs.su3_exp_gauge(dims, 0.5, gauge_seed)
+        c = scale.power_scale(dirac.Operator(U, -1.8, mu).A, inputs.gaussian_spinor(dims, gauge_seed + 3), 100)
+        om, sg = fa.neuberger_poles(10)
+        y_o = ms.multishift_double(dirac.Operator(U, -1.8, mu, c).A, src, sg, om, 2, 1e-12)
+        assert rel(to_host(ys[i]), y_o) < 1e-8, i
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32", "mixed_df"])
@@ -167,3 +193,52 @@ def test_graph_cache_follows_context_changes(precision):
     ctx.set_gauge(to_dev(w["U"]))
     ctx.set_params(w["mass"], w["mu"], w["t_bc"], w["c"])
     assert np.array_equal(same(), y0)
+
+
+def test_point_source_batch_every_system_against_oracle():
+    """The batched configuration's structure on stand-in lattices: 12 spin-colour
+    point sources on each of three lattices of different shapes (mu drawn per
+    lattice), 36 systems in one batched FP32 solve (l 2) and one with a
+    double-float head (l 4); every system against the oracle at the bounds of
+    the one-system solves (FP32 bulk 1e-6, precise head 1e-8)."""
+    from oracle import msbicgstab as ms
+    import torch
+    rng = np.random.default_rng(404)
+    shapes = [(4, 4, 4, 4), (3, 3, 3, 6), (4, 4, 4, 8)]
+    stream = torch.cuda.Stream()
+    ctxs, srcs, want = [], [], {2: [], 4: []}
+    om, sg = fa.neuberger_poles(12)
+    with torch.cuda.stream(stream):
+        for k, dims in enumerate(shapes):
+            mu = float(rng.uniform(0.0, 0.2))
+            sources = [inputs.point_source(dims, sp, co) for sp in range(4) for co in range(3)]
+            group, bs, (U, c, _, _) = lattice_systems(dims, 500 + k, mu, sources, stream, poles=12)
+            ctxs += group
+            srcs += bs
+            op = dirac.Operator(U, -1.8, mu, c)
+            for src in sources:
+                for ell in (2, 4):
+                    want[ell].append(ms.multishift_double(op.A, src, sg, om, ell, 1e-12))
+    stream.synchronize()
+    assert len(ctxs) == 36
+    for ell, precision, bound in ((2, "f32", 1e-6), (4, "mixed_df", 1e-8)):
+        ys, st = fa.apply_f_batched(ctxs, srcs, ell=ell, tol=1e-10, mode="pseudo", precision=precision, graph=True)
+        stream.synchronize()
+        assert all(x["status"] == 0 for x in st)
+        worst = max(rel(to_host(y), w) for y, w in zip(ys, want[ell]))
+        assert worst < bound, (ell, precision, worst)
+
+
+def test_batched_autotuner_keeps_results():
+    """fa_autotune_batched times the multi-RHS sweep's shapes and keeps the
+    fastest; the batched solve with the chosen shape equals the default's bit
+    for bit (the shape decides only which block runs which right-hand side)."""
+    ctxs, srcs, _ = build_batch()
+    kw = dict(ell=2, tol=1e-10, mode="pseudo", precision="f32")
+    y0, _ = fa.apply_f_batched(ctxs, srcs, **kw)
+    tune = fa.autotune_batched(ctxs, reps=5)
+    assert tune["rhs_per_block"] in (1, 2, 3, 4, 6, 12, 16) and tune["min_blocks"] in (4, 7)
+    assert all(t > 0 for t in tune["times_ms"].values())
+    y1, _ = fa.apply_f_batched(ctxs, srcs, **kw)
+    for a, b in zip(y0, y1):
+        assert np.array_equal(to_host(a), to_host(b))
