@@ -36,6 +36,7 @@ EXPORTS = (
     "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune", "fa_autotune_batched",
+    "fa_eigs_smallest",
 )
 
 # FP32 sweep launch shapes (fa_hop_shape)
@@ -125,6 +126,8 @@ def load_library(path=LIB_PATH):
         "fa_get_hop_shape": (I, [P]),
         "fa_autotune": (I, [P, I, ctypes.POINTER(D)]),
         "fa_autotune_batched": (I, [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), I]),
+        "fa_eigs_smallest": (I, [P, I, I, D, I, ctypes.POINTER(SolverParams), ctypes.c_ulonglong, P, P, P,
+                                 ctypes.POINTER(I), ctypes.POINTER(I)]),
         "fa_status_string": (ctypes.c_char_p, [I]),
         "fa_last_error": (ctypes.c_char_p, []),
         "fa_version": (ctypes.c_char_p, []),
@@ -402,6 +405,28 @@ class Context:
                                 ctypes.byref(L), gb.data_ptr() if want_db else None, ctypes.byref(p),
                                 ctypes.byref(st)), "fa_grad")
         return L.value, gU, dmu.value, gb, st.as_dict()
+
+    def eigs_smallest(self, k, m=None, tol=1e-10, max_restarts=50, seed=1, solve_tol=1e-12, check=True, **kw):
+        """The k eigenpairs of H = g5 D_w(mu) smallest in magnitude (fa_eigs_smallest):
+        (lambda (k complex), R, Lv (complex128 CUDA tensors (k,) + spinor shape,
+        Lv_i^H R_j = delta_ij), info dict).  tol: Ritz-pair convergence; solve_tol
+        and kw: the inner solves' settings (apply_f's)."""
+        torch = _torch()
+        m = 2 * k + 8 if m is None else m
+        shape = (k,) + tuple(self.spinor_shape)
+        R = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        Lv = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        lam = np.empty(2 * k, dtype=np.float64)
+        nconv, nsolve = ctypes.c_int(), ctypes.c_int()
+        kw["tol"] = solve_tol
+        kw.setdefault("mode", "double")
+        p = self.params(**kw)
+        rc = self.lib.fa_eigs_smallest(self.h, int(k), int(m), float(tol), int(max_restarts), ctypes.byref(p),
+                                       int(seed), lam.ctypes.data, R.data_ptr(), Lv.data_ptr(), ctypes.byref(nconv),
+                                       ctypes.byref(nsolve))
+        if check:
+            _check(rc, "fa_eigs_smallest")
+        return lam[0::2] + 1j * lam[1::2], R, Lv, {"status": rc, "converged": nconv.value, "solves": nsolve.value}
 
     def sync(self):
         _check(self.lib.fa_sync(self.h), "fa_sync")

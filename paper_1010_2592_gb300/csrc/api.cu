@@ -413,6 +413,13 @@ int fa_apply_sign_deflated(fa_ctx* c, const double* b, double* out, int k, const
     return apply_sign_deflated(c, b, out, k, lambda, R, Lv, overlap != 0, p, stats);
 }
 
+int fa_eigs_smallest(fa_ctx* c, int k, int m, double tol, int max_restarts, const fa_solver_params* p,
+                     unsigned long long seed, double* lambda, double* R, double* Lv, int* n_converged,
+                     int* n_solves) {
+    if (!c || !p || !lambda || !R || !Lv || !n_converged || !n_solves || R == Lv) return FA_EINVAL;
+    return eigs_smallest(c, k, m, tol, max_restarts, p, seed, lambda, R, Lv, n_converged, n_solves);
+}
+
 int fa_apply_f_batched(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y,
                        const fa_solver_params* p, fa_solver_stats* stats) {
     if (!ctxs || !b || !y || !p || n < 1 || n > 4096) return FA_EINVAL;
@@ -472,7 +479,7 @@ int fa_device_bytes(const fa_ctx* c, unsigned long long* field_bytes, unsigned l
                                  &c->io32b, &c->tmp64, &c->tmp32, &c->partials, &c->r64, &c->u64, &c->rt64,
                                  &c->r32, &c->u32, &c->rt32, &c->y64, &c->xs64, &c->us64, &c->bhost_dev,
                                  &c->yhost_dev, &c->gx, &c->gpart, &c->store64, &c->store32, &c->snap64,
-                                 &c->snap32, &c->xrel, &c->brel, &c->snapx, &c->defl};
+                                 &c->snap32, &c->xrel, &c->brel, &c->snapx, &c->defl, &c->eig};
     // scalars: solver state, shifts, records, pass-2 weights, batch descriptors
     const fa::DevBuf* scal[] = {&c->state, &c->shiftbuf, &c->rec, &c->prec, &c->coef, &c->cs, &c->coef4,
                                 &c->descbuf, &c->flagbuf};

@@ -92,6 +92,7 @@ struct fa_ctx {
     int mrhs_rpb = 0, mrhs_mb = 0;       // multi-RHS FP32 sweep shape of batches led by this context (0: default)
     fa::DevBuf xrel, brel, snapx;        // reliable updates: seed solution, packed source, snapshot
     fa::DevBuf defl;                     // deflated sign: partial sums, coefficients, projected source
+    fa::DevBuf eig;                      // eigensolver: Krylov basis, work spinors, partials
     std::vector<fa::GraphEntry> graphs;  // captured outer iterations
     void* pinned = nullptr;              // host copy of DevState
     size_t pinned_bytes = 0;
@@ -133,6 +134,8 @@ int solve(fa_ctx* c, const double* b_canon, double* y_canon, double* const* xs_c
 int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* const* y_canon,
                 double* const* xs_canon, const fa_solver_params* p, fa_solver_stats* stats);
 int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out);
+int eigs_smallest(fa_ctx* c, int k, int m, double tol, int max_restarts, const fa_solver_params* p,
+                  unsigned long long seed, double* lambda, double* R, double* Lv, int* nconv, int* nsolve);
 int autotune_batch(fa_ctx* const* ctxs, int n, int reps, int* rhs_per_block, int* min_blocks, double* times_ms,
                    int ntimes);
 int apply_sign(fa_ctx* c, const double* b, double* out, const fa_solver_params* p, fa_solver_stats* stats,

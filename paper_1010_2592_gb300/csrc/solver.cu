@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(kThreads) k_dots_canon(int n, const double2* _
     if (t == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(sre[0], sim[0]);
 }
 // out[e] = base[e] + g(e) sum_i coef[i] V_i[e]; g(e) = -1 on spins 2, 3 (the
-// canonical site holds 4 spins x 3 colours) when g5, else 1.  base may be out.
+// canonical site holds 4 spins x 3 colours) when g5, else 1.  base may be out,
+// or null (then out = the combination alone).
 __global__ void __launch_bounds__(kThreads) k_lincomb_canon(int n, int k, const double2* __restrict__ coef,
                                                             const double2* __restrict__ V, const double2* base,
                                                             double2* out, int g5) {
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_lincomb_canon(int n, int k, const 
             re = -re;
             im = -im;
         }
-        const double2 c = base[e];
+        const double2 c = base != nullptr ? base[e] : make_double2(0.0, 0.0);
         out[e] = make_double2(c.x + re, c.y + im);
     }
 }
@@ -1005,7 +1006,8 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         } else if (prec == FA_F32) {
             cap32 = (long long)std::min<double>(Lo.max_outer, budget / per32t);
         } else {
-            cap64 = (long long)std::min<double>(std::min(Lo.max_outer, 64), 0.4 * budget / per64t);
+            // the head's (wider) slots take up to half of the budget
+            cap64 = (long long)std::min<double>(std::min(Lo.max_outer, 64), 0.5 * budget / per64t);
             cap32 = (long long)std::min<double>(Lo.max_outer, (budget - (double)cap64 * per64t) / per32t);
         }
         cap64 = std::max(0LL, cap64);
@@ -1648,3 +1650,5 @@ int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out) {
 }
 
 }  // namespace fa
+
+#include "eigs_impl.cuh"
