@@ -392,7 +392,8 @@ def run_ns_sweep(args):
     ctx.close()
 
 
-def batched_measure(steps, warmup, ells=None, one_at_a_time=True, name="wilson_batched_72"):
+def batched_measure(steps, warmup, ells=None, one_at_a_time=True, name="wilson_batched_72", store_gb=0.0,
+                    with_head=True):
     """72 systems: 12 spin-colour point sources on each of 6 lattices of three
     shapes (2 x 8^4, 2 x 12^3 x 24, 2 x 16^3 x 32), mu_k ~ U[0, 0.2], 16 Neuberger
     poles, FP32 bulk, pseudo-double-pass.  One step = one fa_apply_f_batched
@@ -421,27 +422,31 @@ def batched_measure(steps, warmup, ells=None, one_at_a_time=True, name="wilson_b
             srcs.append(torch.from_numpy(src).cuda())
         owners.append(owner)
     torch.cuda.synchronize()
-    free, _ = torch.cuda.mem_get_info()
+    torch.cuda.empty_cache()
+    free, total = torch.cuda.mem_get_info()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     out = {"workload": name, "systems": len(ctxs), "ns": w["ns"],
            "lattices": ["x".join(map(str, l["dims"])) for l in w["lattice_systems"]],
            "mu": [round(l["mu"], 4) for l in w["lattice_systems"]], "form": "pseudo",
            "launches": "one launch per kernel for all 72 systems (work tables); FP32 sweeps by lattice group",
-           "l2": "flushed before every timed step (512 MB write)"}
+           "l2": "flushed before every timed step (512 MB write)",
+           "free_gb_at_start": free / 1e9, "device_gb": total / 1e9}
     tune = fa.autotune_batched(ctxs, reps=5)   # multi-RHS sweep shape for this batch (untimed)
     out["mrhs_shape"] = {"rhs_per_block": tune["rhs_per_block"], "min_blocks": tune["min_blocks"]}
     # FP32 bulk at l = 2 and l = 4; at l = 4 the FP32-only form stays above 1e-6
     # (power-basis cancellation), so the same batch also runs with a double-float head
     # (the head switches at 0.04/l^2 = 0.0025: the batch's bound is 1e-6, which
     # this meets with orders of magnitude to spare, for fewer head iterations)
-    runs = [(ell, "f32") for ell in (ells or w["ell"])] + [(4, "mixed_df")]
+    runs = [(ell, "f32") for ell in (ells or w["ell"])] + ([(4, "mixed_df")] if with_head else [])
     for ell, precision in runs:
         kw = dict(ell=ell, tol=w["tol"], max_outer=4000, mode="pseudo", precision=precision,
-                  store_gb=0.4 * free / 1e9, graph=True, switch_resid=0.04 / ell ** 2 if precision != "f32" else 0.0)
+                  store_gb=store_gb if store_gb > 0 else 0.4 * free / 1e9, graph=True,
+                  switch_resid=0.04 / ell ** 2 if precision != "f32" else 0.0)
         ys, st = fa.apply_f_batched(ctxs, srcs, **kw)          # warm-up (also instantiates graphs)
         for _ in range(max(0, warmup - 1)):
             fa.apply_f_batched(ctxs, srcs, **kw)
         times = []
+        torch.cuda.nvtx.range_push(f"batched_l{ell}_{precision}")
         for _ in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -451,9 +456,11 @@ def batched_measure(steps, warmup, ells=None, one_at_a_time=True, name="wilson_b
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
+        torch.cuda.nvtx.range_pop()
         row = {"ms_batched": statistics.mean(times), "systems_per_s": len(ctxs) / (statistics.mean(times) * 1e-3),
                "outer_iters_max": max(x["outer_iters"] for x in st),
-               "outer_iters_min": min(x["outer_iters"] for x in st)}
+               "outer_iters_min": min(x["outer_iters"] for x in st),
+               "stored_outer": st[0]["stored_outer"], "store_gb": kw["store_gb"]}
         if one_at_a_time:
             # the same 72 solves, one at a time, each with its share of the store budget
             kw1 = dict(kw, store_gb=kw["store_gb"] / len(ctxs))
@@ -480,7 +487,11 @@ def batched_measure(steps, warmup, ells=None, one_at_a_time=True, name="wilson_b
 
 
 def run_batched(args):
-    print(json.dumps(dict(mode="batched", **batched_measure(args.steps, args.warmup))), flush=True)
+    """--workload wilson_batched_72: the batch alone (with --quick: l 2, FP32 only,
+    without the one-at-a-time comparison)."""
+    out = batched_measure(args.steps, args.warmup, ells=(2,) if args.quick else None,
+                          one_at_a_time=not args.quick, store_gb=args.store_gb, with_head=not args.quick)
+    print(json.dumps(dict(mode="batched", **out)), flush=True)
 
 
 def large_measure(steps, warmup, name="wilson_32x32x32x64"):
@@ -506,7 +517,8 @@ def large_measure(steps, warmup, name="wilson_32x32x32x64"):
     b = torch.from_numpy(w["b"]).cuda()
     ns = w["ns"]
     del w
-    free, _ = torch.cuda.mem_get_info()
+    torch.cuda.empty_cache()
+    free, total = torch.cuda.mem_get_info()
     ref = ctx.apply_f(b, ell=ell, tol=1e-12, max_outer=4000, mode="double", precision="f64")
     yref, yn = ref.y, torch.linalg.vector_norm(ref.y).item()
     kw = dict(ell=ell, max_outer=4000, mode="pseudo", precision="mixed_df", switch_resid=0.0,
@@ -541,6 +553,7 @@ def large_measure(steps, warmup, name="wilson_32x32x32x64"):
            "ms": statistics.mean(times), "tol": tol, "rel_err_vs_f64": e, "meets_1e-8": e <= TARGET,
            "reference": "the library's FP64 double-pass solve at tol 1e-12", "outer_iters": st["outer_iters"],
            "switch_outer": st["switch_outer"], "stored_outer": st["stored_outer"],
+           "free_gb_at_start": free / 1e9, "store_gb": kw["store_gb"], "device_gb": total / 1e9,
            "hop_f32_plain": {"mean_launch_ms": hop_ms, "launches": hop_n, "gbs": gbs,
                              "frac_of_measured_hbm": gbs / peak if gbs else None,
                              "bytes_per_launch": 384.0 * V},
@@ -697,6 +710,7 @@ def main():
     hop64_ms, hop64_n = ctx.hop_timing("f64")
     hopdf_ms, hopdf_n = ctx.hop_timing("df", dot=False)       # k_hop1_rows<df, false>
     hopdfd_ms, hopdfd_n = ctx.hop_timing("df", dot=True)      # k_hop1_rows<df, true>
+    hopg_ms, hopg_n = ctx.hop_timing("f32", dot="gram")       # k_hop_gram (Gram-matrix epilogue)
 
     # comparison variants (fewer steps)
     other = {}
@@ -830,7 +844,21 @@ def main():
         roofdfd["traffic"] = 128.135e6 + 10.071e6
         for r_ in (roof32, roof32d, roofdf, roofdfd):
             r_["traffic_source"] = src
-    roofs = [roof32, roof32d, roof64, roofdf, roofdfd]
+    roofg = roof(f"k_hop_gram<{ell}> (the outer iteration's last FP32 sweep with the Gram matrix in its epilogue)",
+                 "hbm", (384.0 + 96.0 * ell) * V, hopg_ms, hopg_n, "GB/s", peak, peak_src,
+                 "algorithmic_bytes_per_launch", 1e9)
+    roofg["traffic_source"] = None
+    # the plain FP32 sweep timed alone: the autotuner's chains of back-to-back
+    # launches (each reads the previous one's output) between two CUDA events,
+    # against the burst copy peak
+    alone_ms = min(tune["times_ms"]) if tune.get("times_ms") else None
+    roof_alone = {"kernel": "k_hop1<float, false> timed alone (fa_autotune: chains of back-to-back sweeps, best "
+                            "round, the faster shape)", "bound": "hbm", "achieved": 384.0 * V / (alone_ms * 1e-3) / 1e9
+                  if alone_ms else None, "peak": peak, "unit": "GB/s", "peak_source": peak_src + " (burst copy)",
+                  "mean_launch_ms": alone_ms, "algorithmic_bytes_per_launch": 384.0 * V, "traffic": None,
+                  "traffic_source": None}
+    roof_alone["frac"] = roof_alone["achieved"] / peak if roof_alone["achieved"] else None
+    roofs = [roof32, roof32d, roof64, roofdf, roofdfd, roofg]
     dominant = max(roofs, key=lambda r: r["total_ms"])
 
     line = {
@@ -848,6 +876,8 @@ def main():
         "roofline_hop_f64": roof64,
         "roofline_hop_df": roofdf,
         "roofline_hop_df_dot": roofdfd,
+        "roofline_hop_f32_gram": roofg,
+        "roofline_hop_f32_alone": roof_alone,
         "stencil_gbs": achieved,
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": int(b_pin.numel() * 16),
                 "d2h_bytes_per_step": int(y_pin.numel() * 16), "rel_err": e2e_err,
