@@ -562,6 +562,59 @@ def large_measure(steps, warmup, name="wilson_32x32x32x64"):
     return out
 
 
+def trace_timeline(ctx, run, stats, V):
+    """One more graph-replayed solve with the kernel timeline tracer on
+    (fa_trace_start / fa_trace_stop): every block's entry and exit time, so the
+    launches are timed as they run in the replayed graphs, with nothing between
+    them.  Pass-1 outer iteration m is the run of launches that ends with its
+    k_mr; the first `switch_outer` are the double-float head, the rest up to
+    `outer_iters` the FP32 tail (iterations enqueued past convergence return at
+    once and are left out).  Returns the per-kernel spans of the FP32 tail, the
+    time per outer iteration, and the plain FP32 sweep's mean span."""
+    import paper_1010_2592_gb300 as fa
+    fa.trace_start(1 << 22)
+    try:
+        run()
+    finally:
+        rec, dropped = fa.trace_stop(1 << 22)
+    launches = fa.trace_launches(rec)
+    M, sw = stats["outer_iters"], max(0, stats["switch_outer"])
+    iters, cur = [], []
+    for L in launches:
+        cur.append(L)
+        if L["name"].startswith("k_mr<") and len(iters) < M:
+            iters.append(cur)
+            cur = []
+    if len(iters) < M:
+        return {"error": f"{len(iters)} outer iterations traced of {M}", "dropped": dropped}
+
+    def summary(lo, hi):
+        if hi <= lo:
+            return None
+        per = {}
+        for it in iters[lo:hi]:
+            for L in it:
+                d = per.setdefault(L["name"], [0, 0.0, 0.0])
+                d[0] += 1
+                d[1] += (L["end_ns"] - L["start_ns"]) / 1e3
+                d[2] += L["tail_ns"] / 1e3
+        n = hi - lo
+        # iteration time: first launch of iteration k to first launch of k + 1
+        spans = [iters[k + 1][0]["start_ns"] - iters[k][0]["start_ns"] for k in range(lo, min(hi, M - 1))]
+        busy = sum(L["end_ns"] - L["start_ns"] for it in iters[lo:hi] for L in it) / n / 1e3
+        per_it = sum(spans) / len(spans) / 1e3 if spans else None
+        return {"outer_iterations": n, "us_per_outer_iteration": per_it, "kernel_us_per_outer_iteration": busy,
+                "gaps_us_per_outer_iteration": (per_it - busy) if per_it else None,
+                "kernels": {k: {"launches_per_iteration": v[0] / n, "mean_span_us": v[1] / v[0],
+                                "mean_last_block_tail_us": v[2] / v[0]} for k, v in per.items()}}
+    tail = iters[sw:M]
+    plain = [L for it in tail for L in it if L["name"] == "k_hop1<f32>"]
+    mean_ms = sum(L["end_ns"] - L["start_ns"] for L in plain) / len(plain) / 1e6 if plain else None
+    return {"fp32_tail": summary(sw, M), "double_float_head": summary(0, sw), "dropped": dropped,
+            "launches_traced": len(launches), "hop_f32_plain_mean_ms": mean_ms, "hop_f32_plain_launches": len(plain),
+            "pass1_us": (iters[M - 1][-1]["end_ns"] - iters[0][0]["start_ns"]) / 1e3}
+
+
 def measured_hbm_peak():
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
@@ -705,6 +758,14 @@ def main():
     clk = clocks.stop()
     torch.cuda.synchronize()
     ms_step = max_over_ranks(statistics.mean(head_ms), dist, "cuda")
+    # the same solve once more, graph-replayed, with the kernel timeline tracer on
+    try:
+        kw_t = dict(variants["pseudo_mixed"])
+        tol_t = chosen["pseudo_mixed"][0]
+        timeline = trace_timeline(ctx, lambda: ctx.apply_f(b, ell=ell, tol=tol_t, max_outer=4000, **kw_t),
+                                  head_res.stats, V)
+    except Exception as ex:   # reported, never fatal to the bench line
+        timeline = {"error": f"{type(ex).__name__}: {ex}"}
     hop32_ms, hop32_n = ctx.hop_timing("f32", dot=False)      # k_hop1<float, false>
     hop32d_ms, hop32d_n = ctx.hop_timing("f32", dot=True)     # k_hop1<float, true>
     hop64_ms, hop64_n = ctx.hop_timing("f64")
@@ -767,7 +828,8 @@ def main():
                           "hop_f32_gram_ms": ctx.hop_timing("f32", dot="gram")[0],
                           "gram_epilogue": not args.no_gram_epilogue,
                           "hop_f32_gbs": 384.0 * V / (hop32_ms * 1e-3) / 1e9 if hop32_ms else None,
-                          "launches_per_solve": head_launches // max(1, args.steps), "clocks": clk}),
+                          "launches_per_solve": head_launches // max(1, args.steps), "clocks": clk,
+                          "timeline": timeline}),
               flush=True)
         ctx.close()
         return
@@ -849,15 +911,29 @@ def main():
                  "algorithmic_bytes_per_launch", 1e9)
     roofg["traffic_source"] = None
     # the plain FP32 sweep timed alone: the autotuner's chains of back-to-back
-    # launches (each reads the previous one's output) between two CUDA events,
-    # against the burst copy peak
+    # launches (each reads the previous one's output), replayed from a CUDA graph
+    # as in the solve, between two CUDA events, against the burst copy peak
     alone_ms = min(tune["times_ms"]) if tune.get("times_ms") else None
-    roof_alone = {"kernel": "k_hop1<float, false> timed alone (fa_autotune: chains of back-to-back sweeps, best "
-                            "round, the faster shape)", "bound": "hbm", "achieved": 384.0 * V / (alone_ms * 1e-3) / 1e9
+    roof_alone = {"kernel": "k_hop1<float, false> timed alone (fa_autotune: a CUDA graph of 20 back-to-back "
+                            "sweeps, best of three rounds, the faster shape)", "bound": "hbm", "achieved": 384.0 * V / (alone_ms * 1e-3) / 1e9
                   if alone_ms else None, "peak": peak, "unit": "GB/s", "peak_source": peak_src + " (burst copy)",
                   "mean_launch_ms": alone_ms, "algorithmic_bytes_per_launch": 384.0 * V, "traffic": None,
                   "traffic_source": None}
     roof_alone["frac"] = roof_alone["achieved"] / peak if roof_alone["achieved"] else None
+    # the plain FP32 sweep inside the graph-replayed solve: mean span (first block
+    # entry to last block exit) from the kernel timeline tracer, over the FP32
+    # tail's launches of one traced repeat of the timed solve
+    tr_ms = timeline.get("hop_f32_plain_mean_ms") if isinstance(timeline, dict) else None
+    roof_graph = {"kernel": "k_hop1<float, false> inside the graph-replayed solve", "bound": "hbm",
+                  "measured_over": "kernel spans (earliest block entry to latest block exit, %globaltimer, "
+                                   "fa_trace_start/fa_trace_stop) of the FP32 tail of one graph-replayed repeat of "
+                                   "the timed solve; no events or other work between the launches",
+                  "achieved": 384.0 * V / (tr_ms * 1e-3) / 1e9 if tr_ms else None, "peak": peak, "unit": "GB/s",
+                  "peak_source": peak_src, "mean_launch_ms": tr_ms,
+                  "launches": timeline.get("hop_f32_plain_launches") if isinstance(timeline, dict) else None,
+                  "algorithmic_bytes_per_launch": 384.0 * V, "traffic": roof32["traffic"],
+                  "traffic_source": roof32["traffic_source"]}
+    roof_graph["frac"] = roof_graph["achieved"] / peak if roof_graph["achieved"] else None
     roofs = [roof32, roof32d, roof64, roofdf, roofdfd, roofg]
     dominant = max(roofs, key=lambda r: r["total_ms"])
 
@@ -878,6 +954,8 @@ def main():
         "roofline_hop_df_dot": roofdfd,
         "roofline_hop_f32_gram": roofg,
         "roofline_hop_f32_alone": roof_alone,
+        "roofline_hop_f32_graph": roof_graph,
+        "timeline": timeline,
         "stencil_gbs": achieved,
         "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": int(b_pin.numel() * 16),
                 "d2h_bytes_per_step": int(y_pin.numel() * 16), "rel_err": e2e_err,

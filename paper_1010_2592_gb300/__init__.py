@@ -36,7 +36,7 @@ EXPORTS = (
     "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune", "fa_autotune_batched",
-    "fa_eigs_smallest",
+    "fa_eigs_smallest", "fa_trace_start", "fa_trace_stop",
 )
 
 # FP32 sweep launch shapes (fa_hop_shape)
@@ -128,6 +128,8 @@ def load_library(path=LIB_PATH):
         "fa_autotune_batched": (I, [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D), I]),
         "fa_eigs_smallest": (I, [P, I, I, D, I, ctypes.POINTER(SolverParams), ctypes.c_ulonglong, P, P, P,
                                  ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "fa_trace_start": (I, [LL]),
+        "fa_trace_stop": (I, [P, LL, ctypes.POINTER(LL), ctypes.POINTER(LL)]),
         "fa_status_string": (ctypes.c_char_p, [I]),
         "fa_last_error": (ctypes.c_char_p, []),
         "fa_version": (ctypes.c_char_p, []),
@@ -197,6 +199,70 @@ def autotune_batched(contexts, reps=10):
     grid = [(r, m) for r in (1, 2, 3, 4, 6, 12, 16) for m in (7, 4)]
     return {"rhs_per_block": rpb.value, "min_blocks": mb.value,
             "times_ms": {f"{r}x{m}": float(t) for (r, m), t in zip(grid, times)}}
+
+
+# kernel timeline tracing (fa_trace_start / fa_trace_stop)
+TRACE_KERNELS = {1: "k_update_u", 2: "k_update_r", 3: "k_gram", 4: "k_mr", 5: "k_hop_sys", 6: "k_hop_mrhs",
+                 7: "k_hop_sys_rows", 8: "k_hop1_rows", 9: "k_hop1", 10: "k_hop_gram", 11: "k_reliable",
+                 12: "k_gather", 13: "k_sweep", 14: "k_coef_reduce", 15: "k_advance"}
+TRACE_PRECISION = {0: "f64", 1: "f32", 2: "df"}
+TRACE_DTYPE = [("t_start_ns", "<u8"), ("t_end_ns", "<u8"), ("kernel", "<i4"), ("block", "<i4"), ("sm", "<i4"),
+               ("grid", "<i4")]
+
+
+def trace_start(capacity=1 << 21):
+    """Turn kernel timeline tracing on for the current device (fa_trace_start)."""
+    _check(load_library().fa_trace_start(int(capacity)), "fa_trace_start")
+
+
+def trace_stop(capacity=1 << 21):
+    """Turn tracing off; returns (records, dropped): a numpy structured array
+    with the fields of fa_trace_record, and the number of records lost."""
+    import numpy as np
+    rec = np.zeros(int(capacity), dtype=TRACE_DTYPE)
+    n, dropped = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load_library().fa_trace_stop(rec.ctypes.data, int(capacity), ctypes.byref(n), ctypes.byref(dropped)),
+           "fa_trace_stop")
+    return rec[: n.value], dropped.value
+
+
+def trace_kernel_name(kernel):
+    """'k_hop1<f32, dot>' style name of a record's kernel field."""
+    base = TRACE_KERNELS.get(kernel & 0xff, str(kernel & 0xff))
+    tags = [TRACE_PRECISION.get((kernel >> 8) & 3, "?")]
+    if (kernel >> 10) & 1:
+        tags.append("dot" if base.startswith("k_hop") else "shifts")
+    return f"{base}<{', '.join(tags)}>"
+
+
+def trace_launches(records):
+    """Group block records into launches of one stream: sorted by entry time, a
+    launch ends where a block enters after every block so far has left.
+    Returns a list of dicts: kernel, name, start_ns, end_ns, blocks, grid,
+    tail_ns (latest exit minus the second latest: the last block's own tail)."""
+    import numpy as np
+    if len(records) == 0:
+        return []
+    r = records[np.argsort(records["t_start_ns"], kind="stable")]
+    out = []
+    cur = None
+    ends = []
+    for x in r:
+        t0, t1 = int(x["t_start_ns"]), int(x["t_end_ns"])
+        if cur is None or t0 > cur["end_ns"]:
+            if cur is not None:
+                ends.sort()
+                cur["tail_ns"] = ends[-1] - ends[-2] if len(ends) > 1 else 0
+            cur = {"kernel": int(x["kernel"]), "name": trace_kernel_name(int(x["kernel"])), "start_ns": t0,
+                   "end_ns": t1, "blocks": 0, "grid": int(x["grid"])}
+            out.append(cur)
+            ends = []
+        cur["end_ns"] = max(cur["end_ns"], t1)
+        cur["blocks"] += 1
+        ends.append(t1)
+    ends.sort()
+    cur["tail_ns"] = ends[-1] - ends[-2] if len(ends) > 1 else 0
+    return out
 
 
 def _torch():

@@ -558,26 +558,62 @@ int fa_autotune(fa_ctx* c, int reps, double* times_ms) {
     CUDA_OR(cudaEventCreate(&e1), "fa_autotune: event");
     double best_ms[2] = {1e30, 1e30};
     int rc = FA_OK;
+    const bool saved_timing = c->hop_timing;
+    c->hop_timing = false;
     auto chain = [&](int n) {
         for (int k = 0; k < n && rc == FA_OK; ++k)
             rc = hop_f32(c, buf[k & 1], buf[(k + 1) & 1], 1.0, false, true, false, nullptr, nullptr, nullptr);
     };
+    // The solver replays its outer iterations from CUDA graphs, so the chains are
+    // timed the same way where the stream can be captured (not the legacy or
+    // per-thread default stream); else as direct launches.
+    const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
+    cudaGraphExec_t ge[2] = {nullptr, nullptr};
+    for (int shape = FA_SHAPE_WIDE; capturable && shape <= FA_SHAPE_NARROW && rc == FA_OK; ++shape) {
+        c->hop_shape = shape;
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "fa_autotune: begin capture");
+            break;
+        }
+        chain(reps);
+        const cudaError_t ee = cudaStreamEndCapture(c->stream, &gr);
+        if (rc == FA_OK && ee != cudaSuccess) rc = cuda_fail(ee, "fa_autotune: end capture");
+        if (rc == FA_OK) {
+            const cudaError_t ei = cudaGraphInstantiate(&ge[shape - 1], gr, 0);
+            if (ei != cudaSuccess) rc = cuda_fail(ei, "fa_autotune: instantiate");
+        }
+        if (gr) cudaGraphDestroy(gr);
+    }
     for (int round = 0; round < 3 && rc == FA_OK; ++round) {
         for (int shape = FA_SHAPE_WIDE; shape <= FA_SHAPE_NARROW && rc == FA_OK; ++shape) {
             c->hop_shape = shape;
-            chain(3);
-            cudaEventRecord(e0, c->stream);
-            chain(reps);
-            cudaEventRecord(e1, c->stream);
-            if (rc != FA_OK) break;
+            cudaGraphExec_t x = ge[shape - 1];
+            if (x) {
+                if (round == 0) cudaGraphLaunch(x, c->stream);   // first replay uploads the graph
+                cudaEventRecord(e0, c->stream);
+                cudaGraphLaunch(x, c->stream);
+                cudaEventRecord(e1, c->stream);
+                const cudaError_t el = cudaGetLastError();
+                if (el != cudaSuccess) { rc = cuda_fail(el, "fa_autotune: graph launch"); break; }
+            } else {
+                chain(3);
+                cudaEventRecord(e0, c->stream);
+                chain(reps);
+                cudaEventRecord(e1, c->stream);
+                if (rc != FA_OK) break;
+            }
             if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "fa_autotune: timing"); break; }
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
             best_ms[shape - 1] = std::min(best_ms[shape - 1], (double)ms / reps);
         }
     }
+    for (auto x : ge)
+        if (x) cudaGraphExecDestroy(x);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    c->hop_timing = saved_timing;
     if (rc != FA_OK) {
         c->hop_shape = saved;
         return rc;

@@ -38,6 +38,7 @@ template <int L, int NT, int MB>
 __global__ void __launch_bounds__(NT, MB)
 k_hop_gram(GramHop A, const SolverDev* __restrict__ ds) {
     dep_sync();
+    const TraceScope trace_(trace_kind<float>(FA_TK_HOP_GRAM));
     const SolverDev& d = ds[0];
     if (sys_idle(d, 0)) return;
     const int s = (int)blockIdx.x * NT + (int)threadIdx.x;

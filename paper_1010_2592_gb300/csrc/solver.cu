@@ -1127,8 +1127,9 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
         }
     }
     if (!all_done) {
-        // main loop: chunks of outer iterations; poll the previous chunk's done flags
-        const int chunk = (Lo.V * (long long)n) >= (1 << 17) ? 2 : 8;
+        // main loop: chunks of outer iterations; poll the previous chunk's done
+        // flags (iterations enqueued past convergence return at once)
+        const int chunk = (Lo.V * (long long)n) >= (1 << 17) ? 4 : 8;
         int* pin = static_cast<int*>(c0->pinned);
         cudaEvent_t pe[2];
         FA_CUDA(cudaEventCreateWithFlags(&pe[0], cudaEventDisableTiming), "event");
@@ -1144,8 +1145,14 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
                 if (rc != FA_OK) break;
             }
             if (rc != FA_OK) break;
-            k_flags<<<(n + 127) / 128, 128, 0, st>>>(B.dev, n, B.flags + (k & 1) * n);
-            cudaMemcpyAsync(pin + (k & 1) * n, B.flags + (k & 1) * n, n * sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (n == 1) {
+                // one system: its done flag straight from the device state
+                cudaMemcpyAsync(pin + (k & 1), &B.host[0].st->done, sizeof(int), cudaMemcpyDeviceToHost, st);
+            } else {
+                k_flags<<<(n + 127) / 128, 128, 0, st>>>(B.dev, n, B.flags + (k & 1) * n);
+                c0->launches++;
+                cudaMemcpyAsync(pin + (k & 1) * n, B.flags + (k & 1) * n, n * sizeof(int), cudaMemcpyDeviceToHost, st);
+            }
             cudaEventRecord(pe[k & 1], st);
             if (k > 0) {
                 cudaEventSynchronize(pe[(k - 1) & 1]);
@@ -1652,3 +1659,4 @@ int estimate_scale(fa_ctx* c, const double* v0, int iters, double* scale_out) {
 }  // namespace fa
 
 #include "eigs_impl.cuh"
+#include "trace_impl.cuh"

@@ -23,6 +23,7 @@
 #pragma once
 
 #include "hop_device.cuh"
+#include "trace.cuh"
 
 namespace fa {
 
@@ -169,6 +170,14 @@ template <> struct Ch<double> {
     __device__ __forceinline__ void stv(T* b, int q, int V, int s) const {
         b[(size_t)q * V + s] = make_double2(c[0].r, c[0].i);
     }
+    // evict-first store / load (occurrence store: written once, read once by the gather)
+    __device__ __forceinline__ void stv_cs(T* b, int q, int V, int s) const {
+        __stcs(b + (size_t)q * V + s, make_double2(c[0].r, c[0].i));
+    }
+    __device__ __forceinline__ static Ch ld_cs(const T* b, int q, int V, int s) {
+        double2 t = __ldcs(b + (size_t)q * V + s);
+        Ch r; r.c[0] = {t.x, t.y}; return r;
+    }
 };
 template <> struct Ch<df> {
     static constexpr int W = 1, N = 12;
@@ -181,6 +190,13 @@ template <> struct Ch<df> {
     __device__ __forceinline__ void stv(T* b, int q, int V, int s) const {
         b[(size_t)q * V + s] = make_float4(c[0].r.hi, c[0].r.lo, c[0].i.hi, c[0].i.lo);
     }
+    __device__ __forceinline__ void stv_cs(T* b, int q, int V, int s) const {
+        __stcs(b + (size_t)q * V + s, make_float4(c[0].r.hi, c[0].r.lo, c[0].i.hi, c[0].i.lo));
+    }
+    __device__ __forceinline__ static Ch ld_cs(const T* b, int q, int V, int s) {
+        float4 t = __ldcs(b + (size_t)q * V + s);
+        Ch r; r.c[0] = {df(t.x, t.y), df(t.z, t.w)}; return r;
+    }
 };
 template <> struct Ch<float> {
     static constexpr int W = 2, N = 6;
@@ -192,6 +208,13 @@ template <> struct Ch<float> {
     }
     __device__ __forceinline__ void stv(T* b, int q, int V, int s) const {
         b[(size_t)q * V + s] = make_float4(c[0].r, c[0].i, c[1].r, c[1].i);
+    }
+    __device__ __forceinline__ void stv_cs(T* b, int q, int V, int s) const {
+        __stcs(b + (size_t)q * V + s, make_float4(c[0].r, c[0].i, c[1].r, c[1].i));
+    }
+    __device__ __forceinline__ static Ch ld_cs(const T* b, int q, int V, int s) {
+        float4 t = __ldcs(b + (size_t)q * V + s);
+        Ch r; r.c[0] = {t.x, t.y}; r.c[1] = {t.z, t.w}; return r;
     }
 };
 
@@ -775,6 +798,7 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_update_u(const SolverDev* __restrict__ ds, int j, int pass2, const int4* tab) {
     dep_sync();
+    const TraceScope trace_(trace_kind<R>(FA_TK_UPDATE_U));
     const Where w = where<false>(tab);
     const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
@@ -810,6 +834,7 @@ template <typename R, bool ACC, bool SHIFTS, bool XS = false>
 __global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_update_r(const SolverDev* __restrict__ ds, int j, int pass2, const int4* tab) {
     dep_sync();
+    const TraceScope trace_(trace_kind<R>(FA_TK_UPDATE_R, XS));
     const Where w = where<XS>(tab);
     const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
@@ -840,7 +865,7 @@ k_update_r(const SolverDev* __restrict__ ds, int j, int pass2, const int4* tab) 
         for (int i = 0; i <= j; ++i) {
             typename Ch<R>::T* ri = r + i * vs;
             Ch<R> a = Ch<R>::ld(ri, q, d.V, s), b = Ch<R>::ld(u + (i + 1) * vs, q, d.V, s);
-            if (store != nullptr) a.stv(store + slot_old(j, i) * vs, q, d.V, s);
+            if (store != nullptr) a.stv_cs(store + slot_old(j, i) * vs, q, d.V, s);
             if (ACC) {
                 const cx<R> c = weight<R>(d.coef, d.coef4, cf0 + slot_old(j, i));
 #pragma unroll
@@ -907,6 +932,7 @@ template <typename R, int L>
 __global__ void __launch_bounds__(kThreads, gram_min_blocks<R, L>())
 k_gram(const SolverDev* __restrict__ ds, int shifts, const int4* tab) {
     dep_sync();
+    const TraceScope trace_(trace_kind<R>(FA_TK_GRAM));
     const Where w = where<false>(tab);
     const SolverDev& d = ds[w.sys];
     if (sys_idle(d, 0)) return;
@@ -964,6 +990,7 @@ template <typename R, int L, bool ACC, bool SHIFTS, bool DOT, bool XS = false>
 __global__ void __launch_bounds__(kThreads, mr_min_blocks<R, L>())
 k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step, const int4* tab) {
     dep_sync();
+    const TraceScope trace_(trace_kind<R>(FA_TK_MR, XS));
     const Where w = where<XS>(tab);
     const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
@@ -1001,7 +1028,7 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step, const int4* t
             for (int i = 0; i <= L; ++i) rv[i] = Ch<R>::ld(r + i * vs, q, d.V, s);
             if (store != nullptr) {
 #pragma unroll
-                for (int k = 0; k < L; ++k) rv[k].stv(store + slot_mr(L, k) * vs, q, d.V, s);
+                for (int k = 0; k < L; ++k) rv[k].stv_cs(store + slot_mr(L, k) * vs, q, d.V, s);
             }
             if (ACC) {
                 cx<R> t[Ch<R>::W];
@@ -1129,6 +1156,7 @@ __global__ void __launch_bounds__(kThreads, hop_min_blocks<R>())
 k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
           ScalarStep step, const int4* tab) {
     dep_sync();
+    const TraceScope trace_(trace_kind<R>(FA_TK_HOP_SYS, DOT));
     const Where w = where<false>(tab);
     const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
@@ -1181,6 +1209,7 @@ k_hop_mrhs(const SolverDev* __restrict__ ds, const GroupDev* __restrict__ groups
            int in_sel, int in_j, int out_sel, int out_j, int second, int pass2, ScalarStep step) {
     constexpr int NT = kHopNarrowThreads;
     dep_sync();
+    const TraceScope trace_(trace_kind<float>(FA_TK_HOP_MRHS, DOT));
     const int4 it = items[blockIdx.x];
     const GroupDev& G = groups[it.x];
     const int tile = it.y;
@@ -1219,6 +1248,7 @@ __global__ void __launch_bounds__(kRowThreads, rows_sys_min_blocks<DOT>())
 k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, int out_j, int second, int pass2,
                ScalarStep step, const int4* tab) {
     dep_sync();
+    const TraceScope trace_(trace_kind<R>(FA_TK_HOP_SYS_ROWS, DOT));
     const Where w = where<false>(tab);
     const SolverDev& d = ds[w.sys];
     if (sys_idle(d, pass2)) return;
@@ -1246,6 +1276,7 @@ k_hop1_rows(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag,
             SpinorView<R> dotv, double2* partials, const int* done, const SolverDev* __restrict__ ds,
             ScalarStep step) {
     dep_sync();
+    const TraceScope trace_(trace_kind<R>(FA_TK_HOP1_ROWS, DOT));
     if (done != nullptr && *done) return;
     cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv, blockIdx.x)};
     if (DOT) {
@@ -1259,6 +1290,7 @@ __global__ void __launch_bounds__(NT, MB)
 k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R chop, R ef, R eb, R bc,
        SpinorView<R> dotv, double2* partials, const int* done, const SolverDev* __restrict__ ds, ScalarStep step) {
     dep_sync();
+    const TraceScope trace_(trace_kind<R>(FA_TK_HOP1, DOT));
     if (done != nullptr && *done) return;
     const int s = blockIdx.x * NT + threadIdx.x;
     cx<R> dres[1] = {czero<R>()};
@@ -1288,6 +1320,7 @@ k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R ch
 template <typename R>
 __global__ void __launch_bounds__(kThreads, kVecBlocks)
 k_reliable(const SolverDev* __restrict__ ds, const double2* ax, int pass2, ScalarStep step) {
+    const TraceScope trace_(trace_kind<R>(FA_TK_RELIABLE));
     const SolverDev& d = ds[blockIdx.y];   // one system (reliable updates are not batched)
     if (sys_idle(d, pass2)) return;
     typename Ch<R>::T* r0 = Vec<R>::r(d);
@@ -1356,6 +1389,7 @@ template <> struct GatherAcc<double> {
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_gather(const SolverDev* __restrict__ ds) {
+    const TraceScope trace_(trace_kind<R>(FA_TK_GATHER));
     const SolverDev& d = ds[blockIdx.y];
     const int nsb = (d.V + kThreads - 1) / kThreads;
     const int q = blockIdx.x / nsb;
@@ -1390,7 +1424,7 @@ k_gather(const SolverDev* __restrict__ ds) {
     for (; k0 + 4 <= n; k0 += 4) {
         Ch<R> v[4];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) v[g] = Ch<R>::ld(base + (size_t)(k0 + g) * vs, q, d.V, s);
+        for (int g = 0; g < 4; ++g) v[g] = Ch<R>::ld_cs(base + (size_t)(k0 + g) * vs, q, d.V, s);
         cx<R> t[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) t[w] = czero<R>();
@@ -1407,7 +1441,7 @@ k_gather(const SolverDev* __restrict__ ds) {
 #pragma unroll
         for (int w = 0; w < W; ++w) t[w] = czero<R>();
         for (int k = k0; k < n; ++k) {
-            const Ch<R> v = Ch<R>::ld(base + (size_t)k * vs, q, d.V, s);
+            const Ch<R> v = Ch<R>::ld_cs(base + (size_t)k * vs, q, d.V, s);
             const cx<R> c = weight<R>(d.coef, d.coef4, cf0 + k);
 #pragma unroll
             for (int w = 0; w < W; ++w) t[w] = cfma(c, v.c[w], t[w]);
@@ -1427,6 +1461,7 @@ k_gather(const SolverDev* __restrict__ ds) {
 // pass 2: advance the outer-iteration counter
 __global__ void k_advance(const SolverDev* __restrict__ ds) {
     dep_sync();
+    const TraceScope trace_(FA_TK_ADVANCE);
     DevState* S = ds[blockIdx.x].st;
     if (S->m < S->n_outer) S->m += 1;
 }
@@ -1450,6 +1485,7 @@ __global__ void k_flags(const SolverDev* __restrict__ ds, int n, int* out) {
 // is formed by k_coef_reduce.
 template <int L>
 __global__ void k_sweep(const SolverDev* __restrict__ ds) {
+    const TraceScope trace_(FA_TK_SWEEP);
     const SolverDev& d = ds[blockIdx.y];
     const int sh = blockIdx.x * blockDim.x + threadIdx.x;
     if (sh >= d.ns) return;
@@ -1504,6 +1540,7 @@ __global__ void k_sweep(const SolverDev* __restrict__ ds) {
 
 // coef[m][k] = sum_s omega_s cs[s][m][k] for m < M (fixed order over s)
 __global__ void k_coef_reduce(const SolverDev* __restrict__ ds) {
+    const TraceScope trace_(FA_TK_COEF_REDUCE);
     const SolverDev& d = ds[blockIdx.y];
     const int M = d.st->n_outer;
     const int NC = nc_slots(d.L);

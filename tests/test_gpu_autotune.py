@@ -64,3 +64,32 @@ def test_bad_shape_and_order_errors():
     with pytest.raises(fa.FAError) as e:
         ctx.autotune(reps=2)
     assert e.value.status == fa.FA_ESTATE
+
+
+def test_autotune_on_a_capturable_stream():
+    """On a side stream the chains are replayed from a CUDA graph (as the solver
+    replays its outer iterations); the stream is usable afterwards and the
+    results do not change."""
+    import torch
+    dims = (16, 16, 16, 32)
+    w = inputs.make_workload("wilson_16x16x16x32", dims)
+    stream = torch.cuda.Stream()
+    ctx = fa.Context(dims, stream)
+    ctx.set_gauge(to_dev(w["U"]))
+    ctx.set_params(w["mass"], w["mu"], w["t_bc"], 0.03)
+    with torch.cuda.stream(stream):
+        psi = to_dev(w["b"])
+    stream.synchronize()
+    out = ctx.apply_dw(psi, precision="f32")
+    stream.synchronize()
+    before = to_host(out)
+    r = ctx.autotune(reps=10)
+    assert not r["cached"] and all(0 < x < 1.0 for x in r["times_ms"])
+    assert r["shape"] in (fa.SHAPE_WIDE, fa.SHAPE_NARROW)
+    out = ctx.apply_dw(psi, precision="f32")
+    stream.synchronize()
+    assert np.array_equal(before, to_host(out))
+    ctx.set_poles(*fa.neuberger_poles(4))
+    res = ctx.apply_f(psi, ell=2, tol=1e-6, mode="pseudo", precision="f32", graph=True)
+    stream.synchronize()
+    assert res.stats["status"] == 0
