@@ -297,7 +297,21 @@ __device__ __forceinline__ void acc_x(double2* x, int q, int V, int s, double2 a
 // sub-partition's FP64 pipe for tens of cycles, a division for hundreds), so
 // the steps use fused multiply-adds, one real division per complex inverse,
 // and reuse inverses between the per-shift scalars.
-__device__ __forceinline__ bool last_block(DevState* S, int ntickets) {
+//
+// The step's code runs once per launch, in whichever block takes the last
+// ticket, so its instructions are usually not in that SM's instruction cache:
+// on GB300 (16^3 x 32 solve) fetching them from L2 took most of the last
+// block's time (a reduction of 2 x 512 partials: 4.6 us with cold code, 1.3 us
+// with the same code run once before on other data).  So the blocks that take
+// one of the last kWarmTickets tickets, other than the last, run the step as a
+// dry run (no partial loads, no stores; `dry` below) before they exit: the
+// blocks that share an SM with the last block finish shortly before it, and
+// their dry runs bring the code into that SM's instruction cache while the
+// last block still works.  Results do not change: a dry run reads state but
+// writes nothing outside its own shared memory.
+constexpr unsigned kWarmTickets = 1024, kWarmSkip = 32;
+enum { LB_NONE = 0, LB_WARM = 1, LB_LAST = 2 };
+__device__ __forceinline__ int last_block(DevState* S, int ntickets) {
     __shared__ int is_last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -307,14 +321,18 @@ __device__ __forceinline__ bool last_block(DevState* S, int ntickets) {
         // read the partials after the barrier, from L2)
         __threadfence();
         const unsigned t = atomicAdd(&S->ticket, 1u);
-        is_last = t == (unsigned)ntickets - 1u;
-        if (is_last) {
+        // (the last kWarmSkip before the last block run no dry run: they would
+        // end after it on an SM whose code is still cold)
+        is_last = t == (unsigned)ntickets - 1u ? LB_LAST
+                  : (t + kWarmTickets >= (unsigned)ntickets && t + 1u + kWarmSkip < (unsigned)ntickets ? LB_WARM
+                                                                                                 : LB_NONE);
+        if (is_last == LB_LAST) {
             S->ticket = 0u;   // every block of this launch has taken its ticket
             __threadfence();
         }
     }
     __syncthreads();
-    return is_last != 0;
+    return is_last;
 }
 
 __device__ __forceinline__ dcx zneg(dcx a) { return {-a.r, -a.i}; }   // a sign flip, free on FMA operands
@@ -363,21 +381,29 @@ __device__ __forceinline__ void recip2(double p, double q, double& ip, double& i
 // otherwise FP64 values summed in FP64.
 template <typename R> constexpr bool dfp_of() { return !std::is_same<R, double>::value; }
 
+// dry: warp 0 runs the code of one quarter once, every load predicated off
+// (the sums are 0); the other warps only meet the barriers.
 template <int NSMAX, bool DFP>
-__device__ __forceinline__ void reduce_slots(const double2* part, int nblk, int ns, dcx* out) {
+__device__ __forceinline__ void reduce_slots(const double2* part, int nblk, int ns, dcx* out, bool dry = false) {
     __shared__ double2 qs[4 * NSMAX];
     __shared__ float4 qf[4 * NSMAX];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int per = (nblk + 3) >> 2;
-    for (int u = warp; u < 4 * ns; u += nw) {
+    const int ntask = dry ? 1 : 4 * ns;
+    if (dry && (int)threadIdx.x < 4 * ns) {   // the quarters a dry run leaves out
+        qs[threadIdx.x] = make_double2(0.0, 0.0);
+        qf[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    for (int u = warp; u < ntask; u += nw) {
         const int k = u >> 2;
-        const int i0 = (u & 3) * per, i1 = min(nblk, i0 + per);
+        const int i0 = (u & 3) * per, i1 = dry ? i0 : min(nblk, i0 + per);
+        const int iend = dry ? i0 + 32 : i1;
         if constexpr (DFP) {
             const float4* pf = reinterpret_cast<const float4*>(part) + (size_t)k * nblk;
             df a(0.0f), b(0.0f);
             // eight loads in flight per lane before the adds (zero padding
             // leaves the sums unchanged)
-            for (int ib = i0 + lane; ib < i1; ib += 32 * 8) {
+            for (int ib = i0 + lane; ib < iend; ib += 32 * 8) {
                 float4 v[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
@@ -399,14 +425,14 @@ __device__ __forceinline__ void reduce_slots(const double2* part, int nblk, int 
         } else {
             const double2* pd = part + (size_t)k * nblk;
             double a = 0.0, b = 0.0;
-            for (int ib = i0 + lane; ib < i1; ib += 32 * 8) {
+            for (int ib = i0 + lane; ib < iend; ib += 32 * 8) {
                 double2 v[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int i = ib + 32 * t;
                     v[t] = i < i1 ? __ldcg(pd + i) : make_double2(0.0, 0.0);
                 }
-                const int nt = min(8, (i1 - ib + 31) >> 5);   // loads that hit (FP64 adds are scarce)
+                const int nt = min(8, (max(i1, ib + 1) - ib + 31) >> 5);   // loads that hit (FP64 adds are scarce)
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     if (t < nt) {
@@ -427,7 +453,7 @@ __device__ __forceinline__ void reduce_slots(const double2* part, int nblk, int 
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
         if constexpr (DFP) {
             df a(0.0f), b(0.0f);
-#pragma unroll
+#pragma unroll 1
             for (int q = 0; q < 4; ++q) {
                 const float4 t = qf[4 * k + q];
                 a = addR(a, df(t.x, t.y));
@@ -486,20 +512,21 @@ __device__ __noinline__ void sc_init(const SolverDev& d, int nblk, double tol, d
 
 // beta of BiCG sub-step j >= 1 from partials of <rt, r_j>
 template <bool DFP>
-__device__ __noinline__ void sc_beta(const SolverDev& d, int j, int nblk) {
+__device__ __noinline__ void sc_beta(const SolverDev& d, int j, int nblk, bool dry) {
     DevState* S = d.st;
     // the state loads are issued with the partial loads and consumed after the
     // reduction (one memory round trip; the done flag only matters then)
     const int done = S->done, m = S->m;
     const dcx rho0 = ld(S->rho0), alpha = ld(S->alpha);
     __shared__ dcx red[1];
-    reduce_slots<1, DFP>(d.part, nblk, 1, red);
+    reduce_slots<1, DFP>(d.part, nblk, 1, red, dry);
     if (done) return;
     if (threadIdx.x == 0) {
         const dcx rho1 = red[0];
-        if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
+        if (zabs2(rho0) == 0.0) { if (!dry) fail(S, FA_EBREAKDOWN); return; }
         const dcx beta = zmul(zmul(alpha, rho1), zinv(rho0));
-        if (!zfinite(beta)) { fail(S, FA_ENONFINITE); return; }
+        if (!zfinite(beta)) { if (!dry) fail(S, FA_ENONFINITE); return; }
+        if (dry) { red[0] = beta; return; }   // (kept, so that the arithmetic stays on the dry path)
         S->rho0 = pk(rho1);
         d.rec_beta[m * d.L + j] = pk(beta);
     }
@@ -507,18 +534,19 @@ __device__ __noinline__ void sc_beta(const SolverDev& d, int j, int nblk) {
 
 // alpha of BiCG sub-step j from partials of <rt, u_{j+1}> (seed part)
 template <bool DFP>
-__device__ __noinline__ void sc_alpha_seed(const SolverDev& d, int j, int nblk) {
+__device__ __noinline__ void sc_alpha_seed(const SolverDev& d, int j, int nblk, bool dry) {
     DevState* S = d.st;
     const int done = S->done, m = S->m;
     const dcx rho0 = ld(S->rho0);
     __shared__ dcx red[1];
-    reduce_slots<1, DFP>(d.part, nblk, 1, red);
+    reduce_slots<1, DFP>(d.part, nblk, 1, red, dry);
     if (done) return;
     if (threadIdx.x == 0) {
-        const dcx den = red[0];
+        const dcx den = dry ? mk(1.0) : red[0];
         if (zabs2(den) == 0.0) { fail(S, FA_EBREAKDOWN); return; }
         const dcx alpha = zmul(rho0, zinv(den));
-        if (!zfinite(alpha)) { fail(S, FA_ENONFINITE); return; }
+        if (!zfinite(alpha)) { if (!dry) fail(S, FA_ENONFINITE); return; }
+        if (dry) { red[0] = alpha; return; }
         d.rec_alpha[m * d.L + j] = pk(alpha);
         S->alpha = pk(alpha);
         S->alpha_prev = pk(alpha);
@@ -576,16 +604,18 @@ __device__ __noinline__ void sc_alpha_shifts(const SolverDev& d, int j) {
 // MR coefficients gamma (seed part) from the Gram partials: diagonally scaled
 // normal equations, Gaussian elimination with partial pivoting.
 template <int L, bool DFP>
-__device__ __noinline__ void sc_mr_seed(const SolverDev& d, int nblk) {
+__device__ __noinline__ void sc_mr_seed(const SolverDev& d, int nblk, bool dry) {
     DevState* S = d.st;
     const int done = S->done, m = S->m;
     constexpr int NG = n_gram(L);
     __shared__ dcx G[NG];
-    reduce_slots<NG, DFP>(d.part, nblk, NG, G);
+    reduce_slots<NG, DFP>(d.part, nblk, NG, G, dry);
     if (done || threadIdx.x != 0) return;
     int bad = 0;
     // slot of (i, k), i <= k, in the row-major upper triangle
     auto slot = [](int i, int k) { return i * (L + 1) - i * (i - 1) / 2 + (k - i); };
+    if (dry)   // a regular Gram matrix, so that the dry run takes the solving path
+        for (int i = 0; i <= L; ++i) G[slot(i, i)] = mk(1.0);
     dcx gam[L + 1];
     gam[0] = mk(-1.0);
     for (int i = 1; i <= L; ++i) {
@@ -656,6 +686,10 @@ __device__ __noinline__ void sc_mr_seed(const SolverDev& d, int nblk) {
     if (!bad)
         for (int j = 1; j <= L; ++j)
             if (!zfinite(gam[j])) bad = FA_ENONFINITE;
+    if (dry) {
+        if (!bad) G[0] = gam[L];
+        return;
+    }
     if (bad) { fail(S, bad); return; }
     for (int j = 0; j <= L; ++j) d.rec_gamma[m * (L + 1) + j] = pk(gam[j]);
     S->omega = pk(gam[L]);
@@ -706,7 +740,7 @@ __device__ __noinline__ void sc_mr_shifts(const SolverDev& d) {
 
 // end of an outer iteration: convergence and freezing of shifts, next beta
 template <bool DFP>
-__device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
+__device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head, bool dry) {
     DevState* S = d.st;
     // every load the step needs is issued with the partial loads and consumed
     // after the reduction (one memory round trip)
@@ -717,10 +751,10 @@ __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     const int act = sh < d.ns ? d.active[sh] : 0;
     const double2 zv = sh < d.ns ? d.zeta[sh] : make_double2(0.0, 0.0);
     __shared__ dcx red[2];
-    reduce_slots<2, DFP>(d.part, nblk, 2, red);
+    reduce_slots<2, DFP>(d.part, nblk, 2, red, dry);
     if (done) return;
-    const dcx rtr = red[0];
-    const double rn2 = red[1].r;
+    const dcx rtr = dry ? mk(1.0) : red[0];
+    const double rn2 = dry ? 1.0 : red[1].r;
     __shared__ int n_act, all_small;
     if (threadIdx.x == 0) { n_act = 0; all_small = 1; }
     __syncthreads();
@@ -728,8 +762,10 @@ __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     if (act) {
         const double z2 = zabs2(ld(zv));
         if (last || rn2 <= tol2b * z2) {
-            d.active[sh] = 0;
-            d.iters[sh] = m + 1;
+            if (!dry) {
+                d.active[sh] = 0;
+                d.iters[sh] = m + 1;
+            }
         } else {
             atomicAdd(&n_act, 1);
             if (rn2 > theta2b * z2) atomicAnd(&all_small, 0);
@@ -737,16 +773,31 @@ __device__ __noinline__ void sc_conv(const SolverDev& d, int nblk, int head) {
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    S->rnorm2 = rn2;
-    S->m = m + 1;
-    S->n_active = n_act;
-    if (!isfinite(rn2) || !zfinite(rtr)) { fail(S, FA_ENONFINITE); S->n_outer = m + 1; return; }
-    if (head && all_small) S->switch_req = 1;
-    if (n_act == 0) { S->done = 1; S->n_outer = m + 1; return; }
-    if (m + 1 >= d.max_outer) { fail(S, FA_ENOCONV); S->n_outer = m + 1; return; }
+    if (!dry) {
+        S->rnorm2 = rn2;
+        S->m = m + 1;
+        S->n_active = n_act;
+    }
+    if (!isfinite(rn2) || !zfinite(rtr)) {
+        if (!dry) { fail(S, FA_ENONFINITE); S->n_outer = m + 1; }
+        return;
+    }
+    if (head && all_small && !dry) S->switch_req = 1;
+    if (n_act == 0) {
+        if (!dry) { S->done = 1; S->n_outer = m + 1; }
+        return;
+    }
+    if (m + 1 >= d.max_outer) {
+        if (!dry) { fail(S, FA_ENOCONV); S->n_outer = m + 1; }
+        return;
+    }
     const dcx rho0 = zneg(zmul(omega, rho_old));
-    if (zabs2(rho0) == 0.0) { fail(S, FA_EBREAKDOWN); S->n_outer = m + 1; return; }
+    if (zabs2(rho0) == 0.0) {
+        if (!dry) { fail(S, FA_EBREAKDOWN); S->n_outer = m + 1; }
+        return;
+    }
     const dcx beta = zmul(zmul(alpha, rtr), zinv(rho0));
+    if (dry) { red[0] = beta; return; }
     S->rho0 = pk(rtr);
     d.rec_beta[(m + 1) * d.L] = pk(beta);
 }
@@ -764,20 +815,26 @@ struct ScalarStep {
     int arg;
 };
 
-// nblk: partials of the reduction; ntickets: blocks of the system in this launch
+// nblk: partials of the reduction; ntickets: blocks of the system in this launch;
+// warm: a late block that is not the last may run the step dry (last_block)
 template <bool DFP>
-__device__ __forceinline__ void run_step(const SolverDev& d, ScalarStep e, int nblk, int ntickets) {
-    if (e.kind == STEP_NONE || !last_block(d.st, ntickets)) return;
+__device__ __forceinline__ void run_step(const SolverDev& d, ScalarStep e, int nblk, int ntickets, bool warm = true) {
+    if (e.kind == STEP_NONE) return;
+    const int lb = last_block(d.st, ntickets);
+    // (FP64 kernels run no dry runs: their sweeps are bound by the FP64 pipe,
+    // which the dry step would share)
+    if (lb == LB_NONE || (lb == LB_WARM && (!warm || !DFP))) return;
+    const bool dry = lb == LB_WARM;
     if (e.kind == STEP_BETA) {
-        sc_beta<DFP>(d, e.arg, nblk);
+        sc_beta<DFP>(d, e.arg, nblk, dry);
     } else if (e.kind == STEP_ALPHA || e.kind == STEP_ALPHA_ALL) {
-        sc_alpha_seed<DFP>(d, e.arg, nblk);
-        if (e.kind == STEP_ALPHA_ALL) {
+        sc_alpha_seed<DFP>(d, e.arg, nblk, dry);
+        if (e.kind == STEP_ALPHA_ALL && !dry) {
             __syncthreads();
             sc_alpha_shifts(d, e.arg);
         }
     } else {
-        sc_conv<DFP>(d, nblk, e.arg);
+        sc_conv<DFP>(d, nblk, e.arg, dry);
     }
 }
 
@@ -963,9 +1020,10 @@ k_gram(const SolverDev* __restrict__ ds, int shifts, const int4* tab) {
         }
     }
     block_reduce_store<NG, R>(acc, partials, w.nbx, w.bx);
-    if (last_block(d.st, w.ntk)) {
-        sc_mr_seed<L, dfp_of<R>()>(d, w.nbx);
-        if (shifts) {
+    const int lb = last_block(d.st, w.ntk);
+    if (lb == LB_LAST || (lb == LB_WARM && dfp_of<R>())) {
+        sc_mr_seed<L, dfp_of<R>()>(d, w.nbx, lb == LB_WARM);
+        if (shifts && lb == LB_LAST) {
             __syncthreads();
             sc_mr_shifts<L>(d);
         }
@@ -1138,7 +1196,7 @@ k_dot2_sys(const SolverDev* __restrict__ ds, double tol, double theta, const int
     const Where w = where<false>(tab);
     const SolverDev& d = ds[w.sys];
     k_dot2_body<R>(d.V, Vec<R>::rt(d), Vec<R>::r(d), d.part, w.bx, w.nbx);
-    if (last_block(d.st, w.ntk)) sc_init<dfp_of<R>()>(d, w.nbx, tol, theta);
+    if (last_block(d.st, w.ntk) == LB_LAST) sc_init<dfp_of<R>()>(d, w.nbx, tol, theta);
 }
 
 // A application inside the solver: out = scale * g5 D in on the system's own
@@ -1237,7 +1295,7 @@ k_hop_mrhs(const SolverDev* __restrict__ ds, const GroupDev* __restrict__ groups
         }
         if (DOT) {
             block_reduce_store<1, float, NT>(dres, d.part, 0, tile);
-            run_step<true>(d, step, G.ntile, G.ntile);
+            run_step<true>(d, step, G.ntile, G.ntile, r == it.w - 1);   // no dry run before another sweep
         }
     }
 }
@@ -1262,7 +1320,7 @@ k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_s
                                                         w.bx)};
     if (DOT) {
         block_reduce_store<1, R, kRowThreads>(dres, d.part, 0, w.bx);
-        run_step<dfp_of<R>()>(d, step, w.nbx, w.ntk);
+        run_step<dfp_of<R>()>(d, step, w.nbx, w.ntk, false);   // ALU-bound sweep: no dry runs
     }
 }
 
@@ -1281,7 +1339,7 @@ k_hop1_rows(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag,
     cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv, blockIdx.x)};
     if (DOT) {
         block_reduce_store<1, R, kRowThreads>(dres, partials, 0, blockIdx.x);
-        run_step<dfp_of<R>()>(ds[0], step, gridDim.x, gridDim.x);
+        run_step<dfp_of<R>()>(ds[0], step, gridDim.x, gridDim.x, false);   // ALU-bound sweep: no dry runs
     }
 }
 
