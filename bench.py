@@ -906,21 +906,19 @@ def main():
                    11650.0 * V, hopdfd_ms, hopdfd_n, "T FP32-instructions/s", 40.3, nom,
                    "algorithmic_instructions_per_launch", 1e12)
     achieved = roof32["achieved"]
-    # DRAM traffic per launch from one ncu capture of the same kernels in the
-    # timed solve on this lattice (dram__bytes_read.sum + dram__bytes_write.sum;
-    # means over 10 + 6 FP32 and 30 + 18 double-float launches)
-    # (constants from that capture, applied only on its lattice; null elsewhere)
+    # DRAM traffic per launch from one ncu capture of the FP32 sweeps in the timed
+    # solve on this lattice (dram__bytes_read.sum + dram__bytes_write.sum; means
+    # over 2 + 2 launches); constants from that capture, applied only on its
+    # lattice, null elsewhere and for the double-float sweeps (not re-captured)
     src = ("ncu capture (dram__bytes_read.sum + dram__bytes_write.sum per launch) of these kernels inside "
            "the 16^3x32 headline solve, profiles/hop_traffic_16x16x16x32.md; fixed constants, not "
            "re-measured by this run")
     for r_ in (roof32, roof32d, roof64, roofdf, roofdfd):
         r_["traffic_source"] = None
     if V == 16 * 16 * 16 * 32:
-        roof32["traffic"] = 37.776e6 + 0.001e6
-        roof32d["traffic"] = 50.415e6 + 0.029e6
-        roofdf["traffic"] = 102.530e6 + 7.053e6
-        roofdfd["traffic"] = 128.135e6 + 10.071e6
-        for r_ in (roof32, roof32d, roofdf, roofdfd):
+        roof32["traffic"] = 37.777e6 + 0.005e6
+        roof32d["traffic"] = 50.423e6 + 0.183e6
+        for r_ in (roof32, roof32d):
             r_["traffic_source"] = src
     roofg = roof(f"k_hop_gram<{ell}> (the outer iteration's last FP32 sweep with the Gram matrix in its epilogue)",
                  "hbm", (384.0 + 96.0 * ell) * V, hopg_ms, hopg_n, "GB/s", peak, peak_src,
