@@ -899,11 +899,21 @@ def main():
     roof64 = roof("k_hop1<double> (one D_w sweep, FP64; both instances)", "alu", 1704.0 * V, hop64_ms, hop64_n,
                   "TFLOP/s", 1.25, "nominal GB300 FP64 (no measured FP64 peak)", "algorithmic_flops_per_launch",
                   1e12)
-    nom = "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal)"
+    # the FP32 issue peak measured on this GPU by the library's probe (eight
+    # independent FMA chains per thread, 2048 threads per SM); nominal
+    # 152 SMs x 128 lanes x 2.07 GHz = 40.3 T/s if the probe fails
+    try:
+        rate, _ = fa.fp32_issue_rate(5)
+        fp32_peak = rate / 1e12
+        nom = "measured: fa_fp32_issue_rate (FP32 FMA probe, 8 independent chains per thread, 2048 threads/SM)"
+    except Exception:
+        fp32_peak = 40.3
+        nom = "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal; the probe failed)"
     roofdf = roof("k_hop1_rows<df, false> (one D_w sweep, double-float head, row split)", "alu", 11650.0 * V,
-                  hopdf_ms, hopdf_n, "T FP32-instructions/s", 40.3, nom, "algorithmic_instructions_per_launch", 1e12)
+                  hopdf_ms, hopdf_n, "T FP32-instructions/s", fp32_peak, nom, "algorithmic_instructions_per_launch",
+                  1e12)
     roofdfd = roof("k_hop1_rows<df, true> (sweep + <rt, out> + seed step; the sweep's instructions only)", "alu",
-                   11650.0 * V, hopdfd_ms, hopdfd_n, "T FP32-instructions/s", 40.3, nom,
+                   11650.0 * V, hopdfd_ms, hopdfd_n, "T FP32-instructions/s", fp32_peak, nom,
                    "algorithmic_instructions_per_launch", 1e12)
     achieved = roof32["achieved"]
     # DRAM traffic per launch from one ncu capture of the FP32 sweeps in the timed
@@ -961,8 +971,8 @@ def main():
         "k_hop1<f32>": ("hbm", 384.0 * V, 1e9, peak, "GB/s", peak_src, roof32),
         "k_hop1<f32, dot>": ("hbm", 480.0 * V, 1e9, peak, "GB/s", peak_src, roof32d),
         "k_hop_gram<f32>": ("hbm", (384.0 + 96.0 * ell) * V, 1e9, peak, "GB/s", peak_src, roofg),
-        "k_hop1_rows<df>": ("alu", 11650.0 * V, 1e12, 40.3, "T FP32-instructions/s", nom, roofdf),
-        "k_hop1_rows<df, dot>": ("alu", 11650.0 * V, 1e12, 40.3, "T FP32-instructions/s", nom, roofdfd),
+        "k_hop1_rows<df>": ("alu", 11650.0 * V, 1e12, fp32_peak, "T FP32-instructions/s", nom, roofdf),
+        "k_hop1_rows<df, dot>": ("alu", 11650.0 * V, 1e12, fp32_peak, "T FP32-instructions/s", nom, roofdfd),
     }
     in_graph = [k for k in per_k if k in cand]
     dominant = dominant_events

@@ -36,7 +36,7 @@ EXPORTS = (
     "fa_hop_timing_split", "fa_hop_timing_reset", "fa_device_bytes", "fa_status_string", "fa_last_error", "fa_version",
     "fa_apply_A_noalloc", "fa_grad", "fa_apply_f_batched", "fa_share_gauge",
     "fa_set_hop_shape", "fa_get_hop_shape", "fa_autotune", "fa_autotune_batched",
-    "fa_eigs_smallest", "fa_trace_start", "fa_trace_stop",
+    "fa_eigs_smallest", "fa_trace_start", "fa_trace_stop", "fa_fp32_issue_rate",
 )
 
 # FP32 sweep launch shapes (fa_hop_shape)
@@ -118,6 +118,7 @@ def load_library(path=LIB_PATH):
                         ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
         "fa_sync": (I, [P]),
         "fa_launch_count": (LL, [P]),
+        "fa_fp32_issue_rate": (I, [I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "fa_hop_timing": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_split": (I, [P, I, I, ctypes.POINTER(D), ctypes.POINTER(LL)]),
         "fa_hop_timing_reset": (I, [P]),
@@ -208,6 +209,14 @@ TRACE_KERNELS = {1: "k_update_u", 2: "k_update_r", 3: "k_gram", 4: "k_mr", 5: "k
 TRACE_PRECISION = {0: "f64", 1: "f32", 2: "df"}
 TRACE_DTYPE = [("t_start_ns", "<u8"), ("t_end_ns", "<u8"), ("kernel", "<i4"), ("block", "<i4"), ("sm", "<i4"),
                ("grid", "<i4")]
+
+
+def fp32_issue_rate(reps=5):
+    """Measured FP32 instruction issue rate of the current device (fa_fp32_issue_rate):
+    (thread instructions per second, ms of the best probe launch)."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().fa_fp32_issue_rate(int(reps), ctypes.byref(rate), ctypes.byref(ms)), "fa_fp32_issue_rate")
+    return rate.value, ms.value
 
 
 def trace_start(capacity=1 << 21):

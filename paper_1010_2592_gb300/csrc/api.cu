@@ -472,6 +472,55 @@ int fa_sync(fa_ctx* c) {
 
 long long fa_launch_count(const fa_ctx* c) { return c ? c->launches : -1; }
 
+namespace fa {
+// FP32 issue-rate probe: eight independent FMA chains per thread, kFmaIters
+// steps of eight FMAs each; the sums leave the kernel only if a runtime value
+// says so (never), which keeps the chains alive.
+constexpr int kFmaIters = 4096;
+static __device__ float g_fma_sink;
+__global__ void __launch_bounds__(256) k_fma_probe(float b, float c, int never) {
+    float a0 = threadIdx.x * 1e-3f, a1 = a0 + 1.f, a2 = a0 + 2.f, a3 = a0 + 3.f;
+    float a4 = a0 + 4.f, a5 = a0 + 5.f, a6 = a0 + 6.f, a7 = a0 + 7.f;
+    for (int i = 0; i < kFmaIters; ++i) {
+        a0 = __fmaf_rn(a0, b, c); a1 = __fmaf_rn(a1, b, c); a2 = __fmaf_rn(a2, b, c); a3 = __fmaf_rn(a3, b, c);
+        a4 = __fmaf_rn(a4, b, c); a5 = __fmaf_rn(a5, b, c); a6 = __fmaf_rn(a6, b, c); a7 = __fmaf_rn(a7, b, c);
+    }
+    if (never) g_fma_sink = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+}  // namespace fa
+
+int fa_fp32_issue_rate(int reps, double* rate, double* ms_out) {
+    using namespace fa;
+    if (reps < 1 || !rate || !ms_out) return FA_EINVAL;
+    int dev = 0, nsm = 0;
+    CUDA_OR(cudaGetDevice(&dev), "fa_fp32_issue_rate: device");
+    CUDA_OR(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "fa_fp32_issue_rate: SMs");
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_OR(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "fa_fp32_issue_rate: stream");
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    const int blocks = 8 * nsm;   // 2048 threads per SM
+    float best = 0.f;
+    for (int r = 0; r <= reps && err == cudaSuccess; ++r) {   // launch 0: warm-up
+        cudaEventRecord(e0, st);
+        k_fma_probe<<<blocks, 256, 0, st>>>(0.999f, 1e-3f, 0);
+        cudaEventRecord(e1, st);
+        err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaGetLastError();
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && r > 0 && (best == 0.f || ms < best)) best = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (err != cudaSuccess) return cuda_fail(err, "fa_fp32_issue_rate");
+    *ms_out = best;
+    *rate = (double)blocks * 256.0 * 8.0 * (double)kFmaIters / (best * 1e-3);
+    return FA_OK;
+}
+
 int fa_device_bytes(const fa_ctx* c, unsigned long long* field_bytes, unsigned long long* scalar_bytes) {
     if (!c || !field_bytes || !scalar_bytes) return FA_EINVAL;
     // lattice-sized buffers: links, spinors, stores, staging, reduction partials

@@ -404,7 +404,53 @@ __device__ __forceinline__ void reduce_slots(const double2* part, int nblk, int 
         qs[threadIdx.x] = make_double2(0.0, 0.0);
         qf[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
-    for (int u = warp; u < ntask; u += nw) {
+    // Several slots (the Gram matrix) and quarters of at most 256 partials: each
+    // warp takes two quarters at a time, u and u + nw, with the sixteen loads in
+    // flight together (the loads were the time: six rounds of them for 6 x 1024
+    // partials in a 128-thread block).  The additions of each quarter are those
+    // of the loop below, in the same order.  A dry run takes this path too (its
+    // code is the one to bring into the instruction cache).
+    int u_first = warp;
+    if constexpr (DFP && NSMAX >= 3) {
+        if (per <= 256) {
+            for (int u = warp; u < ntask; u += 2 * nw) {
+                const int u2 = u + nw;
+                const bool two = u2 < ntask;
+                const int i0 = (u & 3) * per, i1 = dry ? i0 : min(nblk, i0 + per);
+                const int j0 = (u2 & 3) * per, j1 = (two && !dry) ? min(nblk, j0 + per) : j0;
+                const float4* pf = reinterpret_cast<const float4*>(part) + (size_t)(u >> 2) * nblk;
+                const float4* pg = reinterpret_cast<const float4*>(part) + (size_t)(u2 >> 2) * nblk;
+                float4 v[8], x[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int i = i0 + lane + 32 * t, j = j0 + lane + 32 * t;
+                    v[t] = i < i1 ? __ldcg(pf + i) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    x[t] = j < j1 ? __ldcg(pg + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+                df a(0.0f), b(0.0f), c(0.0f), e(0.0f);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    a = addR(a, df(v[t].x, v[t].y));
+                    b = addR(b, df(v[t].z, v[t].w));
+                    c = addR(c, df(x[t].x, x[t].y));
+                    e = addR(e, df(x[t].z, x[t].w));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a = addR(a, shfl_down_df(a, o));
+                    b = addR(b, shfl_down_df(b, o));
+                    c = addR(c, shfl_down_df(c, o));
+                    e = addR(e, shfl_down_df(e, o));
+                }
+                if (lane == 0) {
+                    qf[u] = make_float4(a.hi, a.lo, b.hi, b.lo);
+                    if (two) qf[u2] = make_float4(c.hi, c.lo, e.hi, e.lo);
+                }
+            }
+            u_first = ntask;   // every quarter done
+        }
+    }
+    for (int u = u_first; u < ntask; u += nw) {
         const int k = u >> 2;
         const int i0 = (u & 3) * per, i1 = dry ? i0 : min(nblk, i0 + per);
         const int iend = dry ? i0 + 32 : i1;

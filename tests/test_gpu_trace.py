@@ -70,3 +70,18 @@ def test_trace_full_ring_drops_and_errors():
     with pytest.raises(fa.FAError) as e:
         fa.trace_start(0)
     assert e.value.status == fa.FA_EINVAL
+
+
+def test_fp32_issue_rate_probe():
+    """The FP32 issue-rate probe (denominator of the double-float sweep's
+    roofline): positive, below the SMs x 128 lanes x 2.2 GHz ceiling, and the
+    argument checks."""
+    import ctypes
+    import torch
+    rate, ms = fa.fp32_issue_rate(3)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert ms > 0 and 0.2 * nsm * 128 * 1.0e9 < rate < nsm * 128 * 2.2e9, (rate, ms)
+    lib = fa.load_library()
+    r, m = ctypes.c_double(), ctypes.c_double()
+    assert lib.fa_fp32_issue_rate(0, ctypes.byref(r), ctypes.byref(m)) == fa.FA_EINVAL
+    assert lib.fa_fp32_issue_rate(1, None, ctypes.byref(m)) == fa.FA_EINVAL
