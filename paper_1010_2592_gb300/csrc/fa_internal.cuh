@@ -32,20 +32,11 @@ struct Geom {
 // serialization may be placed on the SMs while its predecessor in the stream
 // is still running; it must not touch global memory before `griddepcontrol.wait`
 // returns, which happens once the predecessor grid has completed and its writes
-// are visible.  For an ordinary launch the instruction returns at once.  Every
-// kernel that the solver may launch this way calls this first.
+// are visible.  `launch_dependents` then lets the successor start its own launch.
+// For an ordinary launch both instructions return at once.  Every kernel that
+// the solver may launch this way calls this first.
 __device__ __forceinline__ void dep_sync() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-// The dependent kernel may be launched once every block of this one has
-// passed dep_trigger() or exited; each kernel calls it (every thread of the
-// block) where its main work ends, before the reduction and scalar step of its
-// last block, so that the next kernel's blocks are placed on the SMs during
-// that step and wait in dep_sync() (no early launch during the main work: in
-// a launch of several waves the waiting blocks would take the slots of this
-// kernel's later blocks).  Memory order does not depend on it: dep_sync()
-// waits for this kernel to finish and its writes to be visible.
-__device__ __forceinline__ void dep_trigger() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 

@@ -74,7 +74,6 @@ k_hop_gram(GramHop A, const SolverDev* __restrict__ ds) {
                 }
         }
     }
-    dep_trigger();
     block_reduce_store<NG, float, NT>(red, A.part, gridDim.x, blockIdx.x);
     const int lb = last_block(d.st, gridDim.x);
     if (lb != LB_NONE) sc_mr_seed<L, true>(d, gridDim.x, lb == LB_WARM);

@@ -675,7 +675,7 @@ static int enqueue_outer_any(Batch& B, int rp, bool pass2, bool single, bool hea
     if (!B.use_graph) return enqueue_outer_direct(B, rp, pass2, single, head, rel);
     fa_ctx* c = B.c0;
     const int key = rp | (pass2 ? 4 : 0) | (single ? 8 : 0) | (head ? 16 : 0) | (rel ? 32 : 0) |
-                    (B.Lo.gram_hop ? 64 : 0) | (B.pdl ? 128 : 0);
+                    (B.Lo.gram_hop ? 64 : 0);
     std::vector<unsigned long long> sig = graph_signature(B);
     GraphEntry* ge = nullptr;
     for (auto& e : c->graphs)
@@ -962,11 +962,9 @@ int solve_batch(fa_ctx* const* ctxs, int n, const double* const* b, double* cons
     B.flags = c0->flagbuf.as<int>();
     // graphs need a capturable stream (not the legacy default stream)
     B.use_graph = (p->flags & 4) != 0 && c0->stream != nullptr && c0->stream != cudaStreamLegacy;
-    // programmatic dependent launch inside an outer iteration, direct or replayed
-    // from a graph (each kernel lets its successor launch where its main work
-    // ends, dep_trigger; 16^3 x 32 headline under graph replay 14.10-14.12 ms
-    // against 14.15-14.16 ms without)
-    B.pdl = (p->flags & 16) == 0;
+    // programmatic dependent launch for direct launches only: under CUDA-graph
+    // replay it measured slower (16^3 x 32 headline: 15.00 against 14.62 ms)
+    B.pdl = (p->flags & 16) == 0 && !B.use_graph;
     for (int i = 0; i < n; ++i) B.host.push_back(make_dev(B.sys[i], B.lo[i]));
     for (auto& h : B.host) h.fixed_iters = (p->flags & 8) ? 1 : 0;
     // Several systems: every launch serves all of them through work tables (any

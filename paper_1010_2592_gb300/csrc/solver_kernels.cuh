@@ -1075,7 +1075,6 @@ k_gram(const SolverDev* __restrict__ ds, int shifts, const int4* tab) {
                 }
         }
     }
-    dep_trigger();
     block_reduce_store<NG, R>(acc, partials, w.nbx, w.bx);
     const int lb = last_block(d.st, w.ntk);
     if (lb == LB_LAST || (lb == LB_WARM && dfp_of<R>())) {
@@ -1212,7 +1211,6 @@ k_mr(const SolverDev* __restrict__ ds, int pass2, ScalarStep step, const int4* t
             }
         }
     }
-    dep_trigger();
     if (DOT) {
         block_reduce_store<2, R>(dots, partials, nbx, bx);
         run_step<dfp_of<R>()>(d, step, nbx, w.ntk);
@@ -1296,7 +1294,6 @@ k_hop_sys(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_sel, i
             dres[0] = a;
         }
     }
-    dep_trigger();
     if (DOT) {
         block_reduce_store<1, R>(dres, d.part, 0, w.bx);
         run_step<dfp_of<R>()>(d, step, w.nbx, w.ntk);
@@ -1377,7 +1374,6 @@ k_hop_sys_rows(const SolverDev* __restrict__ ds, int in_sel, int in_j, int out_s
                                                         fromdbl<R>(sc * d.diag), fromdbl<R>(-0.5 * sc),
                                                         fromdbl<R>(d.ef), fromdbl<R>(d.eb), fromdbl<R>(d.bc), rt,
                                                         w.bx)};
-    dep_trigger();
     if (DOT) {
         block_reduce_store<1, R, kRowThreads>(dres, d.part, 0, w.bx);
         run_step<dfp_of<R>()>(d, step, w.nbx, w.ntk, false);   // ALU-bound sweep: no dry runs
@@ -1397,7 +1393,6 @@ k_hop1_rows(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag,
     const TraceScope trace_(trace_kind<R>(FA_TK_HOP1_ROWS, DOT));
     if (done != nullptr && *done) return;
     cx<R> dres[1] = {hop_rows_body<R, false, true, DOT>(g, U, in, out, cdiag, chop, ef, eb, bc, dotv, blockIdx.x)};
-    dep_trigger();
     if (DOT) {
         block_reduce_store<1, R, kRowThreads>(dres, partials, 0, blockIdx.x);
         run_step<dfp_of<R>()>(ds[0], step, gridDim.x, gridDim.x, false);   // ALU-bound sweep: no dry runs
@@ -1426,7 +1421,6 @@ k_hop1(Geom g, LinkView<R> U, SpinorView<R> in, SpinorView<R> out, R cdiag, R ch
             dres[0] = a;
         }
     }
-    dep_trigger();
     if (DOT) {
         block_reduce_store<1, R, NT>(dres, partials, 0, blockIdx.x);
         run_step<dfp_of<R>()>(ds[0], step, gridDim.x, gridDim.x);
