@@ -122,3 +122,34 @@ def test_invalid_arguments_rejected_before_any_device_call():
 
     ms, n = ctypes.c_double(), ctypes.c_longlong()
     assert lib.fa_hop_timing_split(None, fa.F32, 0, ctypes.byref(ms), ctypes.byref(n)) == fa.FA_EINVAL
+
+
+def _struct_fields(name):
+    """Field names, in order, of the typedef struct `name` in include/fapath.h."""
+    src = open(os.path.join(ROOT, "include", "fapath.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = re.sub(r"\[[^\]]*\]", "", decl).strip()     # drop array sizes
+        if decl:
+            # "type a, b, c": the first piece ends with the first name
+            fields += [piece.split()[-1].lstrip("*") for piece in decl.split(",")]
+    return fields
+
+
+def test_binding_structs_follow_the_header():
+    """The ctypes mirrors of fa_solver_params and fa_solver_stats list the
+    header's fields in the header's order (a field added on one side only would
+    shift every later one)."""
+    assert [f for f, _ in fa.SolverParams._fields_] == _struct_fields("fa_solver_params")
+    assert [f for f, _ in fa.SolverStats._fields_] == _struct_fields("fa_solver_stats")
+
+
+def test_status_codes_follow_the_header():
+    """Every fa_status code of the header has the same value in the binding."""
+    src = open(os.path.join(ROOT, "include", "fapath.h")).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"\b(FA_E[A-Z]+|FA_OK)\s*=\s*(-?\d+)", src))
+    assert len(codes) == 9
+    for k, v in codes.items():
+        assert getattr(fa, k) == v, k
